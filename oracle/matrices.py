@@ -1,0 +1,231 @@
+"""Dense Galerkin matrices of Sec. 3, from exact inner products (oracle, test infrastructure).
+
+Convention (Sec. 3, X_{lq} = (phi_q, phi_l)): row index = test function k,
+column index = trial function j, entry X[k, j] = (D^d trial_j, test_k)_sigma.
+
+Stiffness sign (reading of Sec. 3): the paper defines A = -(phi'', phi) but its
+Eqs. ufin, gfin, Biharmonic_matrix and Helmholtz_matrix are the Crank-Nicolson
+discretisation of Eqs. biharmonic / g only when A = +(phi'', phi).  Every
+stiffness matrix here is therefore the plain inner product (phi_j'', phi_k).
+
+Each entry is computed as an exact rational multiple of pi (``chebyshev``) and
+rounded to float64 once (correctly rounded integer division), then multiplied
+by pi in float64.
+"""
+import functools
+import math
+
+import numpy as np
+
+from . import chebyshev as cb
+
+
+def _exact_matrix(N, trial, test, nderiv, n_trial, n_test):
+    """Exact matrix X[k, j] = (D^nderiv trial_j, test_k)_sigma / pi as (num, den) ints.
+
+    trial(j, M) / test(k, M) return (integer coefficient list, integer scale):
+    the basis function equals coeffs / scale.
+    """
+    M = N  # N Chebyshev modes: coefficient indices 0..N-1
+    num = np.zeros((n_test, n_trial), dtype=object)
+    den = np.ones((n_test, n_trial), dtype=object)
+    tests = []
+    for k in range(n_test):
+        cv, sc = test(k, M)
+        nz = [(n, v) for n, v in enumerate(cv) if v]
+        tests.append((nz, sc))
+    for j in range(n_trial):
+        cv, sj = trial(j, M)
+        g = cb.cscale(cv)
+        for _ in range(nderiv):
+            g = cb.derivative_scaled(g)
+        for k in range(n_test):
+            nz, sk = tests[k]
+            s = 0
+            for n, v in nz:
+                if g[n]:
+                    s += g[n] * v
+            # (D^d trial_j, test_k)/pi = (1/2) sum_n g_n v_n / (sj * sk)
+            num[k, j] = s
+            den[k, j] = 2 * sj * sk
+    return num, den
+
+
+def _to_f64(num, den):
+    out = np.empty(num.shape, dtype=np.float64)
+    flat_n, flat_d, flat_o = num.ravel(), den.ravel(), out.ravel()
+    for i in range(flat_n.size):
+        n = flat_n[i]
+        flat_o[i] = 0.0 if n == 0 else n / flat_d[i]  # int/int: correctly rounded
+    return out * math.pi
+
+
+def _dirichlet(k, M):
+    return cb.dirichlet_int(k, M), 1
+
+
+def _biharmonic(k, M):
+    return cb.biharmonic_int(k, M), cb.biharmonic_scale(k)
+
+
+def _chebyshev(k, M):
+    c = [0] * M
+    c[k] = 1
+    return c, 1
+
+
+def _check_N(N, minimum):
+    if N < minimum:
+        raise ValueError(f"N={N} too small (need N >= {minimum})")
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet space (phi_k = T_k - T_{k+2}, k = 0..N-3)
+# ---------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=None)
+def mass_dirichlet_exact(N):
+    """B_D[k, j] = (phi_j, phi_k)_sigma / pi, exact (num, den) (Table tab:matrices)."""
+    _check_N(N, 4)
+    return _exact_matrix(N, _dirichlet, _dirichlet, 0, N - 2, N - 2)
+
+
+@functools.lru_cache(maxsize=None)
+def stiff_dirichlet_exact(N):
+    """A_D[k, j] = (phi_j'', phi_k)_sigma / pi, exact (Sec. 3, sign per the reading above)."""
+    _check_N(N, 4)
+    return _exact_matrix(N, _dirichlet, _dirichlet, 2, N - 2, N - 2)
+
+
+@functools.lru_cache(maxsize=None)
+def mass_dirichlet(N):
+    return _to_f64(*mass_dirichlet_exact(N))
+
+
+@functools.lru_cache(maxsize=None)
+def stiff_dirichlet(N):
+    return _to_f64(*stiff_dirichlet_exact(N))
+
+
+# ---------------------------------------------------------------------------
+# Biharmonic space (psi_k, k = 0..N-5)
+# ---------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=None)
+def mass_biharmonic_exact(N):
+    """B_B[k, j] = (psi_j, psi_k)_sigma / pi, exact (Table tab:matrices)."""
+    _check_N(N, 6)
+    return _exact_matrix(N, _biharmonic, _biharmonic, 0, N - 4, N - 4)
+
+
+@functools.lru_cache(maxsize=None)
+def stiff_biharmonic_exact(N):
+    """A_B[k, j] = (psi_j'', psi_k)_sigma / pi, exact."""
+    _check_N(N, 6)
+    return _exact_matrix(N, _biharmonic, _biharmonic, 2, N - 4, N - 4)
+
+
+@functools.lru_cache(maxsize=None)
+def bilaplace_biharmonic_exact(N):
+    """Q[k, j] = (psi_j'''', psi_k)_sigma / pi, exact (Eqs. N_Q, pk, rk)."""
+    _check_N(N, 6)
+    return _exact_matrix(N, _biharmonic, _biharmonic, 4, N - 4, N - 4)
+
+
+@functools.lru_cache(maxsize=None)
+def mass_biharmonic(N):
+    return _to_f64(*mass_biharmonic_exact(N))
+
+
+@functools.lru_cache(maxsize=None)
+def stiff_biharmonic(N):
+    return _to_f64(*stiff_biharmonic_exact(N))
+
+
+@functools.lru_cache(maxsize=None)
+def bilaplace_biharmonic(N):
+    return _to_f64(*bilaplace_biharmonic_exact(N))
+
+
+# ---------------------------------------------------------------------------
+# Coupling matrices of Table tab:matrices (used here only as further pins of
+# the inner-product machinery against printed closed forms).
+# ---------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=None)
+def coupling_exact(N, name):
+    """Exact (num, den) of a Table tab:matrices coupling matrix.
+
+    'M_B'  (phi_j, psi_k)     k = 0..N-5, j = 0..N-3
+    'C_B'  (phi_j', psi_k)    k = 0..N-5, j = 0..N-3
+    'C_D'  (psi_j', phi_k)    k = 0..N-3, j = 0..N-5
+    'C_T'  (phi_j', T_k)      k = 0..N-1, j = 0..N-3
+    """
+    _check_N(N, 6)
+    if name == "M_B":
+        return _exact_matrix(N, _dirichlet, _biharmonic, 0, N - 2, N - 4)
+    if name == "C_B":
+        return _exact_matrix(N, _dirichlet, _biharmonic, 1, N - 2, N - 4)
+    if name == "C_D":
+        return _exact_matrix(N, _biharmonic, _dirichlet, 1, N - 4, N - 2)
+    if name == "C_T":
+        return _exact_matrix(N, _dirichlet, _chebyshev, 1, N - 2, N)
+    raise ValueError(name)
+
+
+def coupling(N, name):
+    return _to_f64(*coupling_exact(N, name))
+
+
+# ---------------------------------------------------------------------------
+# Systems.  Scaled forms (c = 2 / (nu dt), z2 = squared wavenumber):
+#   Helmholtz   H_h = (z2 + c) B_D - A_D                      (alpha B - A)
+#   biharmonic  H_b = Q - (2 z2 + c) A_B + z2 (z2 + c) B_B     (S + a A + b B)
+# Paper forms (Eqs. Helmholtz_matrix, Biharmonic_matrix):
+#   Hbar = -(nu dt/2) A_D + (1 + nu dt z2/2) B_D
+#   Hchk = -(nu dt/2) Q + (1 + nu dt z2) A_B - (2 z2 + nu dt z2^2)/2 B_B
+# Right-hand-side operators (Eqs. gfin, ufin):
+#   paper:  2 B_D - Hbar ;  2 A_B - 2 z2 B_B - Hchk
+#   scaled: R_h = (c - z2) B_D + A_D ;  R_b = Q + (c - 2 z2) A_B + z2 (z2 - c) B_B
+# ---------------------------------------------------------------------------
+
+def helmholtz_system(N, alpha):
+    """alpha B_D - A_D, the Helmholtz matrix in scaled form."""
+    return alpha * mass_dirichlet(N) - stiff_dirichlet(N)
+
+
+def biharmonic_system(N, a, b):
+    """Q + a A_B + b B_B, the biharmonic matrix in scaled form."""
+    return bilaplace_biharmonic(N) + a * stiff_biharmonic(N) + b * mass_biharmonic(N)
+
+
+def helmholtz_rhs_operator(N, z2, c):
+    """R_h = (c - z2) B_D + A_D  (Eq. gfin, scaled by 2/(nu dt))."""
+    return (c - z2) * mass_dirichlet(N) + stiff_dirichlet(N)
+
+
+def biharmonic_rhs_operator(N, z2, c):
+    """R_b = Q + (c - 2 z2) A_B + z2 (z2 - c) B_B  (Eq. ufin, scaled by 2/(nu dt))."""
+    return (bilaplace_biharmonic(N) + (c - 2.0 * z2) * stiff_biharmonic(N)
+            + z2 * (z2 - c) * mass_biharmonic(N))
+
+
+def paper_helmholtz(N, z2, nu, dt):
+    """Hbar of Eq. Helmholtz_matrix (with A = +(phi'', phi))."""
+    return -(nu * dt / 2) * stiff_dirichlet(N) + (1 + nu * dt * z2 / 2) * mass_dirichlet(N)
+
+
+def paper_biharmonic(N, z2, nu, dt):
+    """Hchk of Eq. Biharmonic_matrix (with A = +(psi'', psi))."""
+    return (-(nu * dt / 2) * bilaplace_biharmonic(N) + (1 + nu * dt * z2) * stiff_biharmonic(N)
+            - (2 * z2 + nu * dt * z2 * z2) / 2 * mass_biharmonic(N))
+
+
+def paper_helmholtz_rhs(N, z2, nu, dt):
+    """2 B_D - Hbar  (Eq. gfin)."""
+    return 2 * mass_dirichlet(N) - paper_helmholtz(N, z2, nu, dt)
+
+
+def paper_biharmonic_rhs(N, z2, nu, dt):
+    """2 A_B - 2 z2 B_B - Hchk  (Eq. ufin)."""
+    return 2 * stiff_biharmonic(N) - 2 * z2 * mass_biharmonic(N) - paper_biharmonic(N, z2, nu, dt)
