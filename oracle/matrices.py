@@ -229,3 +229,33 @@ def paper_helmholtz_rhs(N, z2, nu, dt):
 def paper_biharmonic_rhs(N, z2, nu, dt):
     """2 A_B - 2 z2 B_B - Hchk  (Eq. ufin)."""
     return 2 * stiff_biharmonic(N) - 2 * z2 * mass_biharmonic(N) - paper_biharmonic(N, z2, nu, dt)
+
+
+# ---------------------------------------------------------------------------
+# Extended-precision copies (numpy longdouble) of the exact matrices, used only
+# to compute residuals for the refined reference solution in ``solve``.
+# ---------------------------------------------------------------------------
+
+def _to_ld(num, den):
+    out = np.empty(num.shape, dtype=np.longdouble)
+    flat_n, flat_d, flat_o = num.ravel(), den.ravel(), out.ravel()
+    for i in range(flat_n.size):
+        n = flat_n[i]
+        if n == 0:
+            flat_o[i] = 0
+        else:
+            # split so that numerator and denominator each fit a longdouble exactly enough
+            flat_o[i] = np.longdouble(n) / np.longdouble(flat_d[i])
+    return out * PI_LD
+
+
+PI_LD = np.longdouble("3.14159265358979323846264338327950288")
+
+
+@functools.lru_cache(maxsize=None)
+def ld_matrices(N, problem):
+    """(mass, stiffness[, bi-Laplacian]) in longdouble for 'helmholtz' / 'biharmonic'."""
+    if problem == "helmholtz":
+        return (_to_ld(*mass_dirichlet_exact(N)), _to_ld(*stiff_dirichlet_exact(N)))
+    return (_to_ld(*mass_biharmonic_exact(N)), _to_ld(*stiff_biharmonic_exact(N)),
+            _to_ld(*bilaplace_biharmonic_exact(N)))

@@ -401,3 +401,16 @@ def test_mode_layout():
     assert Z[0, 16] == pytest.approx((2 * 16) ** 2)      # Nyquist kz = -16
     for iz in range(1, 32):
         assert Z[5, iz] == Z[5, 32 - iz] or iz == 16     # (kx, kz) and (kx, -kz): same system
+
+
+@pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
+def test_refined_reference_matches_brute_force(problem):
+    """The longdouble-refined reference agrees with the 50-digit brute force to ~1e-15."""
+    N = 24
+    c = so.c_of(1 / 2000, 1e-4)
+    rng = np.random.default_rng(21)
+    for z2 in (0.0, 1145.0 ** 2):
+        f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        r = so.solve_mode_ref(problem, N, z2, c, f)
+        ub = so.solve_mp(problem, N, z2, c, f)
+        assert so.rel_l2(r, ub) <= 2e-15
