@@ -1,0 +1,314 @@
+"""Benchmark: batched Shen solves (Helmholtz + biharmonic per Fourier mode) on GB300.
+
+One step = one Helmholtz solve and one biharmonic solve of every mode of the
+workload (two right-hand-side fields in, two solution fields out), through the C
+ABI of libshensolve.  Default workload: N = 1024 Chebyshev modes, 1024 x 1024
+Fourier grid (513 x 1024 = 525,312 modes), nu = 1/2000, dt = 1e-4.
+
+Metric: Shen solves*N/s = (systems solved per step * N) / step time.
+Prints one JSON line (rank 0).  `--impl reference` times the oracle's O(N) C code
+(the paper's algorithms, OpenMP) on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "small": dict(N=64, Nx=32, Nz=32, nu=1 / 180, dt=1e-3),
+    "retau180": dict(N=128, Nx=128, Nz=128, nu=1 / 180, dt=5e-4),
+    "n1024": dict(N=1024, Nx=1024, Nz=1024, nu=1 / 2000, dt=1e-4),
+    "large": dict(N=1536, Nx=2048, Nz=1536, nu=1 / 2000, dt=5e-5),
+}
+METRIC = "Shen solves*N/s (Helmholtz + biharmonic, all modes)"
+BYTES_PER_ROW = 32          # algorithmic bytes per complex row of one solve: read f + write u
+
+
+def n_modes_of(w):
+    return (w["Nx"] // 2 + 1) * w["Nz"]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, precision_note, seconds_target=8.0, seed=0):
+    """The oracle's O(N) C solvers (paper's algorithms, OpenMP over modes) on a bounded
+    sample of the workload's modes; returns solves*N/s."""
+    from oracle import on
+    from oracle import solve as so
+    from paper_1701_03787_gb300 import inputs
+    N = w["N"]
+    c = so.c_of(w["nu"], w["dt"])
+    z2_all = so.mode_z2(w["Nx"], w["Nz"])
+    n_sample = min(z2_all.size, max(1024, int(2 ** 26 // (16 * N))))       # ~64 MB per field
+    idx = np.linspace(0, z2_all.size - 1, n_sample).astype(np.int64)
+    z2 = z2_all[idx]
+    F = inputs.rhs_numpy(n_sample, N, seed)
+    on.solve_modes("helmholtz", N, z2, c, F[:8])                             # load / warm
+    reps, t_total, t0 = 0, 0.0, time.perf_counter()
+    while True:
+        t = time.perf_counter()
+        on.solve_modes("helmholtz", N, z2, c, F)
+        on.solve_modes("biharmonic", N, z2, c, F)
+        t_total += time.perf_counter() - t
+        reps += 1
+        if time.perf_counter() - t0 > seconds_target or reps >= 50:
+            break
+    value = reps * 2 * n_sample * N / t_total
+    return {"value": value, "unit": "solves*N/s", "cores": on.max_threads(), "kind": "oracle",
+            "sample": f"{n_sample} of {z2_all.size} modes (evenly spaced), Helmholtz + biharmonic, "
+                      f"{reps} repetitions, O(N) C oracle (Sec. 4 algorithms), float64"}
+
+
+def oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined_modes):
+    """Error of the GPU result vs the oracle: O(N) C oracle on `modes`, refined dense
+    reference on `refined_modes` (both sets of mode indices)."""
+    from oracle import on
+    from oracle import solve as so
+    N = w["N"]
+    c = so.c_of(w["nu"], w["dt"])
+    z2 = so.mode_z2(w["Nx"], w["Nz"])
+    out = {}
+    for problem, F, U in (("helmholtz", F_h, U_h), ("biharmonic", F_b, U_b)):
+        n = so.n_unknowns(problem, N)
+        R = on.solve_modes(problem, N, z2[modes], c, F)
+        errs = [so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))]
+        pos = {m: i for i, m in enumerate(modes)}
+        ref_errs = []
+        for m in refined_modes:
+            r = so.solve_mode_ref(problem, N, float(z2[m]), c, F[pos[m]])
+            ref_errs.append(so.rel_l2(U[pos[m], :n], r))
+        out[problem] = {"vs_on_max": float(max(errs)), "vs_on_median": float(np.median(errs)),
+                        "n_modes_checked": len(modes),
+                        "vs_refined_max": float(max(ref_errs)) if ref_errs else None,
+                        "n_refined": len(ref_errs)}
+    return out
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    base = cpu_baseline(w, "reference", seconds_target=max(2.0, 2.0 * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": base["unit"],
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 2 * n_modes_of(w) * w["N"] / base["value"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **w, "n_modes": n_modes_of(w)},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": base["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    from paper_1701_03787_gb300 import Plan, inputs
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    N = w["N"]
+    stream = torch.cuda.Stream()
+    t_plan = time.perf_counter()
+    plan = Plan(N, w["Nx"], w["Nz"], w["nu"], w["dt"], stream=stream)
+    t_plan = time.perf_counter() - t_plan
+    nm = plan.n_modes
+    with torch.cuda.stream(stream):
+        f_h = inputs.rhs_torch(nm, N, seed=100 + rank)
+        f_b = inputs.rhs_torch(nm, N, seed=200 + rank)
+        u_h = torch.empty_like(f_h)
+        u_b = torch.empty_like(f_b)
+    stream.synchronize()
+
+    def step():
+        plan.helmholtz_solve(f_h, u_h, precision=args.precision, stream=stream)
+        plan.biharmonic_solve(f_b, u_b, precision=args.precision, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    # per-kernel durations (events on the launching stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        plan.helmholtz_solve(f_h, u_h, precision=args.precision, stream=stream)
+        ev[s][1].record(stream)
+        plan.biharmonic_solve(f_b, u_b, precision=args.precision, stream=stream)
+        ev[s][2].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t_h = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    t_b = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    rows = nm * N
+    value = world * 2 * rows / (ms * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hf_h = f_h.cpu().pin_memory()
+        hf_b = f_b.cpu().pin_memory()
+        hu = torch.empty_like(hf_h).pin_memory()
+        hu2 = torch.empty_like(hf_h).pin_memory()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                f_h.copy_(hf_h, non_blocking=True)
+                f_b.copy_(hf_b, non_blocking=True)
+                plan.helmholtz_solve(f_h, u_h, precision=args.precision, stream=stream)
+                plan.biharmonic_solve(f_b, u_b, precision=args.precision, stream=stream)
+                hu.copy_(u_h, non_blocking=True)
+                hu2.copy_(u_b, non_blocking=True)
+        e2e_step()
+        stream.synchronize()
+        k = max(1, min(args.steps, 3))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            e2e_step()
+        b.record(stream)
+        stream.synchronize()
+        e2e_ms = a.elapsed_time(b) / k
+        e2e = {"value": world * 2 * rows / (e2e_ms * 1e-3), "unit": "solves*N/s",
+               "h2d_bytes_per_step": int(2 * rows * 16), "d2h_bytes_per_step": int(2 * rows * 16),
+               "ms_per_step": e2e_ms}
+
+    peak, peak_kind = peaks()
+    dom = "biharmonic" if t_b >= t_h else "helmholtz"
+    t_dom = max(t_b, t_h)
+    achieved = rows * BYTES_PER_ROW / (t_dom * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"solve_{dom}_{args.precision}", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": peak_kind, "bytes_per_row": BYTES_PER_ROW}
+    line = {"metric": METRIC, "value": value, "unit": "solves*N/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+refine",
+            "data": "synthetic", "precision": args.precision,
+            "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+            "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "plan_s": t_plan,
+            "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e}
+    if rank == 0 and not args.no_check:
+        z2 = plan.n_modes
+        special = list(inputs.grid_modes(w["Nx"], w["Nz"]).values())
+        modes = inputs.sample_modes(nm, 0.01, 3, must_include=special)
+        refined = inputs.sample_modes(nm, 8.0 / nm, 4, must_include=special)
+        idx = torch.as_tensor(modes, device="cuda")
+        F_h, U_h = f_h[idx].cpu().numpy(), u_h[idx].cpu().numpy()
+        F_b, U_b = f_b[idx].cpu().numpy(), u_b[idx].cpu().numpy()
+        line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, args.precision)
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,147 @@
+/*
+ * shensolve -- batched Shen-Galerkin wall-normal solves on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Every pointer argument is a plain pointer; every size is in elements.
+ * Nothing here depends on PyTorch or any other framework.
+ *
+ * The operations (Mortensen, "A spectral-Galerkin turbulent channel flow solver for
+ * large-scale simulations", arXiv:1701.03787):
+ *
+ *   For every Fourier mode (kx, kz) of a wall-normal resolution of N Chebyshev modes
+ *   (N = N_x + 1 in the paper's notation), with z2 = (2 pi kx / Lx)^2 + (2 pi kz / Lz)^2
+ *   and c = 2 / (nu dt):
+ *
+ *   Helmholtz  (Sec. 3, Eqs. gfin, Helmholtz_matrix):  (alpha B - A) u = f,
+ *       alpha = z2 + c, Shen Dirichlet basis phi_k = T_k - T_{k+2} (Sec. 2, Eq. phiD),
+ *       B = (phi_j, phi_k), A = (phi_j'', phi_k); N - 2 unknowns.  This is the paper's
+ *       Hbar scaled by 2 / (nu dt).
+ *   Biharmonic (Sec. 3, Eqs. ufin, Biharmonic_matrix):  (Q + a A + b B) u = f,
+ *       a = -(2 z2 + c), b = z2 (z2 + c), Shen biharmonic basis (Sec. 2, Eq. phiN),
+ *       Q = (psi_j'''', psi_k) (Eqs. N_Q, pk, rk); N - 4 unknowns.  This is the paper's
+ *       Hchk scaled by -2 / (nu dt).
+ *   Right-hand-side operators (Eqs. gfin, ufin, scaled by 2 / (nu dt)):
+ *       Helmholtz  R_h = (c - z2) B + A            (= 2 Bbar - Hbar)
+ *       biharmonic R_b = Q + (c - 2 z2) A + z2 (z2 - c) B   (= 2 Achk - 2 z2 Bchk - Hchk)
+ *   Scalar products are Chebyshev-Gauss (Sec. 2); stiffness matrices carry the sign
+ *   A = +(phi'', phi) under which Eqs. ufin / gfin discretise the PDEs.
+ *
+ *   The solves use the paper's O(N) direct algorithms (Sec. 4): odd/even decoupling,
+ *   LU without pivoting, U rows with three stored values plus the constant tail
+ *   (Helmholtz) or the a_k q_j + b_k s_j tail of Eq. ab (biharmonic; Algorithms
+ *   LUbiharmonic, ReduceAB, LUSolveBiharmonic).  Factorisation happens once, in
+ *   shen_plan_create (the paper's "compute LU decompositions" before the time loop).
+ *
+ * Data layout ("mode-major"): a field is n_modes columns of N complex values, each
+ * complex value two doubles (re, im) interleaved; element (m, k) is at
+ * [2 * (m * N + k)].  Mode index m = ix * Nz + iz, ix = 0 .. Nx/2 (kx = ix),
+ * iz = 0 .. Nz-1 (kz = iz for iz < Nz/2, else iz - Nz).  Input entries k >= N-2
+ * (Helmholtz) or k >= N-4 (biharmonic) are ignored; the same output entries are
+ * written as 0.  Field pointers are DEVICE pointers unless a function says HOST,
+ * must be 16-byte aligned, and stay owned by the caller.  u == f (in place) is
+ * allowed; any other overlap between input and output is an error.
+ *
+ * Asynchrony: calls enqueue work on `stream` (a cudaStream_t passed as void*;
+ * NULL = the legacy default stream) and return once it is enqueued.  The status
+ * reports argument and launch errors; device-side conditions (a zero pivot) are
+ * recorded in the plan and returned by shen_plan_check after the stream is synced.
+ *
+ * Errors: no function throws; a failed call leaves the plan valid.
+ */
+#ifndef SHENSOLVE_H
+#define SHENSOLVE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct shen_plan_s *shen_plan_t;
+
+typedef enum {
+    SHEN_OK = 0,
+    SHEN_ERR_ARG = 1,          /* invalid argument (size, pointer, alignment, overlap) */
+    SHEN_ERR_ALLOC = 2,        /* device or host allocation failed */
+    SHEN_ERR_CUDA = 3,         /* a CUDA call or kernel launch failed */
+    SHEN_ERR_SINGULAR = 4,     /* a zero or non-finite pivot was met in a factorisation */
+    SHEN_ERR_UNSUPPORTED = 5   /* valid request the library does not implement */
+} shen_status;
+
+typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
+
+/* Arithmetic of a solve.  All variants read and write float64 (complex128) fields and
+ * use the same float64 LU factors (built once per plan); they differ in how the
+ * sweeps run:
+ *   SHEN_FP64       forward elimination and back substitution in float64 (the
+ *                   paper's algorithm as printed).
+ *   SHEN_FP32_R1 /  sweeps in float32 with the factors rounded to float32, then
+ *   SHEN_FP32_R2    1 / 2 steps of iterative refinement whose residual r = f - H u
+ *                   and correction u += d are computed in float64.
+ *   SHEN_DF_R1 /    as SHEN_FP32_R*, but the residual and the correction use
+ *   SHEN_DF_R2      float-float arithmetic (pairs of float32, error-free
+ *                   transformations of Dekker and Knuth) instead of float64.
+ * Plan creation fails with SHEN_ERR_UNSUPPORTED for variants not built in. */
+typedef enum {
+    SHEN_FP64 = 0,
+    SHEN_FP32_R1 = 1,
+    SHEN_FP32_R2 = 2,
+    SHEN_DF_R1 = 3,
+    SHEN_DF_R2 = 4
+} shen_precision;
+
+/* Create a plan for one channel: N Chebyshev modes (8 <= N <= 4096), Fourier grid
+ * Nx x Nz (even, >= 2), viscosity nu > 0, time step dt > 0, box lengths Lx, Lz > 0
+ * (the paper's Re_tau = 2000 box is Lx = 2 pi, Lz = pi).  Builds the per-N tables,
+ * groups modes by z2 (modes with equal z2 share one factorisation) and computes the
+ * float64 LU factors of both systems for every distinct z2 on the device, on
+ * `stream`.  Blocks until the plan is ready.  flags: must be 0.
+ * Errors: SHEN_ERR_ARG on bad sizes/parameters; SHEN_ERR_ALLOC; SHEN_ERR_CUDA;
+ * SHEN_ERR_SINGULAR if a pivot is zero or not finite. */
+shen_status shen_plan_create(shen_plan_t *plan, int N, int Nx, int Nz, double nu, double dt,
+                             double Lx, double Lz, unsigned flags, void *stream);
+
+/* Same, for an explicit list of n_modes squared wavenumbers z2[] (HOST array,
+ * z2 >= 0, finite), in the order the fields store their columns. */
+shen_status shen_plan_create_z2(shen_plan_t *plan, int N, long n_modes, const double *z2_host,
+                                double nu, double dt, unsigned flags, void *stream);
+
+/* Helmholtz solve (alpha B - A) u = f for every mode of the plan. f, u: DEVICE
+ * fields of n_modes * N complex values. */
+shen_status shen_helmholtz_solve(shen_plan_t plan, const double *f, double *u, int precision,
+                                 void *stream);
+
+/* Biharmonic solve (Q + a A + b B) u = f for every mode of the plan. */
+shen_status shen_biharmonic_solve(shen_plan_t plan, const double *f, double *u, int precision,
+                                  void *stream);
+
+/* Solve modes [mode_begin, mode_begin + mode_count) only: f and u point at the
+ * column of mode_begin (a shard of a larger field).  problem: shen_problem. */
+shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, long mode_count,
+                             const double *f, double *u, int precision, void *stream);
+
+/* Right-hand-side operator: out = R x + beta * y for every mode (R = R_h or R_b by
+ * `problem`).  y may be NULL (then beta is ignored).  x, y, out: DEVICE fields;
+ * out must not overlap x or y.  float64 arithmetic. */
+shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y,
+                            double beta, double *out, void *stream);
+
+/* Plan facts: number of modes, number of distinct z2 (factorisations), device bytes
+ * held by the plan.  Any output pointer may be NULL. */
+shen_status shen_plan_info(shen_plan_t plan, long *n_modes, long *n_classes, long *N,
+                           long long *device_bytes);
+
+/* Device-side error state of the plan after the stream is synchronised: SHEN_OK, or
+ * SHEN_ERR_SINGULAR (with the first offending class index in *where if non-NULL). */
+shen_status shen_plan_check(shen_plan_t plan, long *where);
+
+/* Free the plan (after any work using it has completed).  NULL is ignored. */
+void shen_plan_destroy(shen_plan_t plan);
+
+/* Static description of a status code. */
+const char *shen_status_string(int status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int shen_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHENSOLVE_H */

@@ -1,0 +1,206 @@
+"""Thin Python binding of libshensolve (ctypes; argument marshalling only).
+
+Every operation runs in the library's CUDA kernels; this module only converts
+arguments (tensor data pointers, stream handles, enums) and raises on a non-OK
+status.  It never computes anything itself and has no fallback: if the library
+is missing, importing it raises.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libshensolve.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "shensolve.h")
+
+SHEN_OK, SHEN_ERR_ARG, SHEN_ERR_ALLOC, SHEN_ERR_CUDA, SHEN_ERR_SINGULAR, SHEN_ERR_UNSUPPORTED = range(6)
+SHEN_HELMHOLTZ, SHEN_BIHARMONIC = 0, 1
+PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4}
+PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
+
+_lib = None
+
+
+class ShenError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+def lib():
+    """Load libshensolve.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libshensolve.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, Lg = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+    sig = {
+        "shen_plan_create": ([P, I, I, I, D, D, D, D, ctypes.c_uint, P], I),
+        "shen_plan_create_z2": ([P, I, Lg, P, D, D, ctypes.c_uint, P], I),
+        "shen_helmholtz_solve": ([P, P, P, I, P], I),
+        "shen_biharmonic_solve": ([P, P, P, I, P], I),
+        "shen_solve_modes": ([P, I, Lg, Lg, P, P, I, P], I),
+        "shen_rhs_matvec": ([P, I, P, P, D, P, P], I),
+        "shen_plan_info": ([P, P, P, P, P], I),
+        "shen_plan_check": ([P, P], I),
+        "shen_plan_destroy": ([P], None),
+        "shen_status_string": ([I], ctypes.c_char_p),
+        "shen_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Names of the functions declared in include/shensolve.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(shen_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(status):
+    return lib().shen_status_string(int(status)).decode()
+
+
+def check(status, what):
+    if status != SHEN_OK:
+        raise ShenError(status, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _prec(precision):
+    if isinstance(precision, str):
+        return PRECISIONS[precision]
+    return int(precision)
+
+
+def _problem(problem):
+    if isinstance(problem, str):
+        return PROBLEMS[problem]
+    return int(problem)
+
+
+def _field_ok(t, n_modes, N, name):
+    import torch
+    if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+    if t.numel() != n_modes * N:
+        raise ValueError(f"{name} has {t.numel()} entries, expected n_modes*N = {n_modes * N}")
+
+
+class Plan:
+    """One channel's plan (C type shen_plan_t).  Fields are complex128 CUDA tensors of
+    shape (n_modes, N) in mode-major order."""
+
+    def __init__(self, N, Nx=None, Nz=None, nu=None, dt=None, Lx=None, Lz=None, z2=None, stream=None):
+        import math
+        self._h = ctypes.c_void_p()
+        if z2 is not None:
+            import numpy as np
+            z = np.ascontiguousarray(np.asarray(z2, dtype=np.float64))
+            st = lib().shen_plan_create_z2(ctypes.byref(self._h), int(N), int(z.size),
+                                           z.ctypes.data_as(ctypes.c_void_p), float(nu), float(dt), 0,
+                                           _stream(stream))
+        else:
+            Lx = 2 * math.pi if Lx is None else Lx
+            Lz = math.pi if Lz is None else Lz
+            st = lib().shen_plan_create(ctypes.byref(self._h), int(N), int(Nx), int(Nz), float(nu), float(dt),
+                                        float(Lx), float(Lz), 0, _stream(stream))
+        check(st, "shen_plan_create")
+        n_modes, n_classes, n = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        nbytes = ctypes.c_longlong()
+        check(lib().shen_plan_info(self._h, ctypes.byref(n_modes), ctypes.byref(n_classes), ctypes.byref(n),
+                                   ctypes.byref(nbytes)), "shen_plan_info")
+        self.N, self.n_modes, self.n_classes, self.device_bytes = n.value, n_modes.value, n_classes.value, nbytes.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().shen_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _solve(self, fn, name, f, u, precision, stream):
+        import torch
+        _field_ok(f, self.n_modes, self.N, "f")
+        if u is None:
+            u = torch.empty_like(f)
+        _field_ok(u, self.n_modes, self.N, "u")
+        check(fn(self._h, _ptr(f), _ptr(u), _prec(precision), _stream(stream)), name)
+        return u
+
+    def helmholtz_solve(self, f, u=None, precision="fp64", stream=None):
+        return self._solve(lib().shen_helmholtz_solve, "shen_helmholtz_solve", f, u, precision, stream)
+
+    def biharmonic_solve(self, f, u=None, precision="fp64", stream=None):
+        return self._solve(lib().shen_biharmonic_solve, "shen_biharmonic_solve", f, u, precision, stream)
+
+    def solve(self, problem, f, u=None, precision="fp64", stream=None):
+        if _problem(problem) == SHEN_HELMHOLTZ:
+            return self.helmholtz_solve(f, u, precision, stream)
+        return self.biharmonic_solve(f, u, precision, stream)
+
+    def solve_modes(self, problem, mode_begin, f, u=None, precision="fp64", stream=None):
+        """Solve the modes [mode_begin, mode_begin + f.shape[0]) (a shard)."""
+        import torch
+        count = f.numel() // self.N
+        _field_ok(f, count, self.N, "f")
+        if u is None:
+            u = torch.empty_like(f)
+        _field_ok(u, count, self.N, "u")
+        check(lib().shen_solve_modes(self._h, _problem(problem), int(mode_begin), int(count), _ptr(f), _ptr(u),
+                                     _prec(precision), _stream(stream)), "shen_solve_modes")
+        return u
+
+    def rhs_matvec(self, problem, x, y=None, beta=0.0, out=None, stream=None):
+        import torch
+        _field_ok(x, self.n_modes, self.N, "x")
+        if y is not None:
+            _field_ok(y, self.n_modes, self.N, "y")
+        if out is None:
+            out = torch.empty_like(x)
+        _field_ok(out, self.n_modes, self.N, "out")
+        check(lib().shen_rhs_matvec(self._h, _problem(problem), _ptr(x), _ptr(y), float(beta), _ptr(out),
+                                    _stream(stream)), "shen_rhs_matvec")
+        return out
+
+    def check_device(self):
+        where = ctypes.c_long()
+        check(lib().shen_plan_check(self._h, ctypes.byref(where)), "shen_plan_check")

@@ -1,0 +1,305 @@
+// Plan construction and the C ABI of libshensolve.
+//
+// A plan holds, for one channel (N, Fourier grid, nu, dt): the per-N row tables of
+// the Galerkin matrices (Table tab:matrices, Eqs. N_Q, pk, rk of arXiv:1701.03787),
+// the grouping of modes by z2 (modes with equal z2 have equal systems), and the
+// float64 LU factors of the Helmholtz and biharmonic systems of every distinct z2,
+// computed once on the device (Alg. NS: LU decompositions before the time loop).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "shen_internal.h"
+
+using namespace shen;
+
+namespace {
+
+#define SHEN_CUDA_TRY(expr)                                \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) {                           \
+            (void)cudaGetLastError();                      \
+            return e_ == cudaErrorMemoryAllocation ? SHEN_ERR_ALLOC : SHEN_ERR_CUDA; \
+        }                                                  \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Row tables of the Galerkin matrices for N Chebyshev modes (Chebyshev-Gauss scalar
+// product, so c_0 = 2 and c_k = 1 for k > 0 including k = N - 1).
+void build_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride) {
+    const double pi = kPi;
+    stride = N;
+    h.assign((size_t)16 * N, 0.0);
+    h32.assign((size_t)2 * N, 0.0f);
+    double *bd0 = &h[0 * N], *ad0 = &h[1 * N], *adt = &h[2 * N];
+    double *bb0 = &h[3 * N], *bb2 = &h[4 * N], *bb4 = &h[5 * N];
+    double *ab0 = &h[6 * N], *abp = &h[7 * N], *abm = &h[8 * N], *qb0 = &h[9 * N];
+    double *pk = &h[10 * N], *rk = &h[11 * N], *qk = &h[12 * N], *sk = &h[13 * N];
+    for (int k = 0; k < N; k++) {
+        const double K = k, ck = (k == 0) ? 2.0 : 1.0;
+        // Dirichlet phi_k = T_k - T_{k+2}: B_kk = pi/2 (c_k + c_{k+2}); A = (phi_j'', phi_k)
+        bd0[k] = pi / 2 * (ck + 1.0);
+        ad0[k] = -2 * pi * (K + 1) * (K + 2);
+        adt[k] = -4 * pi * (K + 1);
+        // biharmonic psi_k: B (Table tab:matrices), A = (psi_j'', psi_k), Q (Eqs. N_Q, pk, rk)
+        const double r2 = (K + 2) / (K + 3), r1 = (K + 1) / (K + 3);
+        bb0[k] = pi / 2 * (ck + 4 * r2 * r2 + r1 * r1);
+        bb2[k] = -pi * (r2 + (K + 4) * (K + 1) / ((K + 5) * (K + 3)));
+        bb4[k] = pi / 2 * r1;
+        ab0[k] = -4 * pi * (K + 1) * (K + 2) * (K + 2) / (K + 3);
+        abp[k] = 2 * pi * (K + 1) * (K + 2);
+        abm[k] = 2 * pi * (K - 1) * (K + 2);
+        qb0[k] = 8 * pi * (K + 1) * (K + 1) * (K + 2) * (K + 4);
+        pk[k] = 8 * pi * K * (K + 1) * (K + 2) * (K + 4);
+        rk[k] = 24 * pi * (K + 1) * (K + 2);
+        qk[k] = 1.0 / (K + 3);
+        sk[k] = (K + 2) * (K + 2) / (K + 3);
+        h32[k] = (float)qk[k];
+        h32[N + k] = (float)sk[k];
+    }
+}
+
+void free_plan(Plan &p) {
+    cudaFree(p.d_class_z2);
+    cudaFree(p.d_mode_class);
+    cudaFree(p.d_order);
+    cudaFree(p.d_tab);
+    cudaFree(p.d_tab32);
+    cudaFree(p.d_fac_h);
+    cudaFree(p.d_fac_b);
+    cudaFree(p.d_fac_h32);
+    cudaFree(p.d_fac_b32);
+    cudaFree(p.d_err);
+    p = Plan{};
+}
+
+template <class T>
+cudaError_t dalloc(T **ptr, size_t count, long long &bytes) {
+    bytes += (long long)(count * sizeof(T));
+    return cudaMalloc((void **)ptr, count * sizeof(T));
+}
+
+shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *z2, double nu, double dt,
+                           unsigned flags, void *stream) {
+    if (!out) return SHEN_ERR_ARG;
+    *out = nullptr;
+    if (flags != 0 || N < 8 || N > 4096 || n_modes < 1 || n_modes > (1L << 30) || !z2) return SHEN_ERR_ARG;
+    if (!(nu > 0) || !(dt > 0) || !std::isfinite(nu) || !std::isfinite(dt)) return SHEN_ERR_ARG;
+    const double c = 2.0 / (nu * dt);
+    if (!std::isfinite(c)) return SHEN_ERR_ARG;
+    for (long m = 0; m < n_modes; m++)
+        if (!(z2[m] >= 0) || !std::isfinite(z2[m])) return SHEN_ERR_ARG;
+
+    // group modes by z2
+    std::vector<std::pair<double, int>> srt((size_t)n_modes);
+    for (long m = 0; m < n_modes; m++) srt[m] = {z2[m], (int)m};
+    std::sort(srt.begin(), srt.end());
+    std::vector<int> order((size_t)n_modes), mode_class((size_t)n_modes);
+    std::vector<double> class_z2;
+    for (long w = 0; w < n_modes; w++) {
+        if (w == 0 || srt[w].first != srt[w - 1].first) class_z2.push_back(srt[w].first);
+        order[w] = srt[w].second;
+        mode_class[srt[w].second] = (int)class_z2.size() - 1;
+    }
+
+    shen_plan_s *plan = new (std::nothrow) shen_plan_s;
+    if (!plan) return SHEN_ERR_ALLOC;
+    Plan &p = plan->p;
+    p.N = N;
+    p.n_modes = n_modes;
+    p.n_classes = (long)class_z2.size();
+    p.nu = nu;
+    p.dt = dt;
+    p.c = c;
+    p.rows_h = (N - 2 + 1) / 2;
+    p.rows_b = (N - 4 + 1) / 2;
+
+    std::vector<double> tab;
+    std::vector<float> tab32;
+    int stride = 0;
+    build_tables(N, tab, tab32, stride);
+
+    cudaStream_t s = as_stream(stream);
+    auto fail = [&](shen_status st) {
+        free_plan(p);
+        delete plan;
+        return st;
+    };
+#define PLAN_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            (void)cudaGetLastError();                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? SHEN_ERR_ALLOC : SHEN_ERR_CUDA); \
+        }                                                                                \
+    } while (0)
+    long long &B = p.device_bytes;
+    PLAN_TRY(dalloc(&p.d_class_z2, (size_t)p.n_classes, B));
+    PLAN_TRY(dalloc(&p.d_mode_class, (size_t)n_modes, B));
+    PLAN_TRY(dalloc(&p.d_order, (size_t)n_modes, B));
+    PLAN_TRY(dalloc(&p.d_tab, tab.size(), B));
+    PLAN_TRY(dalloc(&p.d_tab32, tab32.size(), B));
+    PLAN_TRY(dalloc(&p.d_fac_h, (size_t)p.n_classes * 2 * p.rows_h * kHelmF64, B));
+    PLAN_TRY(dalloc(&p.d_fac_b, (size_t)p.n_classes * 2 * p.rows_b * kBiF64, B));
+    PLAN_TRY(dalloc(&p.d_err, 2, B));
+
+    PLAN_TRY(cudaMemcpyAsync(p.d_class_z2, class_z2.data(), class_z2.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    PLAN_TRY(cudaMemcpyAsync(p.d_mode_class, mode_class.data(), mode_class.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, s));
+    PLAN_TRY(cudaMemcpyAsync(p.d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    PLAN_TRY(cudaMemcpyAsync(p.d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PLAN_TRY(cudaMemcpyAsync(p.d_tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    const int err_init[2] = {0, 0x7fffffff};
+    PLAN_TRY(cudaMemcpyAsync(p.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, s));
+    const double *t = p.d_tab;
+    p.tab.bd0 = t + 0 * stride; p.tab.ad0 = t + 1 * stride; p.tab.adt = t + 2 * stride;
+    p.tab.bb0 = t + 3 * stride; p.tab.bb2 = t + 4 * stride; p.tab.bb4 = t + 5 * stride;
+    p.tab.ab0 = t + 6 * stride; p.tab.abp = t + 7 * stride; p.tab.abm = t + 8 * stride;
+    p.tab.qb0 = t + 9 * stride; p.tab.pk = t + 10 * stride; p.tab.rk = t + 11 * stride;
+    p.tab.qk = t + 12 * stride; p.tab.sk = t + 13 * stride;
+    p.tab.qk32 = p.d_tab32; p.tab.sk32 = p.d_tab32 + stride;
+
+    PLAN_TRY(launch_factor_helmholtz(p, s));
+    PLAN_TRY(launch_factor_biharmonic(p, s));
+    int err_host[2];
+    PLAN_TRY(cudaMemcpyAsync(err_host, p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost, s));
+    PLAN_TRY(cudaStreamSynchronize(s));
+    if (err_host[0]) return fail(SHEN_ERR_SINGULAR);
+#undef PLAN_TRY
+    *out = plan;
+    return SHEN_OK;
+}
+
+bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+// Input and output ranges either coincide (in place) or are disjoint.
+bool overlap_ok(const double *a, const double *b, long n_doubles) {
+    if (!a || !b || a == b) return true;
+    const double *ae = a + n_doubles, *be = b + n_doubles;
+    return ae <= b || be <= a;
+}
+
+shen_status check_precision(int precision) {
+    if (precision == SHEN_FP64) return SHEN_OK;
+    if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
+    return SHEN_ERR_ARG;
+}
+
+shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, const double *f, double *u,
+                        int precision, void *stream) {
+    if (!plan || !f || !u) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (m0 < 0 || count < 0 || m0 + count > p.n_modes) return SHEN_ERR_ARG;
+    if (!aligned16(f) || !aligned16(u)) return SHEN_ERR_ARG;
+    if (!overlap_ok(f, u, 2 * count * (long)p.N)) return SHEN_ERR_ARG;
+    shen_status ps = check_precision(precision);
+    if (ps != SHEN_OK) return ps;
+    if (count == 0) return SHEN_OK;
+    SHEN_CUDA_TRY(launch_solve_fp64(p, problem, m0, count, f, u, as_stream(stream)));
+    return SHEN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+shen_status shen_plan_create(shen_plan_t *plan, int N, int Nx, int Nz, double nu, double dt, double Lx,
+                             double Lz, unsigned flags, void *stream) {
+    if (!plan) return SHEN_ERR_ARG;
+    *plan = nullptr;
+    if (Nx < 2 || Nz < 2 || (Nx & 1) || (Nz & 1)) return SHEN_ERR_ARG;
+    if (!(Lx > 0) || !(Lz > 0) || !std::isfinite(Lx) || !std::isfinite(Lz)) return SHEN_ERR_ARG;
+    const long nxh = Nx / 2 + 1;
+    const long n_modes = nxh * (long)Nz;
+    if (n_modes > (1L << 30)) return SHEN_ERR_ARG;
+    std::vector<double> z2((size_t)n_modes);
+    for (long ix = 0; ix < nxh; ix++) {
+        const double kx = 2 * kPi * (double)ix / Lx;
+        for (long iz = 0; iz < Nz; iz++) {
+            const long kzi = iz < Nz / 2 ? iz : iz - Nz;
+            const double kz = 2 * kPi * (double)kzi / Lz;
+            z2[ix * Nz + iz] = kx * kx + kz * kz;
+        }
+    }
+    return create_from_z2(plan, N, n_modes, z2.data(), nu, dt, flags, stream);
+}
+
+shen_status shen_plan_create_z2(shen_plan_t *plan, int N, long n_modes, const double *z2_host, double nu,
+                                double dt, unsigned flags, void *stream) {
+    return create_from_z2(plan, N, n_modes, z2_host, nu, dt, flags, stream);
+}
+
+shen_status shen_helmholtz_solve(shen_plan_t plan, const double *f, double *u, int precision, void *stream) {
+    if (!plan) return SHEN_ERR_ARG;
+    return solve_range(plan, SHEN_HELMHOLTZ, 0, plan->p.n_modes, f, u, precision, stream);
+}
+
+shen_status shen_biharmonic_solve(shen_plan_t plan, const double *f, double *u, int precision, void *stream) {
+    if (!plan) return SHEN_ERR_ARG;
+    return solve_range(plan, SHEN_BIHARMONIC, 0, plan->p.n_modes, f, u, precision, stream);
+}
+
+shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, long mode_count, const double *f,
+                             double *u, int precision, void *stream) {
+    return solve_range(plan, problem, mode_begin, mode_count, f, u, precision, stream);
+}
+
+shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
+                            double *out, void *stream) {
+    if (!plan || !x || !out) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
+    const long nd = 2 * p.n_modes * (long)p.N;
+    if (x == out || (y && y == out)) return SHEN_ERR_ARG;
+    if (!overlap_ok(x, out, nd) || !overlap_ok(y, out, nd)) return SHEN_ERR_ARG;
+    if (y && !std::isfinite(beta)) return SHEN_ERR_ARG;
+    SHEN_CUDA_TRY(launch_matvec_fp64(p, problem, x, y, beta, out, as_stream(stream)));
+    return SHEN_OK;
+}
+
+shen_status shen_plan_info(shen_plan_t plan, long *n_modes, long *n_classes, long *N, long long *device_bytes) {
+    if (!plan) return SHEN_ERR_ARG;
+    if (n_modes) *n_modes = plan->p.n_modes;
+    if (n_classes) *n_classes = plan->p.n_classes;
+    if (N) *N = plan->p.N;
+    if (device_bytes) *device_bytes = plan->p.device_bytes;
+    return SHEN_OK;
+}
+
+shen_status shen_plan_check(shen_plan_t plan, long *where) {
+    if (!plan) return SHEN_ERR_ARG;
+    int err_host[2];
+    SHEN_CUDA_TRY(cudaMemcpy(err_host, plan->p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost));
+    if (where) *where = err_host[0] ? err_host[1] : -1;
+    return err_host[0] ? SHEN_ERR_SINGULAR : SHEN_OK;
+}
+
+void shen_plan_destroy(shen_plan_t plan) {
+    if (!plan) return;
+    free_plan(plan->p);
+    delete plan;
+}
+
+const char *shen_status_string(int status) {
+    switch (status) {
+    case SHEN_OK: return "ok";
+    case SHEN_ERR_ARG: return "invalid argument";
+    case SHEN_ERR_ALLOC: return "allocation failed";
+    case SHEN_ERR_CUDA: return "CUDA error";
+    case SHEN_ERR_SINGULAR: return "zero or non-finite pivot";
+    case SHEN_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+int shen_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "../../include/shensolve.h"
+
+namespace shen {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Per-N row tables, indexed by the Chebyshev index k of the basis function
+// (Table tab:matrices, Eqs. N_Q, pk, rk; stiffness with the + sign).  Device copies.
+struct RowTables {
+    // Dirichlet space, k = 0 .. N-3
+    const double *bd0;   // B_kk = pi/2 (c_k + 1); B_{k,k+-2} = -pi/2
+    const double *ad0;   // A_kk = -2 pi (k+1)(k+2)
+    const double *adt;   // A_kj = -4 pi (k+1) for j = k+2, k+4, ...
+    // biharmonic space, k = 0 .. N-5 (B symmetric)
+    const double *bb0, *bb2, *bb4;   // B_kk, B_{k,k+2}, B_{k,k+4}
+    const double *ab0, *abp, *abm;   // A_kk, A_{k,k+2}, A_{k,k-2}
+    const double *qb0;               // Q_kk
+    const double *pk, *rk, *qk, *sk; // Q_kj = p_k q_j + r_k s_j (j = k+2, k+4, ...)
+    // float32 copies for the mixed-precision sweeps
+    const float *qk32, *sk32;
+};
+
+// Layout of the per-class LU factors (class = one distinct z2).  Chain (class, parity)
+// holds rows i = 0 .. rows-1 (Chebyshev index k = 2 i + parity).
+//   Helmholtz float64, 4 doubles per row: l_i, 1/U_ii, U_i,i+2 tail value (U2), 0
+//       (U_i,i+1 = U2_i - h with h = alpha pi / 2; l_i = L_{i,i-1})
+//   biharmonic float64, 8 doubles per row: L1 = L_{i,i-1}, L2 = L_{i,i-2}, 1/U_ii,
+//       U1 = U_{i,i+1}, U2 = U_{i,i+2}, ta, tb (tail U_ij = ta_i q_j + tb_i s_j,
+//       j >= i+3; Eq. ab), 0
+constexpr int kHelmF64 = 4;
+constexpr int kBiF64 = 8;
+
+struct Plan {
+    int N = 0;
+    long n_modes = 0, n_classes = 0;
+    double nu = 0, dt = 0, c = 0;
+    int rows_h = 0, rows_b = 0;           // max rows per parity chain
+    // device arrays
+    double *d_class_z2 = nullptr;         // [n_classes]
+    int *d_mode_class = nullptr;          // [n_modes]
+    int *d_order = nullptr;               // [n_modes] modes sorted by class
+    double *d_tab = nullptr;              // backing store of RowTables
+    float *d_tab32 = nullptr;
+    RowTables tab{};
+    double *d_fac_h = nullptr;            // Helmholtz factors
+    double *d_fac_b = nullptr;            // biharmonic factors
+    float *d_fac_h32 = nullptr, *d_fac_b32 = nullptr;
+    int *d_err = nullptr;                 // [2]: flag, first bad class
+    long long device_bytes = 0;
+};
+
+// kernels_fp64.cu
+cudaError_t launch_factor_helmholtz(const Plan &p, cudaStream_t s);
+cudaError_t launch_factor_biharmonic(const Plan &p, cudaStream_t s);
+cudaError_t launch_solve_fp64(const Plan &p, int problem, long m0, long count, const double *f,
+                              double *u, cudaStream_t s);
+cudaError_t launch_matvec_fp64(const Plan &p, int problem, const double *x, const double *y,
+                               double beta, double *out, cudaStream_t s);
+
+}  // namespace shen
+
+struct shen_plan_s {
+    shen::Plan p;
+};
