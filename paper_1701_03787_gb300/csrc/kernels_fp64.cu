@@ -60,9 +60,9 @@ __global__ void factor_helmholtz_kernel(Plan p) {
             U2 = t - l * U2;
         }
         if (bad_pivot(U0)) flag_error(p.d_err, cls);
-        F[i * kHelmF64 + 0] = l;
-        F[i * kHelmF64 + 1] = 1.0 / U0;
-        F[i * kHelmF64 + 2] = U2;
+        F[i * kHelmF64 + 0] = 1.0 / U0;
+        F[i * kHelmF64 + 1] = U2;
+        F[i * kHelmF64 + 2] = l;
         F[i * kHelmF64 + 3] = 0.0;
     }
     for (int i = rows; i < p.rows_h; i++)
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) solve_helmholtz_fp64_kernel(Plan p, const
     double2 y = make_double2(0.0, 0.0);
     for (int i = 0; i < rows; i++) {
         const long e = base + 2 * i + par;
-        const double l = F[i * kHelmF64];
+        const double l = F[i * kHelmF64 + 2];
         const double2 fi = ld2(f, e);
         y.x = fma(-l, y.x, fi.x);
         y.y = fma(-l, y.y, fi.y);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128) solve_helmholtz_fp64_kernel(Plan p, const
     double2 un = make_double2(0.0, 0.0), S = make_double2(0.0, 0.0);
     for (int i = rows - 1; i >= 0; i--) {
         const long e = base + 2 * i + par;
-        const double2 inv_u2 = *reinterpret_cast<const double2 *>(F + i * kHelmF64 + 1);
+        const double2 inv_u2 = *reinterpret_cast<const double2 *>(F + i * kHelmF64);   // 32-byte rows
         const double2 yi = ld2(u, e);
         double2 t;
         t.x = fma(-inv_u2.y, S.x, fma(h, un.x, yi.x));

@@ -167,6 +167,12 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
 
     PLAN_TRY(launch_factor_helmholtz(p, s));
     PLAN_TRY(launch_factor_biharmonic(p, s));
+    // float32 factors in the lane layout of the warp-per-mode kernels
+    p.R_h = helm_mixed_R(N);
+    if (p.R_h > 0) {
+        PLAN_TRY(dalloc(&p.d_fac_h32, (size_t)p.n_classes * 2 * p.R_h * 32 * 2, B));
+        PLAN_TRY(pack_helm_f32(p, p.R_h, reinterpret_cast<float2 *>(p.d_fac_h32), s));
+    }
     int err_host[2];
     PLAN_TRY(cudaMemcpyAsync(err_host, p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost, s));
     PLAN_TRY(cudaStreamSynchronize(s));
@@ -185,10 +191,12 @@ bool overlap_ok(const double *a, const double *b, long n_doubles) {
     return ae <= b || be <= a;
 }
 
-shen_status check_precision(int precision) {
+shen_status check_precision(const Plan &p, int problem, int precision) {
     if (precision == SHEN_FP64) return SHEN_OK;
-    if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
-    return SHEN_ERR_ARG;
+    if (precision < SHEN_FP32_R1 || precision > SHEN_DF_R2) return SHEN_ERR_ARG;
+    if (problem == SHEN_HELMHOLTZ && (precision == SHEN_FP32_R1 || precision == SHEN_DF_R1) && p.R_h > 0)
+        return SHEN_OK;
+    return SHEN_ERR_UNSUPPORTED;
 }
 
 shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, const double *f, double *u,
@@ -199,10 +207,14 @@ shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, cons
     if (m0 < 0 || count < 0 || m0 + count > p.n_modes) return SHEN_ERR_ARG;
     if (!aligned16(f) || !aligned16(u)) return SHEN_ERR_ARG;
     if (!overlap_ok(f, u, 2 * count * (long)p.N)) return SHEN_ERR_ARG;
-    shen_status ps = check_precision(precision);
+    shen_status ps = check_precision(p, problem, precision);
     if (ps != SHEN_OK) return ps;
     if (count == 0) return SHEN_OK;
-    SHEN_CUDA_TRY(launch_solve_fp64(p, problem, m0, count, f, u, as_stream(stream)));
+    if (precision == SHEN_FP64) {
+        SHEN_CUDA_TRY(launch_solve_fp64(p, problem, m0, count, f, u, as_stream(stream)));
+    } else {
+        SHEN_CUDA_TRY(launch_helm_mixed(p, precision == SHEN_DF_R1, m0, count, f, u, as_stream(stream)));
+    }
     return SHEN_OK;
 }
 

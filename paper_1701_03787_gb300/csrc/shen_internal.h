@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cuda_runtime.h>
 #include "../../include/shensolve.h"
 
 namespace shen {
@@ -26,7 +27,7 @@ struct RowTables {
 
 // Layout of the per-class LU factors (class = one distinct z2).  Chain (class, parity)
 // holds rows i = 0 .. rows-1 (Chebyshev index k = 2 i + parity).
-//   Helmholtz float64, 4 doubles per row: l_i, 1/U_ii, U_i,i+2 tail value (U2), 0
+//   Helmholtz float64, 4 doubles per row: 1/U_ii, U_i,i+2 tail value (U2), l_i, 0
 //       (U_i,i+1 = U2_i - h with h = alpha pi / 2; l_i = L_{i,i-1})
 //   biharmonic float64, 8 doubles per row: L1 = L_{i,i-1}, L2 = L_{i,i-2}, 1/U_ii,
 //       U1 = U_{i,i+1}, U2 = U_{i,i+2}, ta, tb (tail U_ij = ta_i q_j + tb_i s_j,
@@ -50,6 +51,7 @@ struct Plan {
     double *d_fac_b = nullptr;            // biharmonic factors
     float *d_fac_h32 = nullptr, *d_fac_b32 = nullptr;
     int *d_err = nullptr;                 // [2]: flag, first bad class
+    int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
     long long device_bytes = 0;
 };
 
@@ -60,6 +62,12 @@ cudaError_t launch_solve_fp64(const Plan &p, int problem, long m0, long count, c
                               double *u, cudaStream_t s);
 cudaError_t launch_matvec_fp64(const Plan &p, int problem, const double *x, const double *y,
                                double beta, double *out, cudaStream_t s);
+
+// kernels_helm_mixed.cu
+int helm_mixed_R(int N);                       // rows per lane for N (0: unsupported)
+cudaError_t pack_helm_f32(const Plan &p, int R, float2 *out, cudaStream_t s);
+cudaError_t launch_helm_mixed(const Plan &p, bool dfres, long m0, long count, const double *f, double *u,
+                              cudaStream_t s);
 
 }  // namespace shen
 

@@ -126,7 +126,11 @@ def test_rhs_matvec(problem):
 
 @pytest.mark.parametrize("problem", PROBLEMS)
 def test_explicit_z2_plan_and_extremes(problem):
-    """shen_plan_create_z2 with repeated, zero and very large z2 (3 modes share one class)."""
+    """shen_plan_create_z2 with repeated, zero and very large z2 (3 modes share one class).
+
+    The parameters are those of the Sec. 5 roundoff study (nu = 1/5200, dt = 1e-5, z up to
+    5400), where the unpivoted O(N) algorithm itself loses accuracy: its roundoff there is
+    of order 1e-11 (Table tab:roundoff), so this case is held to 2e-11."""
     N, nu, dt = 128, 1 / 5200, 1e-5
     c = so.c_of(nu, dt)
     z2 = np.array([0.0, 5400.0 ** 2, 1.0, 1800.0 ** 2, 1.0, 1.0, 200.0 ** 2])
@@ -134,7 +138,7 @@ def test_explicit_z2_plan_and_extremes(problem):
     with Plan(N, z2=z2, nu=nu, dt=dt) as plan:
         assert plan.n_classes == 5
         U = to_host(plan.solve(problem, to_dev(F)))
-    _check_columns(U, F, problem, N, z2, c, range(z2.size), FP64_TOL, ref="refined")
+    _check_columns(U, F, problem, N, z2, c, range(z2.size), 2e-11, ref="refined")
 
 
 def test_error_statuses():
@@ -147,8 +151,8 @@ def test_error_statuses():
             plan.helmholtz_solve(f, u, precision=99)
         assert e.value.status == 1
         big = torch.zeros(plan.n_modes * N + 1, dtype=torch.complex128, device="cuda")
-        with pytest.raises(ShenError) as e:                 # partial overlap
-            plan.helmholtz_solve(f, big[1:].view(plan.n_modes, N))
+        with pytest.raises(ShenError) as e:                 # input and output overlap partially
+            plan.helmholtz_solve(big[:-1].view(plan.n_modes, N), big[1:].view(plan.n_modes, N))
         assert e.value.status == 1
         raw = torch.zeros(2 * plan.n_modes * N + 1, dtype=torch.float64, device="cuda")
         from paper_1701_03787_gb300 import binding
