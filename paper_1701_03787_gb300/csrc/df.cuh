@@ -91,6 +91,17 @@ __device__ __forceinline__ F2 from_f64(double d) {
     return r;
 }
 
+// float64 -> float32 by truncation of the significand (the hi part of from_f64),
+// integer instructions only.  Same range rules as from_f64.
+__device__ __forceinline__ float hi_f64(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t hi32 = (uint32_t)(b >> 32), lo32 = (uint32_t)b;
+    const uint32_t sign = hi32 & 0x80000000u;
+    const uint32_t e = (hi32 >> 20) & 0x7FFu;
+    const uint32_t hb = (__funnelshift_l(lo32, hi32 - (896u << 20), 3) & 0x7FFFFFFFu) | sign;
+    return __uint_as_float(e - 897u <= 253u ? hb : (e > 1150u ? (sign | 0x7F800000u) : sign));
+}
+
 // float32 -> float64 bit pattern with integer instructions (exact for normal floats;
 // zero and subnormals give a signed zero).
 __device__ __forceinline__ double f32_to_f64_bits(float x) {

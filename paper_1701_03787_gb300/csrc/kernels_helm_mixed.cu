@@ -1,5 +1,6 @@
 // Helmholtz solve with float32 sweeps and one step of iterative refinement
-// (Sec. 4 algorithm; the refinement is this library's precision scheme).
+// (Sec. 4 algorithm of arXiv:1701.03787; the refinement is this library's precision
+// scheme):
 //
 //   u0 = H^-1 f     float32 forward elimination + back substitution with the float64
 //                   LU factors rounded to float32
@@ -7,17 +8,18 @@
 //   d  = H^-1 r     float32 sweeps again
 //   u  = u0 + d     float-float / float64, written as float64
 //
-// Work decomposition: one warp per mode.  Lane l owns Chebyshev indices
-// [2 R l, 2 R (l+1)) of the column, i.e. rows l R .. l R + R - 1 of both parity
-// chains (k = 2 i + parity), held in registers.  The sweeps are linear recurrences
-// along each chain; every lane runs its R rows with a zero carry, the warp combines
-// the lane maps with a shuffle scan (affine maps: scalar for the forward sweep, 2x2
+// Work decomposition: one warp per mode.  Lanes 0-15 take the even chain, lanes
+// 16-31 the odd chain (k = 2 i + parity); lane s of a half owns rows s R .. s R + R - 1
+// of its chain, held in registers.  The sweeps are linear recurrences along each
+// chain: every lane runs its R rows with a zero carry, the 16 lanes of a chain combine
+// their maps with a shuffle scan (scalar affine maps for the forward sweep, 2x2 maps
 // for the back substitution whose state is (u_i, sum_{j >= i} u_j)), and each lane
 // then adds the carried part.
 //
 // Helmholtz system per parity (k = 2i + p, alpha = z2 + c, h = alpha pi / 2):
-//   H_{i,i-1} = -h,  H_ii = pi (alpha delta_k + 2 (k+1)(k+2)),  H_{i,j>i} = pi 4 (k+1) - h [j = i+1]
-//   with delta_k = (c_k + 1) / 2.  LU: y_i = f_i + g_i y_{i-1} (g_i = h / U_{i-1,i-1}),
+//   H_{i,i-1} = -h,  H_ii = pi (alpha delta_k + 2 (k+1)(k+2)),
+//   H_{i,i+1} = -h + 4 pi (k+1),  H_{i,j>i+1} = 4 pi (k+1),  delta_k = (c_k + 1) / 2.
+//   LU: y_i = f_i + g_i y_{i-1} (g_i = h / U_{i-1,i-1}),
 //   u_i = (y_i + h u_{i+1} - U2_i S_{i+1}) / U_ii,  S_{i+1} = sum_{j > i} u_j.
 #include "df.cuh"
 #include "shen_internal.h"
@@ -27,385 +29,346 @@ namespace {
 
 constexpr float kPiHi = 3.14159274101257324f;           // float(pi)
 constexpr float kPiLo = -8.74227765734758577e-08f;      // pi - float(pi)
-
-template <int R>
-struct HelmCol {
-    float2 w[2][R];     // working column (re, im) per parity and row-in-lane
-};
+constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Forward elimination y_i = f_i + g_i y_{i-1} across the warp, in place in w.
-// gs (shared, [parity][j][lane]) holds g for row lane*R + j (0 for the chain's first
-// row and for padding rows).  Both parity chains advance in the same loop (ILP).
+// Forward elimination y_i = f_i + g_i y_{i-1}, in place in w.  gs: [j][lane] shared.
 template <int R>
-__device__ __forceinline__ void forward_sweep(float2 (&w)[2][R], const float *gs, int lane) {
-    float2 y[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
-    float G[2] = {1.f, 1.f};
+__device__ __forceinline__ void forward_sweep(float2 (&w)[R], const float *gs, int lane, int s) {
+    float2 y = f2(0.f, 0.f);
+    float G = 1.f;
 #pragma unroll
-    for (int j = 0; j < R; j++)
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const float g = gs[(p * R + j) * 32 + lane];
-            y[p].x = fmaf(g, y[p].x, w[p][j].x);
-            y[p].y = fmaf(g, y[p].y, w[p][j].y);
-            w[p][j] = y[p];
-            G[p] *= g;
-        }
-    // inclusive scan of the lane maps carry -> Y + G carry over lanes 0..31
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1)
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const float Gu = __shfl_up_sync(0xffffffffu, G[p], d);
-            const float Yx = __shfl_up_sync(0xffffffffu, y[p].x, d);
-            const float Yy = __shfl_up_sync(0xffffffffu, y[p].y, d);
-            if (lane >= d) {
-                y[p].x = fmaf(G[p], Yx, y[p].x);
-                y[p].y = fmaf(G[p], Yy, y[p].y);
-                G[p] *= Gu;
-            }
-        }
-    float2 c[2];
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        c[p].x = __shfl_up_sync(0xffffffffu, y[p].x, 1);
-        c[p].y = __shfl_up_sync(0xffffffffu, y[p].y, 1);
-        if (lane == 0) c[p] = f2(0.f, 0.f);
+    for (int j = 0; j < R; j++) {
+        const float g = gs[j * 32 + lane];
+        y.x = fmaf(g, y.x, w[j].x);
+        y.y = fmaf(g, y.y, w[j].y);
+        w[j] = y;
+        G *= g;
     }
-    float P[2] = {1.f, 1.f};
 #pragma unroll
-    for (int j = 0; j < R; j++)
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            P[p] *= gs[(p * R + j) * 32 + lane];
-            w[p][j].x = fmaf(P[p], c[p].x, w[p][j].x);
-            w[p][j].y = fmaf(P[p], c[p].y, w[p][j].y);
+    for (int d = 1; d < 16; d <<= 1) {
+        const float Gu = __shfl_up_sync(kFull, G, d, 16);
+        const float Yx = __shfl_up_sync(kFull, y.x, d, 16);
+        const float Yy = __shfl_up_sync(kFull, y.y, d, 16);
+        if (s >= d) {
+            y.x = fmaf(G, Yx, y.x);
+            y.y = fmaf(G, Yy, y.y);
+            G *= Gu;
         }
+    }
+    float cx = __shfl_up_sync(kFull, y.x, 1, 16), cy = __shfl_up_sync(kFull, y.y, 1, 16);
+    if (s == 0) cx = cy = 0.f;
+    float P = 1.f;
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+        P *= gs[j * 32 + lane];
+        w[j].x = fmaf(P, cx, w[j].x);
+        w[j].y = fmaf(P, cy, w[j].y);
+    }
 }
 
-// Back substitution across the warp, in place in w (y in, u out).
-// Per row: a = h inv0, c = U2 inv0;  u_i = a u_{i+1} - c S_{i+1} + inv0 y_i,  S_i = S_{i+1} + u_i.
-// m0 (shared, [parity][j][lane]) receives row 0 of the lane-local transfer matrices
-// (the response of u_i to the carried state) for the carried part.
-template <int R>
-__device__ __forceinline__ void backward_sweep(float2 (&w)[2][R], const float2 *fac, int lane, float h,
+// Back substitution, in place in w (y in, u out).  Per row a = h inv0, c = U2 inv0:
+//   u_i = a u_{i+1} - c S_{i+1} + inv0 y_i,  S_i = S_{i+1} + u_i.
+// With FIRST, m0 ([j][lane] shared) receives row 0 of the lane-local transfer matrices
+// (response of u_i to the carried state); otherwise the stored rows are reused.
+template <int R, bool FIRST>
+__device__ __forceinline__ void backward_sweep(float2 (&w)[R], const float2 *fac, int lane, int s, float h,
                                                float2 *m0) {
-    float2 u[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, S[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
-    float t00[2] = {1.f, 1.f}, t01[2] = {0.f, 0.f}, t10[2] = {0.f, 0.f}, t11[2] = {1.f, 1.f};
+    float2 u = f2(0.f, 0.f), S = f2(0.f, 0.f);
+    float t00 = 1.f, t01 = 0.f, t10 = 0.f, t11 = 1.f;
 #pragma unroll
-    for (int j = R - 1; j >= 0; j--)
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const float2 fu = fac[(p * R + j) * 32 + lane];   // (inv0, U2)
-            const float a = h * fu.x, c = fu.y * fu.x;
-            float2 un;
-            un.x = fmaf(a, u[p].x, fmaf(-c, S[p].x, fu.x * w[p][j].x));
-            un.y = fmaf(a, u[p].y, fmaf(-c, S[p].y, fu.x * w[p][j].y));
-            S[p].x += un.x;
-            S[p].y += un.y;
-            u[p] = un;
-            w[p][j] = un;
-            const float n00 = fmaf(a, t00[p], -c * t10[p]), n01 = fmaf(a, t01[p], -c * t11[p]);
-            t10[p] += n00;
-            t11[p] += n01;
-            t00[p] = n00;
-            t01[p] = n01;
-            m0[(p * R + j) * 32 + lane] = f2(n00, n01);
-        }
-    // suffix scan over lanes of the affine maps x -> T x + v, state v = (u, S)
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1)
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const float b00 = __shfl_down_sync(0xffffffffu, t00[p], d), b01 = __shfl_down_sync(0xffffffffu, t01[p], d);
-            const float b10 = __shfl_down_sync(0xffffffffu, t10[p], d), b11 = __shfl_down_sync(0xffffffffu, t11[p], d);
-            const float wux = __shfl_down_sync(0xffffffffu, u[p].x, d), wuy = __shfl_down_sync(0xffffffffu, u[p].y, d);
-            const float wSx = __shfl_down_sync(0xffffffffu, S[p].x, d), wSy = __shfl_down_sync(0xffffffffu, S[p].y, d);
-            if (lane + d < 32) {
-                u[p].x = fmaf(t00[p], wux, fmaf(t01[p], wSx, u[p].x));
-                u[p].y = fmaf(t00[p], wuy, fmaf(t01[p], wSy, u[p].y));
-                S[p].x = fmaf(t10[p], wux, fmaf(t11[p], wSx, S[p].x));
-                S[p].y = fmaf(t10[p], wuy, fmaf(t11[p], wSy, S[p].y));
-                const float n00 = fmaf(t00[p], b00, t01[p] * b10), n01 = fmaf(t00[p], b01, t01[p] * b11);
-                const float n10 = fmaf(t10[p], b00, t11[p] * b10), n11 = fmaf(t10[p], b01, t11[p] * b11);
-                t00[p] = n00; t01[p] = n01; t10[p] = n10; t11[p] = n11;
-            }
-        }
-    float2 cu[2], cS[2];
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        cu[p].x = __shfl_down_sync(0xffffffffu, u[p].x, 1);
-        cu[p].y = __shfl_down_sync(0xffffffffu, u[p].y, 1);
-        cS[p].x = __shfl_down_sync(0xffffffffu, S[p].x, 1);
-        cS[p].y = __shfl_down_sync(0xffffffffu, S[p].y, 1);
-        if (lane == 31) cu[p] = cS[p] = f2(0.f, 0.f);
+    for (int j = R - 1; j >= 0; j--) {
+        const float2 fu = fac[j * 16];                  // (inv0, U2) of row s R + j
+        const float a = h * fu.x, c = fu.y * fu.x;
+        float2 un;
+        un.x = fmaf(a, u.x, fmaf(-c, S.x, fu.x * w[j].x));
+        un.y = fmaf(a, u.y, fmaf(-c, S.y, fu.x * w[j].y));
+        S.x += un.x;
+        S.y += un.y;
+        u = un;
+        w[j] = un;
+        const float n00 = fmaf(a, t00, -c * t10), n01 = fmaf(a, t01, -c * t11);
+        t10 += n00;
+        t11 += n01;
+        t00 = n00;
+        t01 = n01;
+        if (FIRST) m0[j * 32 + lane] = f2(n00, n01);
     }
+    // suffix scan over the 16 lanes of the chain of the maps x -> T x + v, v = (u, S)
 #pragma unroll
-    for (int j = 0; j < R; j++)
-#pragma unroll
-        for (int p = 0; p < 2; p++) {
-            const float2 m = m0[(p * R + j) * 32 + lane];
-            w[p][j].x = fmaf(m.x, cu[p].x, fmaf(m.y, cS[p].x, w[p][j].x));
-            w[p][j].y = fmaf(m.x, cu[p].y, fmaf(m.y, cS[p].y, w[p][j].y));
+    for (int d = 1; d < 16; d <<= 1) {
+        const float b00 = __shfl_down_sync(kFull, t00, d, 16), b01 = __shfl_down_sync(kFull, t01, d, 16);
+        const float b10 = __shfl_down_sync(kFull, t10, d, 16), b11 = __shfl_down_sync(kFull, t11, d, 16);
+        const float wux = __shfl_down_sync(kFull, u.x, d, 16), wuy = __shfl_down_sync(kFull, u.y, d, 16);
+        const float wSx = __shfl_down_sync(kFull, S.x, d, 16), wSy = __shfl_down_sync(kFull, S.y, d, 16);
+        if (s + d < 16) {
+            u.x = fmaf(t00, wux, fmaf(t01, wSx, u.x));
+            u.y = fmaf(t00, wuy, fmaf(t01, wSy, u.y));
+            S.x = fmaf(t10, wux, fmaf(t11, wSx, S.x));
+            S.y = fmaf(t10, wuy, fmaf(t11, wSy, S.y));
+            const float n00 = fmaf(t00, b00, t01 * b10), n01 = fmaf(t00, b01, t01 * b11);
+            const float n10 = fmaf(t10, b00, t11 * b10), n11 = fmaf(t10, b01, t11 * b11);
+            t00 = n00; t01 = n01; t10 = n10; t11 = n11;
         }
+    }
+    float cux = __shfl_down_sync(kFull, u.x, 1, 16), cuy = __shfl_down_sync(kFull, u.y, 1, 16);
+    float cSx = __shfl_down_sync(kFull, S.x, 1, 16), cSy = __shfl_down_sync(kFull, S.y, 1, 16);
+    if (s == 15) cux = cuy = cSx = cSy = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+        const float2 m = m0[j * 32 + lane];
+        w[j].x = fmaf(m.x, cux, fmaf(m.y, cSx, w[j].x));
+        w[j].y = fmaf(m.x, cuy, fmaf(m.y, cSy, w[j].y));
+    }
 }
 
-}  // namespace
-}  // namespace shen
-
-namespace shen {
-namespace {
-
-// Residual r = f - H u0 for the lane's rows, written (rounded to float32) into w.
-// u0c: the lane's u0 values (exact float32 numbers).  Float-float (DF = true) or
-// float64 (DF = false) arithmetic.  H / pi row i (chain parity p, k = 2i + p):
+// Residual r = f - H u0 for the lane's rows, rounded to float32 into rs ([j][lane]
+// shared).  u0s ([j][lane] shared) holds u0 (exact float32 values).  H / pi, row i:
 //   E_i = alpha (delta_k u_i - (u_{i-1} + u_{i+1}) / 2) + 2(k+1)(k+2) u_i + 4(k+1) sum_{j>i} u_j
 //   r_i = f_i - pi E_i.
+// The row loop is kept rolled (its body is long) so the kernel stays small.
 template <int R, bool DF>
-__device__ __forceinline__ void residual(float2 (&w)[2][R], const float2 *u0s, const double *fcol,
-                                         int lane, int n, double alpha) {
-#define U0(pp, jj) u0s[((pp) * R + (jj)) * 32 + lane]
+__device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const double *fcol, int lane, int s,
+                                         int p, int n, double alpha) {
     const df::F2 a_df = df::from_f64(alpha);
     const df::F2 pi_df = {kPiHi, kPiLo};
-#pragma unroll
-    for (int p = 0; p < 2; p++) {
-        // lane totals of u0 (for the sum over rows above the lane), then a suffix scan
-        float tre = 0.f, tim = 0.f, ere = 0.f, eim = 0.f;
-        double dre = 0.0, dim = 0.0;
-#pragma unroll
-        for (int j = 0; j < R; j++) {
-            if (DF) {
-                const float2 uv = U0(p, j);
-                df::F2 s = df::two_sum(tre, uv.x); tre = s.hi; ere += s.lo;
-                s = df::two_sum(tim, uv.y); tim = s.hi; eim += s.lo;
-            } else {
-                const float2 uv = U0(p, j);
-                dre += (double)uv.x;
-                dim += (double)uv.y;
-            }
-        }
-        // inclusive suffix scan of the lane totals
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            if (DF) {
-                const float a0 = __shfl_down_sync(0xffffffffu, tre, d), a1 = __shfl_down_sync(0xffffffffu, ere, d);
-                const float b0 = __shfl_down_sync(0xffffffffu, tim, d), b1 = __shfl_down_sync(0xffffffffu, eim, d);
-                if (lane + d < 32) {
-                    df::F2 s = df::add(df::F2{tre, ere}, df::F2{a0, a1}); tre = s.hi; ere = s.lo;
-                    s = df::add(df::F2{tim, eim}, df::F2{b0, b1}); tim = s.hi; eim = s.lo;
-                }
-            } else {
-                const double a0 = __shfl_down_sync(0xffffffffu, dre, d), b0 = __shfl_down_sync(0xffffffffu, dim, d);
-                if (lane + d < 32) { dre += a0; dim += b0; }
-            }
-        }
-        // exclusive: sum over lanes above
-        df::F2 Tre, Tim;
-        double Dre, Dim;
-        {
-            float a0 = __shfl_down_sync(0xffffffffu, tre, 1), a1 = __shfl_down_sync(0xffffffffu, ere, 1);
-            float b0 = __shfl_down_sync(0xffffffffu, tim, 1), b1 = __shfl_down_sync(0xffffffffu, eim, 1);
-            double da = __shfl_down_sync(0xffffffffu, dre, 1), db = __shfl_down_sync(0xffffffffu, dim, 1);
-            if (lane == 31) { a0 = a1 = b0 = b1 = 0.f; da = db = 0.0; }
-            Tre = df::fast_two_sum(a0, a1);
-            Tim = df::fast_two_sum(b0, b1);
-            Dre = da; Dim = db;
-        }
-        // neighbours across lane boundaries
-        const float2 top = U0(p, R - 1), bot = U0(p, 0);
-        float2 below = make_float2(__shfl_up_sync(0xffffffffu, top.x, 1), __shfl_up_sync(0xffffffffu, top.y, 1));
-        float2 above = make_float2(__shfl_down_sync(0xffffffffu, bot.x, 1), __shfl_down_sync(0xffffffffu, bot.y, 1));
-        if (lane == 0) below = make_float2(0.f, 0.f);
-        if (lane == 31) above = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = R - 1; j >= 0; j--) {
-            const int i = lane * R + j;
-            const int k = 2 * i + p;
-            const float2 um = j > 0 ? U0(p, j - 1) : below;
-            const float2 uc = U0(p, j);
-            const float2 up = j < R - 1 ? U0(p, j + 1) : above;
-            if (k < n) {
-                const double2 fk = reinterpret_cast<const double2 *>(fcol)[k];
-                const float delta = k == 0 ? 1.5f : 1.0f;
-                const float e = 2.0f * (float)((k + 1) * (k + 2));
-                const float t = 4.0f * (float)(k + 1);
-                float2 r;
-                if (DF) {
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        const float vm = c ? um.y : um.x, vc = c ? uc.y : uc.x, vp = c ? up.y : up.x;
-                        const df::F2 T = c ? Tim : Tre;
-                        const double fv = c ? fk.y : fk.x;
-                        // b = delta u_i - (u_{i-1} + u_{i+1}) / 2
-                        const df::F2 s = df::two_sum(vm, vp);
-                        const df::F2 q = df::two_prod(delta, vc);
-                        df::F2 b = df::two_sum(q.hi, -0.5f * s.hi);
-                        b.lo = __fadd_rn(b.lo, __fsub_rn(q.lo, 0.5f * s.lo));
-                        df::F2 E = df::mul(a_df, b);                           // alpha b
-                        E = df::add(E, df::two_prod(e, vc));                   // + e u_i
-                        E = df::add(E, df::mul(T, t));                         // + t sum_{j>i} u_j
-                        const df::F2 piE = df::mul(pi_df, E);
-                        const df::F2 fd = df::from_f64(fv);
-                        const df::F2 d0 = df::two_sum(fd.hi, -piE.hi);
-                        const float rv = __fadd_rn(d0.hi, __fadd_rn(d0.lo, __fsub_rn(fd.lo, piE.lo)));
-                        if (c) r.y = rv; else r.x = rv;
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        const double vm = c ? um.y : um.x, vc = c ? uc.y : uc.x, vp = c ? up.y : up.x;
-                        const double T = c ? Dim : Dre;
-                        const double fv = c ? fk.y : fk.x;
-                        const double b = (double)delta * vc - 0.5 * (vm + vp);
-                        const double E = fma(alpha, b, fma((double)e, vc, (double)t * T));
-                        const float rv = (float)fma(-kPi, E, fv);
-                        if (c) r.y = rv; else r.x = rv;
-                    }
-                }
-                w[p][j] = r;
-            } else {
-                w[p][j] = make_float2(0.f, 0.f);
-            }
-            // sum over rows > i-1 for the next (lower) row
-            if (DF) {
-                Tre = df::add(Tre, uc.x);
-                Tim = df::add(Tim, uc.y);
-            } else {
-                Dre += (double)uc.x;
-                Dim += (double)uc.y;
-            }
+    // lane totals of u0, then the sum over the lanes above (rows with larger i)
+    float tre = 0.f, tim = 0.f, ere = 0.f, eim = 0.f;
+    double dre = 0.0, dim = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < R; j++) {
+        const float2 uv = u0s[j * 32 + lane];
+        if (DF) {
+            df::F2 q = df::two_sum(tre, uv.x); tre = q.hi; ere += q.lo;
+            q = df::two_sum(tim, uv.y); tim = q.hi; eim += q.lo;
+        } else {
+            dre += (double)uv.x;
+            dim += (double)uv.y;
         }
     }
-#undef U0
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        if (DF) {
+            const float a0 = __shfl_down_sync(kFull, tre, d, 16), a1 = __shfl_down_sync(kFull, ere, d, 16);
+            const float b0 = __shfl_down_sync(kFull, tim, d, 16), b1 = __shfl_down_sync(kFull, eim, d, 16);
+            if (s + d < 16) {
+                df::F2 q = df::add(df::F2{tre, ere}, df::F2{a0, a1}); tre = q.hi; ere = q.lo;
+                q = df::add(df::F2{tim, eim}, df::F2{b0, b1}); tim = q.hi; eim = q.lo;
+            }
+        } else {
+            const double a0 = __shfl_down_sync(kFull, dre, d, 16), b0 = __shfl_down_sync(kFull, dim, d, 16);
+            if (s + d < 16) { dre += a0; dim += b0; }
+        }
+    }
+    // running sums over rows above the current row: (hi, unnormalised error)
+    float Tre, Tim, Ere, Eim;
+    double Dre, Dim;
+    {
+        float a0 = __shfl_down_sync(kFull, tre, 1, 16), a1 = __shfl_down_sync(kFull, ere, 1, 16);
+        float b0 = __shfl_down_sync(kFull, tim, 1, 16), b1 = __shfl_down_sync(kFull, eim, 1, 16);
+        double da = __shfl_down_sync(kFull, dre, 1, 16), db = __shfl_down_sync(kFull, dim, 1, 16);
+        if (s == 15) { a0 = a1 = b0 = b1 = 0.f; da = db = 0.0; }
+        Tre = a0; Ere = a1; Tim = b0; Eim = b1;
+        Dre = da; Dim = db;
+    }
+    const float2 top = u0s[(R - 1) * 32 + lane], bot = u0s[lane];
+    float2 below = f2(__shfl_up_sync(kFull, top.x, 1, 16), __shfl_up_sync(kFull, top.y, 1, 16));
+    float2 above = f2(__shfl_down_sync(kFull, bot.x, 1, 16), __shfl_down_sync(kFull, bot.y, 1, 16));
+    if (s == 0) below = f2(0.f, 0.f);
+    if (s == 15) above = f2(0.f, 0.f);
+    float2 up = above;
+    float2 uc = top;
+    // per-class constants: pi alpha / 2 (float-float)
+    const df::F2 pih = df::mul(pi_df, df::F2{0.5f * a_df.hi, 0.5f * a_df.lo});
+    const int k_top = 2 * (s * R + R - 1) + p;
+    double2 fnext = k_top < n ? reinterpret_cast<const double2 *>(fcol)[k_top] : make_double2(0.0, 0.0);
+#pragma unroll 1
+    for (int j = R - 1; j >= 0; j--) {
+        const int k = 2 * (s * R + j) + p;
+        const double2 fk = fnext;
+        if (j > 0 && k - 2 < n) fnext = reinterpret_cast<const double2 *>(fcol)[k - 2];   // prefetch
+        const float2 um = j > 0 ? u0s[(j - 1) * 32 + lane] : below;
+        float2 r = f2(0.f, 0.f);
+        if (k < n) {
+            // row coefficients times pi (float-float): pi (alpha delta_k + 2(k+1)(k+2)), 4 pi (k+1)
+            const float delta = k == 0 ? 1.5f : 1.0f;
+            const float e = 2.0f * (float)((k + 1) * (k + 2));
+            const float t = 4.0f * (float)(k + 1);
+            float rv[2];
+            if (DF) {
+                const df::F2 D = df::mul(pi_df, df::add(df::mul(a_df, delta), df::two_prod(e, 1.0f)));
+                const df::F2 piT = df::two_prod(kPiHi, t);
+                const float piTlo = kPiLo * t;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const float vm = c ? um.y : um.x, vc = c ? uc.y : uc.x, vp = c ? up.y : up.x;
+                    const double fv = c ? fk.y : fk.x;
+                    const df::F2 T = df::fast_two_sum(c ? Tim : Tre, c ? Eim : Ere);
+                    const df::F2 nb = df::two_sum(vm, vp);                 // u_{i-1} + u_{i+1}
+                    const df::F2 p1 = df::mul(D, vc);                      // pi H_ii u_i
+                    const df::F2 p2 = df::mul(pih, nb);                    // pi alpha/2 (u_{i-1} + u_{i+1})
+                    df::F2 p3 = df::mul(T, piT.hi);                        // 4 pi (k+1) sum_{j>i} u_j
+                    p3.lo = __fmaf_rn(T.hi, __fadd_rn(piT.lo, piTlo), p3.lo);
+                    const df::F2 fd = df::from_f64(fv);
+                    const df::F2 s1 = df::two_sum(fd.hi, -p1.hi);
+                    const df::F2 s2 = df::two_sum(s1.hi, p2.hi);
+                    const df::F2 s3 = df::two_sum(s2.hi, -p3.hi);
+                    const float lo = __fadd_rn(__fadd_rn(__fsub_rn(fd.lo, p1.lo), __fsub_rn(p2.lo, p3.lo)),
+                                               __fadd_rn(__fadd_rn(s1.lo, s2.lo), s3.lo));
+                    rv[c] = __fadd_rn(s3.hi, lo);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const float vm = c ? um.y : um.x, vc = c ? uc.y : uc.x, vp = c ? up.y : up.x;
+                    const double fv = c ? fk.y : fk.x;
+                    const double T = c ? Dim : Dre;
+                    const double b = (double)delta * vc - 0.5 * ((double)vm + (double)vp);
+                    const double E = fma(alpha, b, fma((double)e, (double)vc, (double)t * T));
+                    rv[c] = (float)fma(-kPi, E, fv);
+                }
+            }
+            r = f2(rv[0], rv[1]);
+        }
+        rs[j * 32 + lane] = r;
+        if (DF) {
+            df::F2 q = df::two_sum(Tre, uc.x); Tre = q.hi; Ere = __fadd_rn(Ere, q.lo);
+            q = df::two_sum(Tim, uc.y); Tim = q.hi; Eim = __fadd_rn(Eim, q.lo);
+        } else {
+            Dre += (double)uc.x;
+            Dim += (double)uc.y;
+        }
+        up = uc;
+        uc = um;
+    }
 }
 
-// One warp per work item.  fac: float32 factors [class][parity][j][lane] = (inv0, U2).
+// One warp per work item.  fac: float32 factors [class][parity][j][segment] = (inv0, U2).
 template <int R, bool DF>
-__global__ void __launch_bounds__(128) helm_mixed_kernel(Plan p, const int *order, long m0, long count,
+__global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order, long m0, long count,
                                                          const double *f, double *u, const float2 *fac) {
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int par = lane >> 4, s = lane & 15;
     const long item = (long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (item >= count) return;                          // whole warp exits together
+    if (item >= count) return;                          // the whole warp leaves together
     const long mode = order ? (long)order[item] : m0 + item;
     const long col = mode - m0;
     const int cls = p.d_mode_class[mode];
     const int N = p.N, n = N - 2;
     const double alpha = p.d_class_z2[cls] + p.c;
     const float h = (float)(alpha * kPi / 2);
-    float2 *m0buf = smem + (size_t)warp * (5 * R * 32);     // [2][R][32] transfer rows
-    float2 *u0buf = m0buf + 2 * R * 32;                      // [2][R][32] u0
-    float *gbuf = reinterpret_cast<float *>(u0buf + 2 * R * 32);   // [2][R][32] g
+    float2 *m0buf = smem + (size_t)warp * (5 * R * 16);            // [R][32] transfer rows / r
+    float2 *u0buf = m0buf + R * 32;                                 // [R][32] u0
+    float *gbuf = reinterpret_cast<float *>(u0buf + R * 32);        // [R][32] g
     const double *fcol = f + 2 * col * N;
     double *ucol = u + 2 * col * N;
-    const float2 *F = fac + (size_t)cls * 2 * R * 32;
+    const float2 *F = fac + ((size_t)cls * 2 + par) * R * 16 + s;  // row s R + j at F[j * 16]
 
-    float2 w[2][R];
+    float2 w[R];
 #pragma unroll
-    for (int j = 0; j < R; j++)
+    for (int j = 0; j < R; j++) {
+        const int i = s * R + j, k = 2 * i + par;
+        if (k < n) {
+            const double2 fk = reinterpret_cast<const double2 *>(fcol)[k];
+            if (DF) w[j] = f2(df::hi_f64(fk.x), df::hi_f64(fk.y));
+            else w[j] = f2((float)fk.x, (float)fk.y);
+        } else {
+            w[j] = f2(0.f, 0.f);
+        }
+        float prev = 0.f;                               // 1/U of row i-1
+        if (i > 0) prev = j > 0 ? F[(j - 1) * 16].x : F[(R - 1) * 16 - 1].x;
+        gbuf[j * 32 + lane] = h * prev;
+    }
+    __syncwarp();
+    forward_sweep<R>(w, gbuf, lane, s);
+    backward_sweep<R, true>(w, F, lane, s, h, m0buf);
 #pragma unroll
-        for (int pp = 0; pp < 2; pp++) {
-            const int i = lane * R + j, k = 2 * i + pp;
+    for (int j = 0; j < R; j++) u0buf[j * 32 + lane] = w[j];
+    __syncwarp();
+    residual<R, DF>(m0buf, u0buf, fcol, lane, s, par, n, alpha);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < R; j++) w[j] = m0buf[j * 32 + lane];
+    __syncwarp();
+    forward_sweep<R>(w, gbuf, lane, s);
+    backward_sweep<R, true>(w, F, lane, s, h, m0buf);
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+        const int k = 2 * (s * R + j) + par;
+        if (k < N) {
+            double2 out = make_double2(0.0, 0.0);
             if (k < n) {
-                const double2 fk = reinterpret_cast<const double2 *>(fcol)[k];
-                if (DF) w[pp][j] = make_float2(df::from_f64(fk.x).hi, df::from_f64(fk.y).hi);
-                else w[pp][j] = make_float2((float)fk.x, (float)fk.y);
-            } else {
-                w[pp][j] = make_float2(0.f, 0.f);
-            }
-            float prev = 0.f;                          // 1/U of row i-1
-            if (i > 0) prev = j > 0 ? F[(pp * R + j - 1) * 32 + lane].x : F[(pp * R + R - 1) * 32 + lane - 1].x;
-            gbuf[(pp * R + j) * 32 + lane] = h * prev;
-        }
-    __syncwarp();
-    // solve 1
-    forward_sweep<R>(w, gbuf, lane);
-    backward_sweep<R>(w, F, lane, h, m0buf);
-#pragma unroll
-    for (int pp = 0; pp < 2; pp++)
-#pragma unroll
-        for (int j = 0; j < R; j++) u0buf[(pp * R + j) * 32 + lane] = w[pp][j];
-    __syncwarp();
-    // residual and solve 2
-    residual<R, DF>(w, u0buf, fcol, lane, n, alpha);
-    forward_sweep<R>(w, gbuf, lane);
-    backward_sweep<R>(w, F, lane, h, m0buf);
-    // u = u0 + d
-#pragma unroll
-    for (int j = 0; j < R; j++)
-#pragma unroll
-        for (int pp = 0; pp < 2; pp++) {
-            const int i = lane * R + j, k = 2 * i + pp;
-            if (k < N) {
-                double2 out = make_double2(0.0, 0.0);
-                if (k < n) {
-                    const float2 a = u0buf[(pp * R + j) * 32 + lane];
-                    if (DF) {
-                        out.x = df::to_f64(df::two_sum(a.x, w[pp][j].x));
-                        out.y = df::to_f64(df::two_sum(a.y, w[pp][j].y));
-                    } else {
-                        out.x = (double)a.x + (double)w[pp][j].x;
-                        out.y = (double)a.y + (double)w[pp][j].y;
-                    }
+                const float2 a = u0buf[j * 32 + lane];
+                if (DF) {   // exact widening of both terms, one float64 add (correctly rounded)
+                    out.x = __dadd_rn(df::f32_to_f64_bits(a.x), df::f32_to_f64_bits(w[j].x));
+                    out.y = __dadd_rn(df::f32_to_f64_bits(a.y), df::f32_to_f64_bits(w[j].y));
+                } else {
+                    out.x = (double)a.x + (double)w[j].x;
+                    out.y = (double)a.y + (double)w[j].y;
                 }
-                reinterpret_cast<double2 *>(ucol)[k] = out;
             }
+            reinterpret_cast<double2 *>(ucol)[k] = out;
         }
-    // trailing entries beyond the lanes' reach (at most 2: N - 2 unknowns <= 64 R)
+    }
+    // trailing entries beyond the lanes' reach (at most 2, since N - 2 <= 32 R)
     if (lane == 0)
-        for (int k = max(n, 64 * R); k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
+        for (int k = max(n, 32 * R); k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
 }
 
-// float64 factors -> float32 table in the lane layout: row i = lane R + j of chain
-// (class, parity) goes to [class][parity][j][lane].
+// float64 factors -> float32 table in the lane layout: row i = s R + j of chain
+// (class, parity) goes to [class][parity][j][s].
 __global__ void pack_helm_f32_kernel(Plan p, int R, float2 *out) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const long total = p.n_classes * 2 * (long)R * 32;
+    const long total = p.n_classes * 2 * (long)R * 16;
     if (t >= total) return;
-    const int lane = (int)(t % 32);
-    const int j = (int)((t / 32) % R);
-    const long chain = t / (32L * R);                  // class * 2 + parity
-    const int i = lane * R + j;
+    const int s = (int)(t % 16);
+    const int j = (int)((t / 16) % R);
+    const long chain = t / (16L * R);                  // class * 2 + parity
+    const int i = s * R + j;
     float2 v = make_float2(0.f, 0.f);
     if (i < p.rows_h) {
         const double *row = p.d_fac_h + (chain * p.rows_h + i) * kHelmF64;
         v = make_float2((float)row[0], (float)row[1]);   // 1/U_ii, U2
-        if (row[0] == 0.0) v = make_float2(0.f, 0.f);
     }
     out[t] = v;
 }
 
 template <int R, bool DF>
 cudaError_t launch_helm_mixed_R(const Plan &p, const int *order, long m0, long count, const double *f, double *u,
-                                const float2 *fac, cudaStream_t s) {
-    const int warps = 4;
-    const size_t smem = (size_t)warps * 5 * R * 32 * sizeof(float2);
+                                const float2 *fac, cudaStream_t st) {
+    const int warps = 2;
+    // per warp: transfer rows and u0 ([R][32] float2 each) and g ([R][32] float)
+    const size_t smem = (size_t)warps * 5 * R * 16 * sizeof(float2);
     auto kern = helm_mixed_kernel<R, DF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((count + warps - 1) / warps);
-    kern<<<blocks, warps * 32, smem, s>>>(p, order, m0, count, f, u, fac);
+    kern<<<blocks, warps * 32, smem, st>>>(p, order, m0, count, f, u, fac);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+// Rows per lane of the warp-per-mode Helmholtz kernels (16 lanes per parity chain).
 int helm_mixed_R(int N) {
     const int rows = (N - 2 + 1) / 2;
-    const int R = (rows + 31) / 32;
-    if (R <= 1) return 1;
+    const int R = (rows + 15) / 16;
+    if (N > 2048) return 0;
     if (R <= 2) return 2;
     if (R <= 4) return 4;
     if (R <= 8) return 8;
     if (R <= 16) return 16;
     if (R <= 24) return 24;
     if (R <= 32) return 32;
+    if (R <= 48) return 48;
+    if (R <= 64) return 64;
     return 0;
 }
 
 cudaError_t pack_helm_f32(const Plan &p, int R, float2 *out, cudaStream_t s) {
-    const long total = p.n_classes * 2 * (long)R * 32;
+    const long total = p.n_classes * 2 * (long)R * 16;
     pack_helm_f32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, R, out);
     return cudaGetLastError();
 }
@@ -415,13 +378,13 @@ cudaError_t launch_helm_mixed(const Plan &p, bool dfres, long m0, long count, co
     if (count <= 0) return cudaSuccess;
     const int *order = (m0 == 0 && count == p.n_modes) ? p.d_order : nullptr;
     const float2 *fac = reinterpret_cast<const float2 *>(p.d_fac_h32);
-    const int R = p.R_h;
 #define SHEN_CASE(RR)                                                                         \
     case RR:                                                                                  \
         return dfres ? launch_helm_mixed_R<RR, true>(p, order, m0, count, f, u, fac, s)       \
                      : launch_helm_mixed_R<RR, false>(p, order, m0, count, f, u, fac, s);
-    switch (R) {
-        SHEN_CASE(1) SHEN_CASE(2) SHEN_CASE(4) SHEN_CASE(8) SHEN_CASE(16) SHEN_CASE(24) SHEN_CASE(32)
+    switch (p.R_h) {
+        SHEN_CASE(2) SHEN_CASE(4) SHEN_CASE(8) SHEN_CASE(16) SHEN_CASE(24) SHEN_CASE(32) SHEN_CASE(48)
+        SHEN_CASE(64)
     default: return cudaErrorInvalidValue;
     }
 #undef SHEN_CASE

@@ -170,7 +170,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.R_h = helm_mixed_R(N);
     if (p.R_h > 0) {
-        PLAN_TRY(dalloc(&p.d_fac_h32, (size_t)p.n_classes * 2 * p.R_h * 32 * 2, B));
+        PLAN_TRY(dalloc(&p.d_fac_h32, (size_t)p.n_classes * 2 * p.R_h * 16 * 2, B));
         PLAN_TRY(pack_helm_f32(p, p.R_h, reinterpret_cast<float2 *>(p.d_fac_h32), s));
     }
     int err_host[2];
