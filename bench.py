@@ -30,6 +30,8 @@ WORKLOADS = {
     "large": dict(N=1536, Nx=2048, Nz=1536, nu=1 / 2000, dt=5e-5),
     # profiling case: N = 1024 columns on a 128 x 128 grid (136 MB per field, > L2)
     "n1024s": dict(N=1024, Nx=128, Nz=128, nu=1 / 2000, dt=1e-4),
+    # 4096 channels with uneven N (64..512), grids 16..64, nu in [1e-4, 1e-2], dt in [1e-4, 1e-2]
+    "batch": dict(n_inst=4096, seed=5),
 }
 METRIC = "Shen solves*N/s (Helmholtz + biharmonic, all modes)"
 BYTES_PER_ROW = 32          # algorithmic bytes per complex row of one solve: read f + write u
@@ -166,7 +168,7 @@ AUTO_PRECISION = {"helmholtz": "df_r1", "biharmonic": "fp64"}
 def resolve_precision(spec):
     if spec == "auto":
         return dict(AUTO_PRECISION)
-    return {"helmholtz": spec, "biharmonic": spec if spec == "fp64" else "fp64"}
+    return {"helmholtz": spec, "biharmonic": spec}
 
 
 def run_reference(args, w):
@@ -212,19 +214,36 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
-    N = w["N"]
     prec = resolve_precision(args.precision)
     stream = torch.cuda.Stream()
+    batched = args.workload == "batch"
     t_plan = time.perf_counter()
-    plan = Plan(N, w["Nx"], w["Nz"], w["nu"], w["dt"], stream=stream)
+    if batched:
+        from paper_1701_03787_gb300 import BatchPlan
+        insts = inputs.batch_instances(w["n_inst"], seed=w["seed"])
+        plan = BatchPlan(insts, stream=stream)
+        N = None
+        nm = plan.n_modes
+        rows = plan.field_elems
+    else:
+        N = w["N"]
+        plan = Plan(N, w["Nx"], w["Nz"], w["nu"], w["dt"], stream=stream)
+        nm = plan.n_modes
+        rows = nm * N
     t_plan = time.perf_counter() - t_plan
-    nm = plan.n_modes
     with torch.cuda.stream(stream):
-        f_h = inputs.rhs_torch(nm, N, seed=100 + rank)
-        f_b = inputs.rhs_torch(nm, N, seed=200 + rank)
+        if batched:
+            f_h = inputs.batch_rhs_torch(plan.offsets, insts, seed=100 + rank)
+            f_b = inputs.batch_rhs_torch(plan.offsets, insts, seed=200 + rank)
+        else:
+            f_h = inputs.rhs_torch(nm, N, seed=100 + rank)
+            f_b = inputs.rhs_torch(nm, N, seed=200 + rank)
         u_h = torch.empty_like(f_h)
         u_b = torch.empty_like(f_b)
     stream.synchronize()
+    if batched:
+        plan.helmholtz_solve = lambda f, u, precision, stream: plan.solve("helmholtz", f, u, precision, stream)
+        plan.biharmonic_solve = lambda f, u, precision, stream: plan.solve("biharmonic", f, u, precision, stream)
 
     def step(ph=prec["helmholtz"], pb=prec["biharmonic"]):
         plan.helmholtz_solve(f_h, u_h, precision=ph, stream=stream)
@@ -258,7 +277,6 @@ def main():
         t = torch.tensor([ms], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    rows = nm * N
     value = world * 2 * rows / (ms * 1e-3)
 
     # end to end through the public API with pinned host buffers
@@ -318,11 +336,11 @@ def main():
             "vs_baseline": None,
             "dtype": "f64" if set(prec.values()) == {"fp64"} else "f32 sweeps + refinement (io f64)",
             "data": "synthetic", "precision": prec,
-            "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes,
+            "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes, "rows": rows,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e}
-    if rank == 0 and not args.no_check:
+    if rank == 0 and not args.no_check and not batched:
         z2 = plan.n_modes
         special = list(inputs.grid_modes(w["Nx"], w["Nz"]).values())
         modes = inputs.sample_modes(nm, 0.01, 3, must_include=special)
@@ -331,7 +349,7 @@ def main():
         F_h, U_h = f_h[idx].cpu().numpy(), u_h[idx].cpu().numpy()
         F_b, U_b = f_b[idx].cpu().numpy(), u_b[idx].cpu().numpy()
         line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and not batched:
         line["cpu_baseline"] = cpu_baseline(w, args.precision)
     if rank == 0:
         print(json.dumps(line))

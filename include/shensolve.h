@@ -78,13 +78,19 @@ typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
  *   SHEN_DF_R1 /    as SHEN_FP32_R*, but the residual and the correction use
  *   SHEN_DF_R2      float-float arithmetic (pairs of float32, error-free
  *                   transformations of Dekker and Knuth) instead of float64.
- * Plan creation fails with SHEN_ERR_UNSUPPORTED for variants not built in. */
+ *   SHEN_DF         forward elimination and back substitution themselves in
+ *                   float-float arithmetic (~48 significant bits) with the factors
+ *                   as float-float pairs; no refinement.
+ * A solve returns SHEN_ERR_UNSUPPORTED for a (problem, precision) pair that is not
+ * built: the float32-sweep variants exist for the Helmholtz problem, N <= 2048, one
+ * refinement step. */
 typedef enum {
     SHEN_FP64 = 0,
     SHEN_FP32_R1 = 1,
     SHEN_FP32_R2 = 2,
     SHEN_DF_R1 = 3,
-    SHEN_DF_R2 = 4
+    SHEN_DF_R2 = 4,
+    SHEN_DF = 5
 } shen_precision;
 
 /* Create a plan for one channel: N Chebyshev modes (8 <= N <= 4096), Fourier grid
@@ -134,6 +140,51 @@ shen_status shen_plan_check(shen_plan_t plan, long *where);
 
 /* Free the plan (after any work using it has completed).  NULL is ignored. */
 void shen_plan_destroy(shen_plan_t plan);
+
+/* ---- Batched plans: many independent channels with uneven sizes in one launch ----
+ *
+ * Each instance is a channel as in shen_plan_create (its own N, Fourier grid, nu, dt,
+ * box).  The batched field stores instance i's mode-major columns (n_modes_i * N_i
+ * complex values) after those of instances 0 .. i-1; shen_batch_offsets returns the
+ * complex-element offset of each instance.  The solve is one persistent launch whose
+ * warps take chunks of modes from a work queue ordered by decreasing N (the queue
+ * counter is plan-owned device memory, reset by an asynchronous memset at every call,
+ * so calls on the same plan must not overlap on the GPU).  Both calls enqueue on
+ * `stream` only (a stream capture records them). */
+typedef struct shen_batch_s *shen_batch_t;
+
+typedef struct {
+    int N;                /* Chebyshev modes, 8 <= N <= 4096 */
+    int Nx, Nz;           /* Fourier grid, even, >= 2 */
+    double nu, dt;        /* viscosity and time step, > 0 */
+    double Lx, Lz;        /* box lengths, > 0 */
+} shen_instance_desc;
+
+/* Build a batched plan from n_inst HOST descriptors.  Blocks until ready.  flags must
+ * be 0.  Errors as shen_plan_create. */
+shen_status shen_batch_plan_create(shen_batch_t *batch, int n_inst, const shen_instance_desc *descs,
+                                   unsigned flags, void *stream);
+
+/* Total modes, total complex elements of a batched field, distinct (instance, z2)
+ * factorisations, device bytes held.  Any output pointer may be NULL. */
+shen_status shen_batch_info(shen_batch_t batch, long *n_modes, long *field_elems, long *n_classes,
+                            long long *device_bytes);
+
+/* offsets[0 .. n_inst]: complex-element offset of each instance's field in the batched
+ * field, and the total (HOST array of n_inst + 1 longs). */
+shen_status shen_batch_offsets(shen_batch_t batch, long *offsets);
+
+/* Solve every mode of every instance: problem SHEN_HELMHOLTZ or SHEN_BIHARMONIC,
+ * precision SHEN_FP64 or SHEN_DF (others: SHEN_ERR_UNSUPPORTED).  f, u: DEVICE batched
+ * fields (u == f allowed).  Layout and zeroed trailing entries as for single plans. */
+shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, double *u, int precision,
+                             void *stream);
+
+/* Device-side error state of the batched plan (SHEN_OK or SHEN_ERR_SINGULAR). */
+shen_status shen_batch_check(shen_batch_t batch);
+
+/* Free a batched plan (after its work has completed).  NULL is ignored. */
+void shen_batch_destroy(shen_batch_t batch);
 
 /* Static description of a status code. */
 const char *shen_status_string(int status);

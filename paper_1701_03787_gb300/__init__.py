@@ -6,6 +6,6 @@ biharmonic basis) and the right-hand-side operators of Eqs. gfin / ufin, with th
 paper's O(N) direct algorithms in hand-written sm_103a CUDA behind the C ABI of
 ``include/shensolve.h``.  ``binding`` is the Python view of that ABI.
 """
-from .binding import Plan, ShenError, lib, PRECISIONS, PROBLEMS  # noqa: F401
+from .binding import BatchPlan, Plan, ShenError, lib, PRECISIONS, PROBLEMS  # noqa: F401
 
-__all__ = ["Plan", "ShenError", "lib", "PRECISIONS", "PROBLEMS"]
+__all__ = ["BatchPlan", "Plan", "ShenError", "lib", "PRECISIONS", "PROBLEMS"]

@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "shensolve.h")
 
 SHEN_OK, SHEN_ERR_ARG, SHEN_ERR_ALLOC, SHEN_ERR_CUDA, SHEN_ERR_SINGULAR, SHEN_ERR_UNSUPPORTED = range(6)
 SHEN_HELMHOLTZ, SHEN_BIHARMONIC = 0, 1
-PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4}
+PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5}
 PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
 
 _lib = None
@@ -46,6 +46,12 @@ def lib():
         "shen_plan_info": ([P, P, P, P, P], I),
         "shen_plan_check": ([P, P], I),
         "shen_plan_destroy": ([P], None),
+        "shen_batch_plan_create": ([P, I, P, ctypes.c_uint, P], I),
+        "shen_batch_info": ([P, P, P, P, P], I),
+        "shen_batch_offsets": ([P, P], I),
+        "shen_batch_solve": ([P, I, P, P, I, P], I),
+        "shen_batch_check": ([P], I),
+        "shen_batch_destroy": ([P], None),
         "shen_status_string": ([I], ctypes.c_char_p),
         "shen_version": ([], I),
     }
@@ -204,3 +210,69 @@ class Plan:
     def check_device(self):
         where = ctypes.c_long()
         check(lib().shen_plan_check(self._h, ctypes.byref(where)), "shen_plan_check")
+
+
+class InstanceDesc(ctypes.Structure):
+    """C struct shen_instance_desc."""
+    _fields_ = [("N", ctypes.c_int), ("Nx", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("Lx", ctypes.c_double), ("Lz", ctypes.c_double)]
+
+
+class BatchPlan:
+    """Batched plan (C type shen_batch_t): many channels with uneven N in one launch.
+
+    instances: sequence of dicts with keys N, Nx, Nz, nu, dt and optional Lx, Lz.
+    The batched field is a flat complex128 CUDA tensor of ``field_elems`` entries;
+    ``offsets[i]`` is where instance i's (n_modes_i, N_i) block starts."""
+
+    def __init__(self, instances, stream=None):
+        import math
+        descs = (InstanceDesc * len(instances))()
+        for d, inst in zip(descs, instances):
+            d.N, d.Nx, d.Nz = int(inst["N"]), int(inst["Nx"]), int(inst["Nz"])
+            d.nu, d.dt = float(inst["nu"]), float(inst["dt"])
+            d.Lx = float(inst.get("Lx", 2 * math.pi))
+            d.Lz = float(inst.get("Lz", math.pi))
+        self._h = ctypes.c_void_p()
+        check(lib().shen_batch_plan_create(ctypes.byref(self._h), len(instances), ctypes.cast(descs, ctypes.c_void_p),
+                                           0, _stream(stream)), "shen_batch_plan_create")
+        n_modes, elems, ncls = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        nbytes = ctypes.c_longlong()
+        check(lib().shen_batch_info(self._h, ctypes.byref(n_modes), ctypes.byref(elems), ctypes.byref(ncls),
+                                    ctypes.byref(nbytes)), "shen_batch_info")
+        self.n_instances = len(instances)
+        self.n_modes, self.field_elems, self.n_classes, self.device_bytes = (
+            n_modes.value, elems.value, ncls.value, nbytes.value)
+        offs = (ctypes.c_long * (len(instances) + 1))()
+        check(lib().shen_batch_offsets(self._h, ctypes.cast(offs, ctypes.c_void_p)), "shen_batch_offsets")
+        self.offsets = list(offs)
+
+    def close(self):
+        if self._h:
+            lib().shen_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, problem, f, u=None, precision="fp64", stream=None):
+        import torch
+        if f.dtype != torch.complex128 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.field_elems:
+            raise ValueError(f"f must be a contiguous complex128 CUDA tensor of {self.field_elems} entries")
+        if u is None:
+            u = torch.empty_like(f)
+        check(lib().shen_batch_solve(self._h, _problem(problem), _ptr(f), _ptr(u), _prec(precision),
+                                     _stream(stream)), "shen_batch_solve")
+        return u
+
+    def check_device(self):
+        check(lib().shen_batch_check(self._h), "shen_batch_check")

@@ -1,0 +1,411 @@
+// Batched plans: many independent channels (instances) with uneven N, Fourier grids,
+// nu and dt, solved in one persistent launch.
+//
+// Each instance is a channel as in shen_plan_create; its field is stored after the
+// previous instance's (complex offset = sum of n_modes_j N_j over earlier instances).
+// Plan time groups each instance's modes by z2 and factorises every distinct (instance,
+// z2) once in float64 (Sec. 4 algorithms, as for single plans).  The solve is a
+// persistent kernel: warps take chunks of 16 modes (32 parity chains) from a work queue
+// ordered by decreasing N (longest chains first, equal N within a chunk), until the
+// queue is empty.  The queue counter lives in plan-owned device memory and is reset by
+// an asynchronous memset before each launch.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "chains.cuh"
+
+namespace shen {
+
+struct BatchInst {
+    int N, rows_h, rows_b, tab;     // tab: index of the per-N table set
+    long n_modes, mode0, col0;      // first global mode, first complex element of the field
+    double c;
+};
+
+struct BatchCls {
+    double z2;
+    int inst;
+    long fh, fb;                    // offsets (in rows) of the chain pair in the factor arrays
+};
+
+struct BatchDev {
+    int n_inst;
+    long n_modes, n_cls;
+    const BatchInst *inst;
+    const int *mode_inst, *mode_cls, *work;
+    const BatchCls *cls;
+    const RowTables *tabs;
+    const float4 *qs_df;            // per table set: N_max + 8 entries each
+    int qs_stride;
+    double *fac_h, *fac_b;          // float64 factors, kHelmF64 / kBiF64 doubles per row
+    float4 *fdf_h, *fdf_b;          // float-float factors, 2 / 4 float4 per row
+    int *queue;
+    int *err;
+};
+
+namespace {
+
+__global__ void batch_factor_kernel(BatchDev b) {
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (tid >= 2 * b.n_cls) return;
+    const long c = tid >> 1;
+    const int par = (int)(tid & 1);
+    const BatchCls cl = b.cls[c];
+    const BatchInst in = b.inst[cl.inst];
+    const RowTables &T = b.tabs[in.tab];
+    double *Fh = b.fac_h + (cl.fh + (long)par * in.rows_h) * kHelmF64;
+    double *Fb = b.fac_b + (cl.fb + (long)par * in.rows_b) * kBiF64;
+    chains::factor_helm_chain(T, in.N, cl.z2, in.c, par, Fh, in.rows_h, b.err, c);
+    chains::factor_bih_chain(T, in.N, cl.z2, in.c, par, Fb, in.rows_b, b.err, c);
+    // float-float copies (hi, lo) of the same rows
+    float4 *Dh = b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2;
+    float4 *Db = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
+    auto split = [](double x) {
+        const float hi = (float)x;
+        return make_float2(hi, (float)(x - (double)hi));
+    };
+    for (int i = 0; i < in.rows_h; i++) {
+        const double *r = Fh + i * kHelmF64;
+        const float2 a = split(r[0]), bb = split(r[1]), l = split(r[2]);
+        Dh[2 * i] = make_float4(a.x, a.y, bb.x, bb.y);
+        Dh[2 * i + 1] = make_float4(l.x, l.y, 0.f, 0.f);
+    }
+    for (int i = 0; i < in.rows_b; i++) {
+        const double *r = Fb + i * kBiF64;
+        float2 v[7];
+        for (int q = 0; q < 7; q++) v[q] = split(r[q]);
+        Db[4 * i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        Db[4 * i + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+        Db[4 * i + 2] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
+        Db[4 * i + 3] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
+    }
+}
+
+__global__ void batch_pack_qs_kernel(BatchDev b, int n_tabs, const int *tab_N) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tabs * b.qs_stride) return;
+    const int tab = t / b.qs_stride, k = t % b.qs_stride;
+    const int N = tab_N[tab];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < N - 4) {
+        const double q = b.tabs[tab].qk[k], s = b.tabs[tab].sk[k];
+        const float qh = (float)q, sh = (float)s;
+        v = make_float4(qh, (float)(q - (double)qh), sh, (float)(s - (double)sh));
+    }
+    const_cast<float4 *>(b.qs_df)[t] = v;
+}
+
+// precision: 0 float64, 1 float-float.  problem: SHEN_HELMHOLTZ / SHEN_BIHARMONIC.
+template <int PREC, int PROBLEM>
+__global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const double *f, double *u) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(b.queue, 16);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= b.n_modes) return;
+        const long item = base + (lane >> 1);
+        const int par = lane & 1;
+        if (item < b.n_modes) {
+            const int m = b.work[item];
+            const BatchInst in = b.inst[b.mode_inst[m]];
+            const BatchCls cl = b.cls[b.mode_cls[m]];
+            const long off = 2 * (in.col0 + (long)(m - in.mode0) * in.N);
+            if (PROBLEM == SHEN_HELMHOLTZ) {
+                if (PREC == 0) {
+                    chains::solve_helm_fp64_chain(in.N, par, f + off, u + off,
+                                                  b.fac_h + (cl.fh + (long)par * in.rows_h) * kHelmF64,
+                                                  (cl.z2 + in.c) * kPi / 2);
+                } else {
+                    chains::solve_helm_df_chain(in.N, par, f + off, u + off,
+                                                b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2,
+                                                df::from_f64((cl.z2 + in.c) * (kPi / 2)));
+                }
+            } else {
+                if (PREC == 0) {
+                    chains::solve_bih_fp64_chain(in.N, par, f + off, u + off,
+                                                 b.fac_b + (cl.fb + (long)par * in.rows_b) * kBiF64,
+                                                 b.tabs[in.tab].qk, b.tabs[in.tab].sk);
+                } else {
+                    chains::solve_bih_df_chain(in.N, par, f + off, u + off,
+                                               b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4,
+                                               b.qs_df + (size_t)in.tab * b.qs_stride);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride);   // plan.cu
+
+}  // namespace shen
+
+using namespace shen;
+
+struct shen_batch_s {
+    BatchDev d{};
+    std::vector<BatchInst> inst;
+    std::vector<int> tab_N;
+    // owned device allocations
+    std::vector<void *> allocs;
+    RowTables *d_tabs = nullptr;
+    long long device_bytes = 0;
+    int grid = 0;
+    ~shen_batch_s() {
+        for (void *p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+template <class T>
+cudaError_t balloc(shen_batch_s *b, T **ptr, size_t count) {
+    b->device_bytes += (long long)(count * sizeof(T));
+    cudaError_t e = cudaMalloc((void **)ptr, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) b->allocs.push_back(*ptr);
+    return e;
+}
+
+shen_status cuda_status(cudaError_t e) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SHEN_ERR_ALLOC : SHEN_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_instance_desc *descs, unsigned flags,
+                                   void *stream) {
+    if (!out) return SHEN_ERR_ARG;
+    *out = nullptr;
+    if (flags != 0 || n_inst < 1 || !descs) return SHEN_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // validate and lay out the instances
+    std::vector<BatchInst> inst((size_t)n_inst);
+    std::map<int, int> tab_of_N;
+    long mode0 = 0, col0 = 0;
+    for (int i = 0; i < n_inst; i++) {
+        const shen_instance_desc &d = descs[i];
+        if (d.N < 8 || d.N > 4096 || d.Nx < 2 || d.Nz < 2 || (d.Nx & 1) || (d.Nz & 1)) return SHEN_ERR_ARG;
+        if (!(d.nu > 0) || !(d.dt > 0) || !(d.Lx > 0) || !(d.Lz > 0) || !std::isfinite(d.nu) ||
+            !std::isfinite(d.dt) || !std::isfinite(d.Lx) || !std::isfinite(d.Lz))
+            return SHEN_ERR_ARG;
+        const double c = 2.0 / (d.nu * d.dt);
+        if (!std::isfinite(c)) return SHEN_ERR_ARG;
+        BatchInst &b = inst[i];
+        b.N = d.N;
+        b.rows_h = (d.N - 2 + 1) / 2;
+        b.rows_b = (d.N - 4 + 1) / 2;
+        b.n_modes = (long)(d.Nx / 2 + 1) * d.Nz;
+        b.mode0 = mode0;
+        b.col0 = col0;
+        b.c = c;
+        if (!tab_of_N.count(d.N)) {
+            const int t = (int)tab_of_N.size();
+            tab_of_N[d.N] = t;
+        }
+        b.tab = tab_of_N[d.N];
+        mode0 += b.n_modes;
+        col0 += b.n_modes * d.N;
+        if (mode0 > (1L << 30)) return SHEN_ERR_ARG;
+    }
+    const long n_modes = mode0;
+    // classes (distinct z2 per instance), factor offsets, per-mode lookups
+    std::vector<BatchCls> cls;
+    std::vector<int> mode_inst((size_t)n_modes), mode_cls((size_t)n_modes);
+    long fh = 0, fb = 0;
+    for (int i = 0; i < n_inst; i++) {
+        const shen_instance_desc &d = descs[i];
+        BatchInst &b = inst[i];
+        const long nxh = d.Nx / 2 + 1;
+        std::vector<std::pair<double, long>> z((size_t)b.n_modes);
+        for (long ix = 0; ix < nxh; ix++)
+            for (long iz = 0; iz < d.Nz; iz++) {
+                const long kzi = iz < d.Nz / 2 ? iz : iz - d.Nz;
+                const double kx = 2 * kPi * (double)ix / d.Lx, kz = 2 * kPi * (double)kzi / d.Lz;
+                z[ix * d.Nz + iz] = {kx * kx + kz * kz, ix * d.Nz + iz};
+            }
+        std::sort(z.begin(), z.end());
+        for (long w = 0; w < b.n_modes; w++) {
+            if (w == 0 || z[w].first != z[w - 1].first) {
+                cls.push_back(BatchCls{z[w].first, i, fh, fb});
+                fh += 2L * b.rows_h;
+                fb += 2L * b.rows_b;
+            }
+            mode_inst[b.mode0 + z[w].second] = i;
+            mode_cls[b.mode0 + z[w].second] = (int)cls.size() - 1;
+        }
+    }
+    // work order: decreasing N, then instance, then class
+    std::vector<int> work((size_t)n_modes);
+    std::iota(work.begin(), work.end(), 0);
+    std::stable_sort(work.begin(), work.end(), [&](int a, int b2) {
+        const int Na = inst[mode_inst[a]].N, Nb = inst[mode_inst[b2]].N;
+        if (Na != Nb) return Na > Nb;
+        if (mode_cls[a] != mode_cls[b2]) return mode_cls[a] < mode_cls[b2];
+        return a < b2;
+    });
+
+    shen_batch_s *b = new (std::nothrow) shen_batch_s;
+    if (!b) return SHEN_ERR_ALLOC;
+    auto fail = [&](shen_status st) {
+        delete b;
+        return st;
+    };
+#define B_TRY(expr)                                  \
+    do {                                             \
+        cudaError_t e_ = (expr);                     \
+        if (e_ != cudaSuccess) return fail(cuda_status(e_)); \
+    } while (0)
+    b->inst = inst;
+    const int n_tabs = (int)tab_of_N.size();
+    b->tab_N.assign((size_t)n_tabs, 0);
+    int N_max = 0;
+    for (auto &kv : tab_of_N) {
+        b->tab_N[kv.second] = kv.first;
+        N_max = std::max(N_max, kv.first);
+    }
+    // per-N row tables
+    std::vector<RowTables> tabs_h((size_t)n_tabs);
+    for (int t = 0; t < n_tabs; t++) {
+        std::vector<double> tab;
+        std::vector<float> tab32;
+        int stride = 0;
+        build_row_tables(b->tab_N[t], tab, tab32, stride);
+        double *dt = nullptr;
+        B_TRY(balloc(b, &dt, tab.size()));
+        B_TRY(cudaMemcpyAsync(dt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        RowTables &T = tabs_h[t];
+        T.bd0 = dt + 0 * stride; T.ad0 = dt + 1 * stride; T.adt = dt + 2 * stride;
+        T.bb0 = dt + 3 * stride; T.bb2 = dt + 4 * stride; T.bb4 = dt + 5 * stride;
+        T.ab0 = dt + 6 * stride; T.abp = dt + 7 * stride; T.abm = dt + 8 * stride;
+        T.qb0 = dt + 9 * stride; T.pk = dt + 10 * stride; T.rk = dt + 11 * stride;
+        T.qk = dt + 12 * stride; T.sk = dt + 13 * stride;
+        T.qk32 = nullptr; T.sk32 = nullptr;
+    }
+    BatchDev &D = b->d;
+    D.n_inst = n_inst;
+    D.n_modes = n_modes;
+    D.n_cls = (long)cls.size();
+    D.qs_stride = N_max + 8;
+    RowTables *d_tabs = nullptr;
+    BatchInst *d_inst = nullptr;
+    BatchCls *d_cls = nullptr;
+    int *d_mi = nullptr, *d_mc = nullptr, *d_work = nullptr, *d_tabN = nullptr;
+    float4 *d_qs = nullptr;
+    B_TRY(balloc(b, &d_tabs, (size_t)n_tabs));
+    B_TRY(balloc(b, &d_inst, inst.size()));
+    B_TRY(balloc(b, &d_cls, cls.size()));
+    B_TRY(balloc(b, &d_mi, (size_t)n_modes));
+    B_TRY(balloc(b, &d_mc, (size_t)n_modes));
+    B_TRY(balloc(b, &d_work, (size_t)n_modes));
+    B_TRY(balloc(b, &d_tabN, (size_t)n_tabs));
+    B_TRY(balloc(b, &d_qs, (size_t)n_tabs * D.qs_stride));
+    B_TRY(balloc(b, &D.fac_h, (size_t)fh * kHelmF64));
+    B_TRY(balloc(b, &D.fac_b, (size_t)fb * kBiF64));
+    B_TRY(balloc(b, &D.fdf_h, (size_t)fh * 2));
+    B_TRY(balloc(b, &D.fdf_b, (size_t)fb * 4));
+    B_TRY(balloc(b, &D.queue, 1));
+    B_TRY(balloc(b, &D.err, 2));
+    B_TRY(cudaMemcpyAsync(d_tabs, tabs_h.data(), tabs_h.size() * sizeof(RowTables), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(d_inst, inst.data(), inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(d_cls, cls.data(), cls.size() * sizeof(BatchCls), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(d_mi, mode_inst.data(), mode_inst.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(d_mc, mode_cls.data(), mode_cls.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(d_tabN, b->tab_N.data(), b->tab_N.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    const int err_init[2] = {0, 0x7fffffff};
+    B_TRY(cudaMemcpyAsync(D.err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, s));
+    D.inst = d_inst;
+    D.cls = d_cls;
+    D.mode_inst = d_mi;
+    D.mode_cls = d_mc;
+    D.work = d_work;
+    D.tabs = d_tabs;
+    D.qs_df = d_qs;
+    b->d_tabs = d_tabs;
+    batch_factor_kernel<<<(unsigned)((2 * D.n_cls + 127) / 128), 128, 0, s>>>(D);
+    B_TRY(cudaGetLastError());
+    batch_pack_qs_kernel<<<(unsigned)((n_tabs * D.qs_stride + 255) / 256), 256, 0, s>>>(D, n_tabs, d_tabN);
+    B_TRY(cudaGetLastError());
+    int err_host[2];
+    B_TRY(cudaMemcpyAsync(err_host, D.err, sizeof(err_host), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (err_host[0]) return fail(SHEN_ERR_SINGULAR);
+    // persistent grid: resident blocks of the largest solve kernel
+    int dev = 0, sms = 0, per_sm = 0;
+    B_TRY(cudaGetDevice(&dev));
+    B_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    B_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_solve_kernel<1, SHEN_BIHARMONIC>, 128, 0));
+    b->grid = std::max(1, sms * std::max(per_sm, 1));
+#undef B_TRY
+    *out = b;
+    return SHEN_OK;
+}
+
+shen_status shen_batch_info(shen_batch_t batch, long *n_modes, long *field_elems, long *n_classes,
+                            long long *device_bytes) {
+    if (!batch) return SHEN_ERR_ARG;
+    if (n_modes) *n_modes = batch->d.n_modes;
+    if (field_elems) {
+        const BatchInst &l = batch->inst.back();
+        *field_elems = l.col0 + l.n_modes * l.N;
+    }
+    if (n_classes) *n_classes = batch->d.n_cls;
+    if (device_bytes) *device_bytes = batch->device_bytes;
+    return SHEN_OK;
+}
+
+shen_status shen_batch_offsets(shen_batch_t batch, long *offsets) {
+    if (!batch || !offsets) return SHEN_ERR_ARG;
+    for (size_t i = 0; i < batch->inst.size(); i++) offsets[i] = batch->inst[i].col0;
+    const BatchInst &l = batch->inst.back();
+    offsets[batch->inst.size()] = l.col0 + l.n_modes * l.N;
+    return SHEN_OK;
+}
+
+shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, double *u, int precision,
+                             void *stream) {
+    if (!batch || !f || !u) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (precision != SHEN_FP64 && precision != SHEN_DF) {
+        if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
+        return SHEN_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(f) & 15u) || (reinterpret_cast<uintptr_t>(u) & 15u)) return SHEN_ERR_ARG;
+    long elems = 0;
+    shen_batch_info(batch, nullptr, &elems, nullptr, nullptr);
+    if (f != u && !(f + 2 * elems <= u || u + 2 * elems <= f)) return SHEN_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(batch->d.queue, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const BatchDev &D = batch->d;
+    if (problem == SHEN_HELMHOLTZ) {
+        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
+        else batch_solve_kernel<1, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
+    } else {
+        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
+        else batch_solve_kernel<1, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SHEN_OK : cuda_status(e);
+}
+
+shen_status shen_batch_check(shen_batch_t batch) {
+    if (!batch) return SHEN_ERR_ARG;
+    int err_host[2];
+    cudaError_t e = cudaMemcpy(err_host, batch->d.err, sizeof(err_host), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    return err_host[0] ? SHEN_ERR_SINGULAR : SHEN_OK;
+}
+
+void shen_batch_destroy(shen_batch_t batch) { delete batch; }
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// Float-float sweeps: the paper's O(N) forward elimination and back substitution
+// (Sec. 4: Helmholtz odd/even LU; Algorithm LUSolveBiharmonic with the Eq. ab tail)
+// carried out in float-float arithmetic (value = hi + lo, two float32) with the float64
+// LU factors stored as float-float pairs.
+//
+// GB300 runs float64 at about 1/64 of its float32 rate, while float-float keeps ~48
+// significant bits on the float32 pipes.  The sweeps need no refinement step.
+//
+// Work decomposition: one thread per (mode, parity) chain, real and imaginary parts
+// side by side.  The forward sweep writes y (float-float, 16 bytes per complex row)
+// into the output column and the back substitution reads it back in reverse and
+// overwrites it with u (float64), so the kernels use no scratch memory and u == f works.
+#include "chains.cuh"
+
+namespace shen {
+namespace {
+
+using df::F2;
+
+struct WorkItem {
+    long col;
+    int cls, par;
+};
+
+__device__ __forceinline__ bool work_item(const Plan &p, const int *order, long m0, long count, WorkItem &w) {
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (tid >= 2 * count) return false;
+    const long item = tid >> 1;
+    w.par = (int)(tid & 1);
+    const long mode = order ? (long)order[item] : m0 + item;
+    w.col = mode - m0;
+    w.cls = p.d_mode_class[mode];
+    return true;
+}
+
+__global__ void __launch_bounds__(128) helm_df_kernel(Plan p, const int *order, long m0, long count,
+                                                      const double *f, double *u, const float4 *fac) {
+    WorkItem w;
+    if (!work_item(p, order, m0, count, w)) return;
+    const long off = 2 * w.col * p.N;
+    const F2 h = df::from_f64((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
+    chains::solve_helm_df_chain(p.N, w.par, f + off, u + off, fac + ((size_t)w.cls * 2 + w.par) * p.rows_h * 2, h);
+}
+
+__global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, long m0, long count,
+                                                     const double *f, double *u, const float4 *fac,
+                                                     const float4 *qs) {
+    WorkItem w;
+    if (!work_item(p, order, m0, count, w)) return;
+    const long off = 2 * w.col * p.N;
+    chains::solve_bih_df_chain(p.N, w.par, f + off, u + off, fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4, qs);
+}
+
+__device__ __forceinline__ float2 split2(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+__global__ void pack_helm_df_kernel(Plan p, float4 *out) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;      // row of all chains
+    if (t >= p.n_classes * 2 * (long)p.rows_h) return;
+    const double *row = p.d_fac_h + t * kHelmF64;                    // 1/U0, U2, l
+    const float2 a = split2(row[0]), b = split2(row[1]), c = split2(row[2]);
+    out[2 * t] = make_float4(a.x, a.y, b.x, b.y);
+    out[2 * t + 1] = make_float4(c.x, c.y, 0.f, 0.f);
+}
+
+__global__ void pack_bih_df_kernel(Plan p, float4 *out) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= p.n_classes * 2 * (long)p.rows_b) return;
+    const double *row = p.d_fac_b + t * kBiF64;                      // L1 L2 1/U0 U1 U2 ta tb
+    float2 v[7];
+    for (int i = 0; i < 7; i++) v[i] = split2(row[i]);
+    out[4 * t] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    out[4 * t + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    out[4 * t + 2] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
+    out[4 * t + 3] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
+}
+
+__global__ void pack_qs_df_kernel(Plan p, float4 *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.N + 8) return;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < p.N - 4) {
+        const float2 q = split2(p.tab.qk[k]), s = split2(p.tab.sk[k]);
+        v = make_float4(q.x, q.y, s.x, s.y);
+    }
+    out[k] = v;
+}
+
+inline unsigned nblocks(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
+
+}  // namespace
+
+size_t df_table_floats(const Plan &p) {
+    return (size_t)p.n_classes * 2 * ((size_t)p.rows_h * 8 + (size_t)p.rows_b * 16) + (size_t)(p.N + 8) * 4;
+}
+
+cudaError_t pack_df(const Plan &p, cudaStream_t s) {
+    float4 *h = reinterpret_cast<float4 *>(p.d_fac_df);
+    float4 *b = h + (size_t)p.n_classes * 2 * p.rows_h * 2;
+    float4 *q = b + (size_t)p.n_classes * 2 * p.rows_b * 4;
+    pack_helm_df_kernel<<<nblocks(p.n_classes * 2 * (long)p.rows_h, 256), 256, 0, s>>>(p, h);
+    pack_bih_df_kernel<<<nblocks(p.n_classes * 2 * (long)p.rows_b, 256), 256, 0, s>>>(p, b);
+    pack_qs_df_kernel<<<nblocks(p.N + 8, 256), 256, 0, s>>>(p, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
+                            cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int *order = (m0 == 0 && count == p.n_modes) ? p.d_order : nullptr;
+    const float4 *h = reinterpret_cast<const float4 *>(p.d_fac_df);
+    const float4 *b = h + (size_t)p.n_classes * 2 * p.rows_h * 2;
+    const float4 *q = b + (size_t)p.n_classes * 2 * p.rows_b * 4;
+    if (problem == SHEN_HELMHOLTZ)
+        helm_df_kernel<<<nblocks(2 * count, 128), 128, 0, s>>>(p, order, m0, count, f, u, h);
+    else
+        bih_df_kernel<<<nblocks(2 * count, 128), 128, 0, s>>>(p, order, m0, count, f, u, b, q);
+    return cudaGetLastError();
+}
+
+}  // namespace shen

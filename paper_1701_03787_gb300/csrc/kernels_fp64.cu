@@ -10,128 +10,31 @@
 // parts share the factors and run side by side in the thread.  The forward sweep
 // writes y into the output column, the backward sweep reads it back in reverse and
 // overwrites it with u, so no scratch memory is needed and u == f works.
-#include "shen_internal.h"
+#include "chains.cuh"
 
 namespace shen {
 namespace {
 
-__device__ __forceinline__ double2 ld2(const double *p, long idx) {
-    return reinterpret_cast<const double2 *>(p)[idx];
-}
-__device__ __forceinline__ void st2(double *p, long idx, double2 v) {
-    reinterpret_cast<double2 *>(p)[idx] = v;
-}
-__device__ __forceinline__ void flag_error(int *err, long cls) {
-    atomicExch(err, 1);
-    atomicMin(err + 1, (int)cls);
-}
-__device__ __forceinline__ bool bad_pivot(double v) { return !(fabs(v) > 0.0) || !isfinite(v); }
+using chains::ld2;
+using chains::st2;
 
-// ---------------------------------------------------------------- factorisation
-
-// Helmholtz, per parity chain:  M = alpha B - A restricted to k = 2i + p:
-//   M_{i,i-1} = -h (h = alpha pi/2),  M_ii = alpha B_kk - A_kk,
-//   M_{i,i+1} = -h + t_i,  M_{i,j>=i+2} = t_i  with t_i = -A_tail(k) = 4 pi (k+1).
-// Doolittle without pivoting: l_i = M_{i,i-1}/U0_{i-1}; U_i* = M_i* - l_i U_{i-1,*};
-// the tail and the superdiagonal stay constant-offset: U1_i = U2_i - h.
 __global__ void factor_helmholtz_kernel(Plan p) {
-    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (tid >= 2 * p.n_classes) return;
     const long cls = tid >> 1;
     const int par = (int)(tid & 1);
-    const int n = p.N - 2;
-    const int rows = (n - par + 1) / 2;
-    const double alpha = p.d_class_z2[cls] + p.c;
-    const double h = alpha * kPi / 2;
-    double *F = p.d_fac_h + ((cls * 2 + par) * (long)p.rows_h) * kHelmF64;
-    double U0 = 0, U2 = 0;
-    for (int i = 0; i < rows; i++) {
-        const int k = 2 * i + par;
-        const double t = -p.tab.adt[k];
-        const double Mii = alpha * p.tab.bd0[k] - p.tab.ad0[k];
-        double l = 0.0;
-        if (i == 0) {
-            U0 = Mii;
-            U2 = t;
-        } else {
-            l = -h / U0;
-            const double U1prev = U2 - h;
-            U0 = Mii - l * U1prev;
-            U2 = t - l * U2;
-        }
-        if (bad_pivot(U0)) flag_error(p.d_err, cls);
-        F[i * kHelmF64 + 0] = 1.0 / U0;
-        F[i * kHelmF64 + 1] = U2;
-        F[i * kHelmF64 + 2] = l;
-        F[i * kHelmF64 + 3] = 0.0;
-    }
-    for (int i = rows; i < p.rows_h; i++)
-        for (int v = 0; v < kHelmF64; v++) F[i * kHelmF64 + v] = 0.0;
+    chains::factor_helm_chain(p.tab, p.N, p.d_class_z2[cls], p.c, par,
+                              p.d_fac_h + ((cls * 2 + par) * (long)p.rows_h) * kHelmF64, p.rows_h, p.d_err, cls);
 }
 
-// Biharmonic, per parity chain (k = 2i + p), H = Q + ca A + cb B:
-//   H_{i,i-2} = cb B_{k,k-4}; H_{i,i-1} = ca A_{k,k-2} + cb B_{k,k-2};
-//   H_ii = Q_kk + ca A_kk + cb B_kk; H_{i,i+1} = Q_{k,k+2} + ca A_{k,k+2} + cb B_{k,k+2};
-//   H_{i,i+2} = Q_{k,k+4} + cb B_{k,k+4};  H_{i,j>=i+3} = p_k q_j + r_k s_j.
-// Algorithm LUbiharmonic row update, with rows i-1, i-2 beyond their three stored
-// values taken from Eq. ab (tail T_m(j) = ta_m q_j + tb_m s_j), and ReduceAB for ta, tb.
 __global__ void factor_biharmonic_kernel(Plan p) {
-    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (tid >= 2 * p.n_classes) return;
     const long cls = tid >> 1;
     const int par = (int)(tid & 1);
-    const int n = p.N - 4;
-    const int rows = (n - par + 1) / 2;
-    const double z2 = p.d_class_z2[cls];
-    const double ca = -(2.0 * z2 + p.c);
-    const double cb = z2 * (z2 + p.c);
-    const RowTables &T = p.tab;
-    double *F = p.d_fac_b + ((cls * 2 + par) * (long)p.rows_b) * kBiF64;
-    // state of rows i-1 (suffix 1) and i-2 (suffix 2)
-    double U0_1 = 0, U1_1 = 0, U2_1 = 0, ta_1 = 0, tb_1 = 0;
-    double U0_2 = 0, U1_2 = 0, U2_2 = 0, ta_2 = 0, tb_2 = 0;
-    for (int i = 0; i < rows; i++) {
-        const int k = 2 * i + par;
-        auto q = [&](int kk) { return T.qk[kk]; };
-        auto s = [&](int kk) { return T.sk[kk]; };
-        double L2 = 0.0, L1 = 0.0;
-        if (i >= 2) L2 = cb * T.bb4[k - 4] / U0_2;
-        if (i >= 1) {
-            double t = ca * T.abm[k] + cb * T.bb2[k - 2];
-            if (i >= 2) t -= L2 * U1_2;               // U_{i-2,i-1}
-            L1 = t / U0_1;
-        }
-        double U0 = T.qb0[k] + ca * T.ab0[k] + cb * T.bb0[k];
-        if (i >= 2) U0 -= L2 * U2_2;                   // U_{i-2,i}
-        if (i >= 1) U0 -= L1 * U1_1;                   // U_{i-1,i}
-        double U1 = 0.0, U2 = 0.0;
-        if (i + 1 < rows) {
-            const int k1 = k + 2;
-            U1 = T.pk[k] * q(k1) + T.rk[k] * s(k1) + ca * T.abp[k] + cb * T.bb2[k];
-            if (i >= 2) U1 -= L2 * (ta_2 * q(k1) + tb_2 * s(k1));   // U_{i-2,i+1}: tail
-            if (i >= 1) U1 -= L1 * U2_1;                              // U_{i-1,i+1}
-        }
-        if (i + 2 < rows) {
-            const int k2 = k + 4;
-            U2 = T.pk[k] * q(k2) + T.rk[k] * s(k2) + cb * T.bb4[k];
-            if (i >= 2) U2 -= L2 * (ta_2 * q(k2) + tb_2 * s(k2));   // U_{i-2,i+2}: tail
-            if (i >= 1) U2 -= L1 * (ta_1 * q(k2) + tb_1 * s(k2));   // U_{i-1,i+2}: tail
-        }
-        double ta = T.pk[k], tb = T.rk[k];
-        if (i >= 1) { ta -= L1 * ta_1; tb -= L1 * tb_1; }
-        if (i >= 2) { ta -= L2 * ta_2; tb -= L2 * tb_2; }
-        if (bad_pivot(U0)) flag_error(p.d_err, cls);
-        double *row = F + i * kBiF64;
-        row[0] = L1; row[1] = L2; row[2] = 1.0 / U0; row[3] = U1;
-        row[4] = U2; row[5] = (i + 3 < rows) ? ta : 0.0; row[6] = (i + 3 < rows) ? tb : 0.0; row[7] = 0.0;
-        U0_2 = U0_1; U1_2 = U1_1; U2_2 = U2_1; ta_2 = ta_1; tb_2 = tb_1;
-        U0_1 = U0; U1_1 = U1; U2_1 = U2; ta_1 = ta; tb_1 = tb;
-    }
-    for (int i = rows; i < p.rows_b; i++)
-        for (int v = 0; v < kBiF64; v++) F[i * kBiF64 + v] = 0.0;
+    chains::factor_bih_chain(p.tab, p.N, p.d_class_z2[cls], p.c, par,
+                             p.d_fac_b + ((cls * 2 + par) * (long)p.rows_b) * kBiF64, p.rows_b, p.d_err, cls);
 }
-
-// ---------------------------------------------------------------------- solves
 
 struct WorkItem {
     long mode;   // global mode index
@@ -156,91 +59,19 @@ __global__ void __launch_bounds__(128) solve_helmholtz_fp64_kernel(Plan p, const
                                                                    long count, const double *f, double *u) {
     WorkItem w;
     if (!work_item(p, order, m0, count, w)) return;
-    const int N = p.N, n = N - 2, par = w.par;
-    const int rows = (n - par + 1) / 2;
-    const long base = w.col * N;
     const double h = (p.d_class_z2[w.cls] + p.c) * kPi / 2;
-    const double *F = p.d_fac_h + ((long)(w.cls * 2 + par) * p.rows_h) * kHelmF64;
-    // forward elimination: y_i = f_i - l_i y_{i-1}
-    double2 y = make_double2(0.0, 0.0);
-    for (int i = 0; i < rows; i++) {
-        const long e = base + 2 * i + par;
-        const double l = F[i * kHelmF64 + 2];
-        const double2 fi = ld2(f, e);
-        y.x = fma(-l, y.x, fi.x);
-        y.y = fma(-l, y.y, fi.y);
-        st2(u, e, y);
-    }
-    // back substitution: u_i = (y_i + h u_{i+1} - U2_i S_{i+1}) / U0_i, S_{i+1} = sum_{j>i} u_j
-    double2 un = make_double2(0.0, 0.0), S = make_double2(0.0, 0.0);
-    for (int i = rows - 1; i >= 0; i--) {
-        const long e = base + 2 * i + par;
-        const double2 inv_u2 = *reinterpret_cast<const double2 *>(F + i * kHelmF64);   // 32-byte rows
-        const double2 yi = ld2(u, e);
-        double2 t;
-        t.x = fma(-inv_u2.y, S.x, fma(h, un.x, yi.x));
-        t.y = fma(-inv_u2.y, S.y, fma(h, un.y, yi.y));
-        un.x = inv_u2.x * t.x;
-        un.y = inv_u2.x * t.y;
-        S.x += un.x;
-        S.y += un.y;
-        st2(u, e, un);
-    }
-    if (par == 0) {
-        st2(u, base + n, make_double2(0.0, 0.0));
-        st2(u, base + n + 1, make_double2(0.0, 0.0));
-    }
+    const long off = 2 * w.col * p.N;
+    chains::solve_helm_fp64_chain(p.N, w.par, f + off, u + off,
+                                  p.d_fac_h + ((long)(w.cls * 2 + w.par) * p.rows_h) * kHelmF64, h);
 }
 
 __global__ void __launch_bounds__(128) solve_biharmonic_fp64_kernel(Plan p, const int *order, long m0,
                                                                     long count, const double *f, double *u) {
     WorkItem w;
     if (!work_item(p, order, m0, count, w)) return;
-    const int N = p.N, n = N - 4, par = w.par;
-    const int rows = (n - par + 1) / 2;
-    const long base = w.col * N;
-    const double *F = p.d_fac_b + ((long)(w.cls * 2 + par) * p.rows_b) * kBiF64;
-    const double *qk = p.tab.qk, *sk = p.tab.sk;
-    // forward elimination: y_i = f_i - L1_i y_{i-1} - L2_i y_{i-2}
-    double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);
-    for (int i = 0; i < rows; i++) {
-        const long e = base + 2 * i + par;
-        const double2 L = *reinterpret_cast<const double2 *>(F + i * kBiF64);
-        const double2 fi = ld2(f, e);
-        double2 y;
-        y.x = fma(-L.y, y2.x, fma(-L.x, y1.x, fi.x));
-        y.y = fma(-L.y, y2.y, fma(-L.x, y1.y, fi.y));
-        st2(u, e, y);
-        y2 = y1;
-        y1 = y;
-    }
-    // back substitution (Algorithm LUSolveBiharmonic):
-    //   u_i = (y_i - U1_i u_{i+1} - U2_i u_{i+2} - ta_i Sq - tb_i Ss) / U0_i,
-    //   Sq = sum_{j>=i+3} q_j u_j, Ss = sum_{j>=i+3} s_j u_j (running sums per parity)
-    double2 u1 = make_double2(0.0, 0.0), u2 = u1, u3 = u1, Sq = u1, Ss = u1;
-    for (int i = rows - 1; i >= 0; i--) {
-        const long e = base + 2 * i + par;
-        if (i + 3 < rows) {
-            const int k3 = 2 * (i + 3) + par;
-            const double q = qk[k3], s = sk[k3];
-            Sq.x = fma(q, u3.x, Sq.x); Sq.y = fma(q, u3.y, Sq.y);
-            Ss.x = fma(s, u3.x, Ss.x); Ss.y = fma(s, u3.y, Ss.y);
-        }
-        const double2 inv_u1 = *reinterpret_cast<const double2 *>(F + i * kBiF64 + 2);
-        const double2 u2_ta = *reinterpret_cast<const double2 *>(F + i * kBiF64 + 4);
-        const double tb = F[i * kBiF64 + 6];
-        const double2 yi = ld2(u, e);
-        double2 t;
-        t.x = yi.x - inv_u1.y * u1.x - u2_ta.x * u2.x - u2_ta.y * Sq.x - tb * Ss.x;
-        t.y = yi.y - inv_u1.y * u1.y - u2_ta.x * u2.y - u2_ta.y * Sq.y - tb * Ss.y;
-        double2 ui = make_double2(inv_u1.x * t.x, inv_u1.x * t.y);
-        st2(u, e, ui);
-        u3 = u2;
-        u2 = u1;
-        u1 = ui;
-    }
-    if (par == 0)
-        for (int k = n; k < N; k++) st2(u, base + k, make_double2(0.0, 0.0));
+    const long off = 2 * w.col * p.N;
+    chains::solve_bih_fp64_chain(p.N, w.par, f + off, u + off,
+                                 p.d_fac_b + ((long)(w.cls * 2 + w.par) * p.rows_b) * kBiF64, p.tab.qk, p.tab.sk);
 }
 
 // ------------------------------------------------------------ RHS operators

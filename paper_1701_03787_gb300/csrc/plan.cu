@@ -29,9 +29,12 @@ namespace {
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+
+namespace shen {
 // Row tables of the Galerkin matrices for N Chebyshev modes (Chebyshev-Gauss scalar
 // product, so c_0 = 2 and c_k = 1 for k > 0 including k = N - 1).
-void build_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride) {
+void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride) {
     const double pi = kPi;
     stride = N;
     h.assign((size_t)16 * N, 0.0);
@@ -63,6 +66,9 @@ void build_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &s
         h32[N + k] = (float)sk[k];
     }
 }
+}  // namespace shen
+
+namespace {
 
 void free_plan(Plan &p) {
     cudaFree(p.d_class_z2);
@@ -75,6 +81,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_fac_h32);
     cudaFree(p.d_fac_b32);
     cudaFree(p.d_err);
+    cudaFree(p.d_fac_df);
     p = Plan{};
 }
 
@@ -122,7 +129,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     std::vector<double> tab;
     std::vector<float> tab32;
     int stride = 0;
-    build_tables(N, tab, tab32, stride);
+    build_row_tables(N, tab, tab32, stride);
 
     cudaStream_t s = as_stream(stream);
     auto fail = [&](shen_status st) {
@@ -167,12 +174,16 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
 
     PLAN_TRY(launch_factor_helmholtz(p, s));
     PLAN_TRY(launch_factor_biharmonic(p, s));
+    // float-float copies of the factors for the float-float sweeps
+    PLAN_TRY(dalloc(&p.d_fac_df, df_table_floats(p), B));
+    PLAN_TRY(pack_df(p, s));
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.R_h = helm_mixed_R(N);
     if (p.R_h > 0) {
         PLAN_TRY(dalloc(&p.d_fac_h32, (size_t)p.n_classes * 2 * p.R_h * 16 * 2, B));
         PLAN_TRY(pack_helm_f32(p, p.R_h, reinterpret_cast<float2 *>(p.d_fac_h32), s));
     }
+
     int err_host[2];
     PLAN_TRY(cudaMemcpyAsync(err_host, p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost, s));
     PLAN_TRY(cudaStreamSynchronize(s));
@@ -192,10 +203,11 @@ bool overlap_ok(const double *a, const double *b, long n_doubles) {
 }
 
 shen_status check_precision(const Plan &p, int problem, int precision) {
-    if (precision == SHEN_FP64) return SHEN_OK;
+    if (precision == SHEN_FP64 || precision == SHEN_DF) return SHEN_OK;
     if (precision < SHEN_FP32_R1 || precision > SHEN_DF_R2) return SHEN_ERR_ARG;
-    if (problem == SHEN_HELMHOLTZ && (precision == SHEN_FP32_R1 || precision == SHEN_DF_R1) && p.R_h > 0)
-        return SHEN_OK;
+    const bool r1 = precision == SHEN_FP32_R1 || precision == SHEN_DF_R1;
+    if (problem == SHEN_HELMHOLTZ && r1 && p.R_h > 0) return SHEN_OK;
+
     return SHEN_ERR_UNSUPPORTED;
 }
 
@@ -212,6 +224,8 @@ shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, cons
     if (count == 0) return SHEN_OK;
     if (precision == SHEN_FP64) {
         SHEN_CUDA_TRY(launch_solve_fp64(p, problem, m0, count, f, u, as_stream(stream)));
+    } else if (precision == SHEN_DF) {
+        SHEN_CUDA_TRY(launch_solve_df(p, problem, m0, count, f, u, as_stream(stream)));
     } else {
         SHEN_CUDA_TRY(launch_helm_mixed(p, precision == SHEN_DF_R1, m0, count, f, u, as_stream(stream)));
     }

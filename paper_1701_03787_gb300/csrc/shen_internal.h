@@ -52,6 +52,8 @@ struct Plan {
     float *d_fac_h32 = nullptr, *d_fac_b32 = nullptr;
     int *d_err = nullptr;                 // [2]: flag, first bad class
     int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
+    float *d_fac_df = nullptr;            // float-float factor tables (Helmholtz, biharmonic, per-N q/s)
+
     long long device_bytes = 0;
 };
 
@@ -68,6 +70,12 @@ int helm_mixed_R(int N);                       // rows per lane for N (0: unsupp
 cudaError_t pack_helm_f32(const Plan &p, int R, float2 *out, cudaStream_t s);
 cudaError_t launch_helm_mixed(const Plan &p, bool dfres, long m0, long count, const double *f, double *u,
                               cudaStream_t s);
+
+// kernels_df.cu
+size_t df_table_floats(const Plan &p);
+cudaError_t pack_df(const Plan &p, cudaStream_t s);
+cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
+                            cudaStream_t s);
 
 }  // namespace shen
 

@@ -48,3 +48,32 @@ def grid_modes(Nx, Nz):
     nxh = Nx // 2 + 1
     return {"mean": 0, "kz_nyquist": Nz // 2, "kx_nyquist": (nxh - 1) * Nz,
             "corner": (nxh - 1) * Nz + Nz // 2, "last": nxh * Nz - 1}
+
+
+def batch_instances(n_inst, seed, Ns=(64, 96, 128, 256, 512), grids=(16, 32, 64),
+                    nu_range=(1e-4, 1e-2), dt_range=(1e-4, 1e-2)):
+    """Instance list of the batching workload: N uniform over Ns, Nx and Nz i.i.d. uniform
+    over grids, nu log-uniform and dt uniform over the given ranges (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    out = []
+    for _ in range(n_inst):
+        out.append({"N": int(rng.choice(Ns)), "Nx": int(rng.choice(grids)), "Nz": int(rng.choice(grids)),
+                    "nu": float(np.exp(rng.uniform(np.log(nu_range[0]), np.log(nu_range[1])))),
+                    "dt": float(rng.uniform(dt_range[0], dt_range[1]))})
+    return out
+
+
+def batch_rhs_torch(offsets, instances, seed, device="cuda"):
+    """Batched field (flat complex128) with each instance's block drawn as rhs_torch."""
+    import torch
+    out = torch.empty(offsets[-1], dtype=torch.complex128, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    for i, inst in enumerate(instances):
+        N = inst["N"]
+        n = (offsets[i + 1] - offsets[i]) // N
+        w = torch.as_tensor(spectrum(N), device=device)
+        re = torch.randn((n, N), generator=g, device=device, dtype=torch.float64) * w
+        im = torch.randn((n, N), generator=g, device=device, dtype=torch.float64) * w
+        out[offsets[i]:offsets[i + 1]] = torch.complex(re, im).reshape(-1)
+    return out
