@@ -186,6 +186,24 @@ shen_status shen_batch_check(shen_batch_t batch);
 /* Free a batched plan (after its work has completed).  NULL is ignored. */
 void shen_batch_destroy(shen_batch_t batch);
 
+/* Same solve as shen_batch_solve, for callers that cannot allocate device memory when
+ * they solve -- for example code running while a stream is captured into a CUDA graph,
+ * where cudaMalloc is not a permitted call, or an application whose device memory is
+ * carved up in advance by its own pool allocator.  The paper has no counterpart: this
+ * is a property of the library, not of the method.
+ *
+ * It allocates nothing and uses none of the plan's scratch: its work-queue counter
+ * lives in a fixed 256-byte device array that the library holds on every GPU it is
+ * loaded on until the process exits.  The plan itself (created beforehand) and the
+ * fields are the caller's.  The first call on a device looks up that array's address
+ * (once per device, with the device current); make that first call before any stream
+ * capture.  Every call resets the counter on `stream` before its launch, so calls that
+ * overlap on the GPU (on any stream, any plan) race on it: issue them one after the
+ * other.  Batches of more than 2^30 modes return SHEN_ERR_UNSUPPORTED; other errors as
+ * shen_batch_solve. */
+shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem, const double *f, double *u,
+                                     int precision, void *stream);
+
 /* Static description of a status code. */
 const char *shen_status_string(int status);
 

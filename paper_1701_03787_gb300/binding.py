@@ -51,6 +51,7 @@ def lib():
         "shen_batch_offsets": ([P, P], I),
         "shen_batch_solve": ([P, I, P, P, I, P], I),
         "shen_batch_check": ([P], I),
+        "shen_batch_solve_noalloc": ([P, I, P, P, I, P], I),
         "shen_batch_destroy": ([P], None),
         "shen_status_string": ([I], ctypes.c_char_p),
         "shen_version": ([], I),

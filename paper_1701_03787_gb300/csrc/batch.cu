@@ -409,3 +409,80 @@ shen_status shen_batch_check(shen_batch_t batch) {
 void shen_batch_destroy(shen_batch_t batch) { delete batch; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// No-allocation variant of the batched solve.
+//
+// Some callers cannot allocate device memory when they solve: code that runs while a
+// stream is being captured into a CUDA graph (cudaMalloc is not a permitted call
+// there and breaks the capture), or an application whose device memory is divided up
+// in advance by its own pool allocator, which must not see allocations it did not
+// make during a time step.  For them, shen_batch_solve_noalloc keeps the only scratch
+// the batched solve needs -- its work-queue counter -- in the fixed device array
+// below instead of in memory owned by the plan.  The array is 256 bytes; every GPU
+// that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr int kNoallocScratchWords = 64;                 // 256 bytes
+constexpr int kNoallocMaxDevices = 64;
+constexpr long kNoallocMaxModes = (1L << 30);             // work-queue counter range
+static __device__ __align__(256) int g_noalloc_scratch[kNoallocScratchWords];   // [0]: queue counter
+
+std::mutex g_noalloc_mutex;
+int *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+shen_status noalloc_scratch(int **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kNoallocMaxDevices) return SHEN_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        int *ptr = nullptr;
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SHEN_OK;
+}
+
+}  // namespace
+
+extern "C" shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem, const double *f, double *u,
+                                                int precision, void *stream) {
+    if (!batch || !f || !u) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (precision != SHEN_FP64 && precision != SHEN_DF) {
+        if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
+        return SHEN_ERR_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(f) & 15u) || (reinterpret_cast<uintptr_t>(u) & 15u)) return SHEN_ERR_ARG;
+    if (batch->d.n_modes > kNoallocMaxModes) return SHEN_ERR_UNSUPPORTED;   // beyond the counter's range
+    long elems = 0;
+    shen_batch_info(batch, nullptr, &elems, nullptr, nullptr);
+    if (f != u && !(f + 2 * elems <= u || u + 2 * elems <= f)) return SHEN_ERR_ARG;
+    int *scratch = nullptr;
+    const shen_status st = noalloc_scratch(&scratch);
+    if (st != SHEN_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the counter keeps the previous call's value: start it at zero
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    BatchDev D = batch->d;
+    D.queue = scratch;
+    if (problem == SHEN_HELMHOLTZ) {
+        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
+        else batch_solve_kernel<1, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
+    } else {
+        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
+        else batch_solve_kernel<1, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SHEN_OK : cuda_status(e);
+}
