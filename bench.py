@@ -28,8 +28,10 @@ WORKLOADS = {
     "retau180": dict(N=128, Nx=128, Nz=128, nu=1 / 180, dt=5e-4),
     "n1024": dict(N=1024, Nx=1024, Nz=1024, nu=1 / 2000, dt=1e-4),
     "large": dict(N=1536, Nx=2048, Nz=1536, nu=1 / 2000, dt=5e-5),
-    # profiling case: N = 1024 columns on a 128 x 128 grid (136 MB per field, > L2)
+    # profiling cases: N = 1024 columns on a 128 x 128 grid (136 MB per field, > L2; under
+    # one wave of blocks) and on a 256 x 256 grid (540 MB per field, several waves)
     "n1024s": dict(N=1024, Nx=128, Nz=128, nu=1 / 2000, dt=1e-4),
+    "n1024q": dict(N=1024, Nx=256, Nz=256, nu=1 / 2000, dt=1e-4),
     # 4096 channels with uneven N (64..512), grids 16..64, nu in [1e-4, 1e-2], dt in [1e-4, 1e-2]
     "batch": dict(n_inst=4096, seed=5),
 }
@@ -162,7 +164,7 @@ def oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined_modes):
 
 
 # Fastest path per problem that meets the 1e-10 bar (see the GPU parity tests).
-AUTO_PRECISION = {"helmholtz": "df_r1", "biharmonic": "fp64"}
+AUTO_PRECISION = {"helmholtz": "df_r1", "biharmonic": "df"}
 
 
 def resolve_precision(spec):
@@ -200,6 +202,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--streams", type=int, default=1, choices=[1, 2],
+                    help="2: run the two solves concurrently on two streams")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -245,15 +249,31 @@ def main():
         plan.helmholtz_solve = lambda f, u, precision, stream: plan.solve("helmholtz", f, u, precision, stream)
         plan.biharmonic_solve = lambda f, u, precision, stream: plan.solve("biharmonic", f, u, precision, stream)
 
+    # The two solves are independent: run them on two streams that fork from and join
+    # back into `stream` (the Helmholtz float32/float-float kernels and the float64
+    # biharmonic kernel use different pipes, so they overlap).
+    s_h, s_b = torch.cuda.Stream(), torch.cuda.Stream()
+    fork, join_h, join_b = (torch.cuda.Event() for _ in range(3))
+
     def step(ph=prec["helmholtz"], pb=prec["biharmonic"]):
-        plan.helmholtz_solve(f_h, u_h, precision=ph, stream=stream)
-        plan.biharmonic_solve(f_b, u_b, precision=pb, stream=stream)
+        if args.streams == 1:
+            plan.helmholtz_solve(f_h, u_h, precision=ph, stream=stream)
+            plan.biharmonic_solve(f_b, u_b, precision=pb, stream=stream)
+            return
+        fork.record(stream)
+        s_h.wait_event(fork)
+        s_b.wait_event(fork)
+        plan.helmholtz_solve(f_h, u_h, precision=ph, stream=s_h)
+        plan.biharmonic_solve(f_b, u_b, precision=pb, stream=s_b)
+        join_h.record(s_h)
+        join_b.record(s_b)
+        stream.wait_event(join_h)
+        stream.wait_event(join_b)
 
     for _ in range(args.warmup):
         step()
     stream.synchronize()
-    # per-kernel durations (events on the launching stream)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # timed region: K whole steps, CUDA events on `stream`
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     if pg:
@@ -261,16 +281,21 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel durations, each kernel alone on `stream` (events on the launching stream)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     for s in range(args.steps):
         ev[s][0].record(stream)
         plan.helmholtz_solve(f_h, u_h, precision=prec["helmholtz"], stream=stream)
         ev[s][1].record(stream)
         plan.biharmonic_solve(f_b, u_b, precision=prec["biharmonic"], stream=stream)
         ev[s][2].record(stream)
-    e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
     t_h = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     t_b = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     if pg:
@@ -291,7 +316,8 @@ def main():
             with torch.cuda.stream(stream):
                 f_h.copy_(hf_h, non_blocking=True)
                 f_b.copy_(hf_b, non_blocking=True)
-                step()
+            step()
+            with torch.cuda.stream(stream):
                 hu.copy_(u_h, non_blocking=True)
                 hu2.copy_(u_b, non_blocking=True)
         e2e_step()
@@ -337,6 +363,7 @@ def main():
             "dtype": "f64" if set(prec.values()) == {"fp64"} else "f32 sweeps + refinement (io f64)",
             "data": "synthetic", "precision": prec,
             "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes, "rows": rows,
+                       "streams": args.streams,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e}

@@ -147,10 +147,11 @@ void shen_plan_destroy(shen_plan_t plan);
  * box).  The batched field stores instance i's mode-major columns (n_modes_i * N_i
  * complex values) after those of instances 0 .. i-1; shen_batch_offsets returns the
  * complex-element offset of each instance.  The solve is one persistent launch whose
- * warps take chunks of modes from a work queue ordered by decreasing N (the queue
- * counter is plan-owned device memory, reset by an asynchronous memset at every call,
- * so calls on the same plan must not overlap on the GPU).  Both calls enqueue on
- * `stream` only (a stream capture records them). */
+ * warps take chunks of modes from a work queue ordered by decreasing N (one queue
+ * counter per problem, plan-owned device memory, reset by an asynchronous memset at
+ * every call: a Helmholtz and a biharmonic solve of the same plan may overlap on the
+ * GPU, two solves of the same problem on the same plan must not).  The solve enqueues
+ * on `stream` only. */
 typedef struct shen_batch_s *shen_batch_t;
 
 typedef struct {

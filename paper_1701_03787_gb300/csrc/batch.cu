@@ -74,14 +74,14 @@ __global__ void batch_factor_kernel(BatchDev b) {
         Dh[2 * i] = make_float4(a.x, a.y, bb.x, bb.y);
         Dh[2 * i + 1] = make_float4(l.x, l.y, 0.f, 0.f);
     }
-    for (int i = 0; i < in.rows_b; i++) {
+    for (int i = 0; i < in.rows_b; i++) {          // rows_b (L1, L2), then 3 rows_b float4
         const double *r = Fb + i * kBiF64;
         float2 v[7];
         for (int q = 0; q < 7; q++) v[q] = split(r[q]);
-        Db[4 * i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-        Db[4 * i + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-        Db[4 * i + 2] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
-        Db[4 * i + 3] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
+        Db[i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        Db[in.rows_b + 3 * i] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+        Db[in.rows_b + 3 * i + 1] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
+        Db[in.rows_b + 3 * i + 2] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
     }
 }
 
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                  b.fac_b + (cl.fb + (long)par * in.rows_b) * kBiF64,
                                                  b.tabs[in.tab].qk, b.tabs[in.tab].sk);
                 } else {
-                    chains::solve_bih_df_chain(in.N, par, f + off, u + off,
-                                               b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4,
+                    const float4 *F = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
+                    chains::solve_bih_df_chain(in.N, par, f + off, u + off, F, F + in.rows_b,
                                                b.qs_df + (size_t)in.tab * b.qs_stride);
                 }
             }
@@ -156,7 +156,7 @@ struct shen_batch_s {
     std::vector<void *> allocs;
     RowTables *d_tabs = nullptr;
     long long device_bytes = 0;
-    int grid = 0;
+    int grid = 0;                                // persistent grid
     ~shen_batch_s() {
         for (void *p : allocs) cudaFree(p);
     }
@@ -312,7 +312,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
     B_TRY(balloc(b, &D.fac_b, (size_t)fb * kBiF64));
     B_TRY(balloc(b, &D.fdf_h, (size_t)fh * 2));
     B_TRY(balloc(b, &D.fdf_b, (size_t)fb * 4));
-    B_TRY(balloc(b, &D.queue, 1));
+    B_TRY(balloc(b, &D.queue, 2));                   // one work-queue counter per problem
     B_TRY(balloc(b, &D.err, 2));
     B_TRY(cudaMemcpyAsync(d_tabs, tabs_h.data(), tabs_h.size() * sizeof(RowTables), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemcpyAsync(d_inst, inst.data(), inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s));
@@ -384,9 +384,10 @@ shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, d
     shen_batch_info(batch, nullptr, &elems, nullptr, nullptr);
     if (f != u && !(f + 2 * elems <= u || u + 2 * elems <= f)) return SHEN_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(batch->d.queue, 0, sizeof(int), s);
+    BatchDev D = batch->d;
+    D.queue = batch->d.queue + problem;        // separate counters: a Helmholtz and a biharmonic
+    cudaError_t e = cudaMemsetAsync(D.queue, 0, sizeof(int), s);   // solve may overlap
     if (e != cudaSuccess) return cuda_status(e);
-    const BatchDev &D = batch->d;
     if (problem == SHEN_HELMHOLTZ) {
         if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
         else batch_solve_kernel<1, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);

@@ -269,55 +269,79 @@ __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, d
                                            F2 h) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
-    // forward elimination y_i = f_i - l_i y_{i-1}; rows are loaded PB at a time ahead of
-    // the stores so the loads overlap (the stores may alias f when u == f)
+    // Forward elimination y_i = f_i - l_i y_{i-1}.  Rows are fetched PB at a time into two
+    // register buffers: the next block's loads are issued before the current block is
+    // computed (software pipelining), and all loads of a block precede its stores (which
+    // may alias f when u == f).
     constexpr int PB = 8;
     CF2 y{F2{0.f, 0.f}, F2{0.f, 0.f}};
-    for (int i0 = 0; i0 < rows; i0 += PB) {
-        double2 fb[PB];
-        float4 lb[PB];
+    {
+        double2 fa[PB], fb[PB];
+        float4 la[PB], lb[PB];
+        auto load = [&](double2 (&fx)[PB], float4 (&lx)[PB], int i0) {
 #pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = min(i0 + q, rows - 1);
-            fb[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
-            lb[q] = F[2 * i + 1];
-        }
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            if (i0 + q < rows) {
-                const F2 l{lb[q].x, lb[q].y};
-                y.re = fnma(l, y.re, df::from_f64(fb[q].x));
-                y.im = fnma(l, y.im, df::from_f64(fb[q].y));
-                store_cf2(ucol, 2 * (i0 + q) + par, y);
+            for (int q = 0; q < PB; q++) {
+                const int i = min(i0 + q, rows - 1);
+                fx[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
+                lx[q] = F[2 * i + 1];
             }
+        };
+        auto run = [&](const double2 (&fx)[PB], const float4 (&lx)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                if (i0 + q < rows) {
+                    const F2 l{lx[q].x, lx[q].y};
+                    y.re = fnma(l, y.re, df::from_f64(fx[q].x));
+                    y.im = fnma(l, y.im, df::from_f64(fx[q].y));
+                    store_cf2(ucol, 2 * (i0 + q) + par, y);
+                }
+            }
+        };
+        load(fa, la, 0);
+        for (int i0 = 0; i0 < rows; i0 += 2 * PB) {
+            load(fb, lb, i0 + PB);
+            run(fa, la, i0);
+            load(fa, la, i0 + 2 * PB);
+            run(fb, lb, i0 + PB);
         }
     }
-    // back substitution u_i = (y_i + h u_{i+1} - U2_i S_{i+1}) / U_ii
+    // back substitution u_i = (y_i + h u_{i+1} - U2_i S_{i+1}) / U_ii (same pipelining)
     CF2 un{F2{0.f, 0.f}, F2{0.f, 0.f}}, S = un;
-    for (int i0 = rows - 1; i0 >= 0; i0 -= PB) {
-        float4 yb[PB], ab[PB];
+    {
+        float4 ya[PB], yb[PB], aa[PB], ab[PB];
+        auto load = [&](float4 (&yx)[PB], float4 (&ax)[PB], int i0) {
 #pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = max(i0 - q, 0);
-            yb[q] = reinterpret_cast<const float4 *>(ucol)[2 * i + par];
-            ab[q] = F[2 * i];
-        }
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            if (i0 - q >= 0) {
-                const F2 inv0{ab[q].x, ab[q].y}, U2{ab[q].z, ab[q].w};
-                const CF2 yi{F2{yb[q].x, yb[q].y}, F2{yb[q].z, yb[q].w}};
-                CF2 t;
-                t.re = fnma(U2, S.re, df::add(yi.re, df::mul(h, un.re)));
-                t.im = fnma(U2, S.im, df::add(yi.im, df::mul(h, un.im)));
-                un.re = df::mul(inv0, t.re);
-                un.im = df::mul(inv0, t.im);
-                un.re = df::fast_two_sum(un.re.hi, un.re.lo);
-                un.im = df::fast_two_sum(un.im.hi, un.im.lo);
-                S.re = df::add(S.re, un.re);
-                S.im = df::add(S.im, un.im);
-                store_f64(ucol, 2 * (i0 - q) + par, un);
+            for (int q = 0; q < PB; q++) {
+                const int i = max(i0 - q, 0);
+                yx[q] = reinterpret_cast<const float4 *>(ucol)[2 * i + par];
+                ax[q] = F[2 * i];
             }
+        };
+        auto run = [&](const float4 (&yx)[PB], const float4 (&ax)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                if (i0 - q >= 0) {
+                    const F2 inv0{ax[q].x, ax[q].y}, U2{ax[q].z, ax[q].w};
+                    const CF2 yi{F2{yx[q].x, yx[q].y}, F2{yx[q].z, yx[q].w}};
+                    CF2 t;
+                    t.re = fnma(U2, S.re, df::add(yi.re, df::mul(h, un.re)));
+                    t.im = fnma(U2, S.im, df::add(yi.im, df::mul(h, un.im)));
+                    un.re = df::mul(inv0, t.re);
+                    un.im = df::mul(inv0, t.im);
+                    un.re = df::fast_two_sum(un.re.hi, un.re.lo);
+                    un.im = df::fast_two_sum(un.im.hi, un.im.lo);
+                    S.re = df::add(S.re, un.re);
+                    S.im = df::add(S.im, un.im);
+                    store_f64(ucol, 2 * (i0 - q) + par, un);
+                }
+            }
+        };
+        load(ya, aa, rows - 1);
+        for (int i0 = rows - 1; i0 >= 0; i0 -= 2 * PB) {
+            load(yb, ab, i0 - PB);
+            run(ya, aa, i0);
+            load(ya, aa, i0 - 2 * PB);
+            run(yb, ab, i0 - PB);
         }
     }
     if (par == 0) {
@@ -326,79 +350,108 @@ __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, d
     }
 }
 
-// Biharmonic: F rows of four float4 (L1, L2) (1/U0, U1) (U2, ta) (tb, 0) as (hi, lo);
-// qs: per-N (q_k, s_k) float-float, indexed by k, zero beyond the unknowns.
-__device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *F,
-                                          const float4 *qs) {
+// Biharmonic float-float chain.  Factors of the chain: Ff[i] = (L1, L2) for the forward
+// elimination and Fb[3 i .. 3 i + 2] = (1/U0, U1) (U2, ta) (tb, 0) for the back
+// substitution, each value as (hi, lo) (separate streams, so each sweep reads only the
+// bytes it uses); qs: per-N (q_k, s_k) float-float by k, zero beyond the unknowns.
+// Rows are fetched PB at a time into two register buffers, the next block's loads
+// issued before the current block is computed; all loads of a block precede its stores
+// (which may alias f when u == f).
+__device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
+                                          const float4 *Fb, const float4 *qs) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
     const F2 zero{0.f, 0.f};
     constexpr int PB = 4;
-    // forward elimination y_i = f_i - L1_i y_{i-1} - L2_i y_{i-2} (loads PB rows ahead)
+    // forward elimination y_i = f_i - L1_i y_{i-1} - L2_i y_{i-2}
     CF2 y1{zero, zero}, y2 = y1;
-    for (int i0 = 0; i0 < rows; i0 += PB) {
-        double2 fb[PB];
-        float4 lb[PB];
+    {
+        double2 fa[PB], fb[PB];
+        float4 la[PB], lb[PB];
+        auto load = [&](double2 (&fx)[PB], float4 (&lx)[PB], int i0) {
 #pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = min(i0 + q, rows - 1);
-            fb[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
-            lb[q] = F[4 * i];
-        }
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            if (i0 + q < rows) {
-                const F2 L1{lb[q].x, lb[q].y}, L2{lb[q].z, lb[q].w};
-                CF2 y;
-                y.re = fnma(L2, y2.re, fnma(L1, y1.re, df::from_f64(fb[q].x)));
-                y.im = fnma(L2, y2.im, fnma(L1, y1.im, df::from_f64(fb[q].y)));
-                store_cf2(ucol, 2 * (i0 + q) + par, y);
-                y2 = y1;
-                y1 = y;
+            for (int q = 0; q < PB; q++) {
+                const int i = min(i0 + q, rows - 1);
+                fx[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
+                lx[q] = Ff[i];
             }
+        };
+        auto run = [&](const double2 (&fx)[PB], const float4 (&lx)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                if (i0 + q < rows) {
+                    const F2 L1{lx[q].x, lx[q].y}, L2{lx[q].z, lx[q].w};
+                    CF2 y;
+                    y.re = fnma(L2, y2.re, fnma(L1, y1.re, df::from_f64(fx[q].x)));
+                    y.im = fnma(L2, y2.im, fnma(L1, y1.im, df::from_f64(fx[q].y)));
+                    store_cf2(ucol, 2 * (i0 + q) + par, y);
+                    y2 = y1;
+                    y1 = y;
+                }
+            }
+        };
+        load(fa, la, 0);
+        for (int i0 = 0; i0 < rows; i0 += 2 * PB) {
+            load(fb, lb, i0 + PB);
+            run(fa, la, i0);
+            load(fa, la, i0 + 2 * PB);
+            run(fb, lb, i0 + PB);
         }
     }
     // back substitution: u_i = (y_i - U1 u_{i+1} - U2 u_{i+2} - ta Sq - tb Ss) / U0,
     // Sq = sum_{j >= i+3} q_j u_j, Ss = sum_{j >= i+3} s_j u_j
     CF2 u1{zero, zero}, u2 = u1, u3 = u1, Sq = u1, Ss = u1;
-    for (int i0 = rows - 1; i0 >= 0; i0 -= PB) {
-        float4 yb[PB], bb[PB], cb[PB], db[PB], qb[PB];
+    {
+        float4 ya[PB], yb[PB], ba[PB], bb[PB], ca[PB], cb[PB], da[PB], db[PB], qa[PB], qb[PB];
+        auto load = [&](float4 (&yx)[PB], float4 (&bx)[PB], float4 (&cx)[PB], float4 (&dx)[PB], float4 (&qx)[PB],
+                        int i0) {
 #pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = max(i0 - q, 0);
-            yb[q] = reinterpret_cast<const float4 *>(ucol)[2 * i + par];
-            bb[q] = F[4 * i + 1];
-            cb[q] = F[4 * i + 2];
-            db[q] = F[4 * i + 3];
-            qb[q] = qs[2 * i + par + 6];
-        }
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = i0 - q;
-            if (i >= 0) {
-                if (i + 3 < rows) {
-                    const F2 qq{qb[q].x, qb[q].y}, ss{qb[q].z, qb[q].w};
-                    Sq.re = df::add(Sq.re, df::mul(qq, u3.re));
-                    Sq.im = df::add(Sq.im, df::mul(qq, u3.im));
-                    Ss.re = df::add(Ss.re, df::mul(ss, u3.re));
-                    Ss.im = df::add(Ss.im, df::mul(ss, u3.im));
-                }
-                const F2 inv0{bb[q].x, bb[q].y}, U1{bb[q].z, bb[q].w}, U2{cb[q].x, cb[q].y};
-                const F2 ta{cb[q].z, cb[q].w}, tb{db[q].x, db[q].y};
-                const CF2 yi{F2{yb[q].x, yb[q].y}, F2{yb[q].z, yb[q].w}};
-                CF2 t;
-                t.re = fnma(tb, Ss.re, fnma(ta, Sq.re, fnma(U2, u2.re, fnma(U1, u1.re, yi.re))));
-                t.im = fnma(tb, Ss.im, fnma(ta, Sq.im, fnma(U2, u2.im, fnma(U1, u1.im, yi.im))));
-                CF2 ui;
-                ui.re = df::mul(inv0, t.re);
-                ui.im = df::mul(inv0, t.im);
-                ui.re = df::fast_two_sum(ui.re.hi, ui.re.lo);
-                ui.im = df::fast_two_sum(ui.im.hi, ui.im.lo);
-                store_f64(ucol, 2 * i + par, ui);
-                u3 = u2;
-                u2 = u1;
-                u1 = ui;
+            for (int q = 0; q < PB; q++) {
+                const int i = max(i0 - q, 0);
+                yx[q] = reinterpret_cast<const float4 *>(ucol)[2 * i + par];
+                bx[q] = Fb[3 * i];
+                cx[q] = Fb[3 * i + 1];
+                dx[q] = Fb[3 * i + 2];
+                qx[q] = qs[2 * i + par + 6];
             }
+        };
+        auto run = [&](const float4 (&yx)[PB], const float4 (&bx)[PB], const float4 (&cx)[PB],
+                       const float4 (&dx)[PB], const float4 (&qx)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                const int i = i0 - q;
+                if (i >= 0) {
+                    if (i + 3 < rows) {
+                        const F2 qq{qx[q].x, qx[q].y}, ss{qx[q].z, qx[q].w};
+                        Sq.re = df::add(Sq.re, df::mul(qq, u3.re));
+                        Sq.im = df::add(Sq.im, df::mul(qq, u3.im));
+                        Ss.re = df::add(Ss.re, df::mul(ss, u3.re));
+                        Ss.im = df::add(Ss.im, df::mul(ss, u3.im));
+                    }
+                    const F2 inv0{bx[q].x, bx[q].y}, U1{bx[q].z, bx[q].w}, U2{cx[q].x, cx[q].y};
+                    const F2 ta{cx[q].z, cx[q].w}, tb{dx[q].x, dx[q].y};
+                    const CF2 yi{F2{yx[q].x, yx[q].y}, F2{yx[q].z, yx[q].w}};
+                    CF2 t;
+                    t.re = fnma(tb, Ss.re, fnma(ta, Sq.re, fnma(U2, u2.re, fnma(U1, u1.re, yi.re))));
+                    t.im = fnma(tb, Ss.im, fnma(ta, Sq.im, fnma(U2, u2.im, fnma(U1, u1.im, yi.im))));
+                    CF2 ui;
+                    ui.re = df::mul(inv0, t.re);
+                    ui.im = df::mul(inv0, t.im);
+                    ui.re = df::fast_two_sum(ui.re.hi, ui.re.lo);
+                    ui.im = df::fast_two_sum(ui.im.hi, ui.im.lo);
+                    store_f64(ucol, 2 * i + par, ui);
+                    u3 = u2;
+                    u2 = u1;
+                    u1 = ui;
+                }
+            }
+        };
+        load(ya, ba, ca, da, qa, rows - 1);
+        for (int i0 = rows - 1; i0 >= 0; i0 -= 2 * PB) {
+            load(yb, bb, cb, db, qb, i0 - PB);
+            run(ya, ba, ca, da, qa, i0);
+            load(ya, ba, ca, da, qa, i0 - 2 * PB);
+            run(yb, bb, cb, db, qb, i0 - PB);
         }
     }
     if (par == 0)

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, l
     WorkItem w;
     if (!work_item(p, order, m0, count, w)) return;
     const long off = 2 * w.col * p.N;
-    chains::solve_bih_df_chain(p.N, w.par, f + off, u + off, fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4, qs);
+    const float4 *F = fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4;   // rows_b (L1, L2), then 3 rows_b
+    chains::solve_bih_df_chain(p.N, w.par, f + off, u + off, F, F + p.rows_b, qs);
 }
 
 __device__ __forceinline__ float2 split2(double x) {
@@ -65,16 +66,20 @@ __global__ void pack_helm_df_kernel(Plan p, float4 *out) {
     out[2 * t + 1] = make_float4(c.x, c.y, 0.f, 0.f);
 }
 
+// Per chain: rows_b float4 (L1, L2) for the forward elimination, then 3 rows_b float4
+// (1/U0, U1) (U2, ta) (tb, 0) for the back substitution, each value as (hi, lo).
 __global__ void pack_bih_df_kernel(Plan p, float4 *out) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= p.n_classes * 2 * (long)p.rows_b) return;
+    const long chain = t / p.rows_b, i = t % p.rows_b;
     const double *row = p.d_fac_b + t * kBiF64;                      // L1 L2 1/U0 U1 U2 ta tb
     float2 v[7];
-    for (int i = 0; i < 7; i++) v[i] = split2(row[i]);
-    out[4 * t] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    out[4 * t + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-    out[4 * t + 2] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
-    out[4 * t + 3] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
+    for (int q = 0; q < 7; q++) v[q] = split2(row[q]);
+    float4 *Ff = out + chain * p.rows_b * 4, *Fb = Ff + p.rows_b;
+    Ff[i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    Fb[3 * i] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    Fb[3 * i + 1] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
+    Fb[3 * i + 2] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
 }
 
 __global__ void pack_qs_df_kernel(Plan p, float4 *out) {

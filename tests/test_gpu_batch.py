@@ -88,3 +88,25 @@ def test_batch_rejects_bad_descriptors_and_precisions():
         with pytest.raises(ShenError) as e:
             bp.solve("helmholtz", f, precision="df_r1")
         assert e.value.status == 5
+
+
+def test_batch_helmholtz_and_biharmonic_overlap_on_two_streams():
+    """The two problems use separate work-queue counters, so their solves may run
+    concurrently on two streams; each result equals its serial solve."""
+    import torch
+    insts = inputs.batch_instances(64, seed=9)
+    with BatchPlan(insts) as bp:
+        fh = inputs.batch_rhs_torch(bp.offsets, insts, seed=1)
+        fb = inputs.batch_rhs_torch(bp.offsets, insts, seed=2)
+        ref_h = bp.solve("helmholtz", fh, precision="df")
+        ref_b = bp.solve("biharmonic", fb, precision="df")
+        torch.cuda.synchronize()
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        for _ in range(3):
+            uh = torch.empty_like(fh)
+            ub = torch.empty_like(fb)
+            bp.solve("helmholtz", fh, uh, precision="df", stream=s1)
+            bp.solve("biharmonic", fb, ub, precision="df", stream=s2)
+            torch.cuda.synchronize()
+            assert torch.equal(uh, ref_h)
+            assert torch.equal(ub, ref_b)
