@@ -123,6 +123,22 @@ shen_status shen_biharmonic_solve(shen_plan_t plan, const double *f, double *u, 
 shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, long mode_count,
                              const double *f, double *u, int precision, void *stream);
 
+/* Solve every mode of the plan (problem SHEN_HELMHOLTZ / SHEN_BIHARMONIC) for fields
+ * in HOST memory: f_host and u_host hold n_modes * N complex values (u_host == f_host
+ * allowed); page-locked (pinned) host memory gives full copy bandwidth, pageable memory
+ * works more slowly.  The field is streamed through three plan-owned device staging
+ * slots (about 256 MB each, allocated at the first call and counted by
+ * shen_plan_info) in chunks of whole modes; copy-in, solve and copy-out of successive
+ * chunks overlap on internal streams.  The work starts after what is already queued
+ * on `stream`, and `stream` waits for the last copy-out: synchronise `stream` before
+ * reading u_host.  Host arrays must stay valid until then.  Successive calls on one
+ * plan share the staging slots and internal streams: calls issued on two different
+ * caller streams follow each other through the pipeline without draining it between
+ * them.  Calls on one plan must come from one host thread at a time.  Errors as the
+ * device solves. */
+shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
+                            void *stream);
+
 /* Right-hand-side operator: out = R x + beta * y for every mode (R = R_h or R_b by
  * `problem`).  y may be NULL (then beta is ignored).  x, y, out: DEVICE fields;
  * out must not overlap x or y.  float64 arithmetic. */

@@ -43,6 +43,7 @@ def lib():
         "shen_biharmonic_solve": ([P, P, P, I, P], I),
         "shen_solve_modes": ([P, I, Lg, Lg, P, P, I, P], I),
         "shen_rhs_matvec": ([P, I, P, P, D, P, P], I),
+        "shen_solve_host": ([P, I, P, P, I, P], I),
         "shen_plan_info": ([P, P, P, P, P], I),
         "shen_plan_check": ([P, P], I),
         "shen_plan_destroy": ([P], None),
@@ -147,6 +148,14 @@ class Plan:
     def handle(self):
         return self._h
 
+    def info(self):
+        """(n_modes, n_classes, N, device_bytes); device_bytes includes host-solve staging."""
+        n_modes, n_classes, n = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        nbytes = ctypes.c_longlong()
+        check(lib().shen_plan_info(self._h, ctypes.byref(n_modes), ctypes.byref(n_classes), ctypes.byref(n),
+                                   ctypes.byref(nbytes)), "shen_plan_info")
+        return n_modes.value, n_classes.value, n.value, nbytes.value
+
     def close(self):
         if self._h:
             lib().shen_plan_destroy(self._h)
@@ -194,6 +203,21 @@ class Plan:
         _field_ok(u, count, self.N, "u")
         check(lib().shen_solve_modes(self._h, _problem(problem), int(mode_begin), int(count), _ptr(f), _ptr(u),
                                      _prec(precision), _stream(stream)), "shen_solve_modes")
+        return u
+
+    def solve_host(self, problem, f, u=None, precision="fp64", stream=None):
+        """Solve a field held in (preferably pinned) host memory; returns u (host).  The
+        call is asynchronous on `stream` (default: the current stream); synchronise the
+        stream before reading u."""
+        import torch
+        if f.dtype != torch.complex128 or f.is_cuda or not f.is_contiguous() or f.numel() != self.n_modes * self.N:
+            raise ValueError("f must be a contiguous complex128 host tensor of n_modes*N entries")
+        if u is None:
+            u = torch.empty_like(f, pin_memory=f.is_pinned())
+        if u.dtype != torch.complex128 or u.is_cuda or not u.is_contiguous() or u.numel() != f.numel():
+            raise ValueError("u must be a contiguous complex128 host tensor shaped like f")
+        check(lib().shen_solve_host(self._h, _problem(problem), _ptr(f), _ptr(u), _prec(precision),
+                                    _stream(stream)), "shen_solve_host")
         return u
 
     def rhs_matvec(self, problem, x, y=None, beta=0.0, out=None, stream=None):

@@ -211,6 +211,20 @@ shen_status check_precision(const Plan &p, int problem, int precision) {
     return SHEN_ERR_UNSUPPORTED;
 }
 
+}  // namespace
+
+namespace shen {
+// Enqueue the kernel of (problem, precision) for modes [m0, m0 + count).
+cudaError_t launch_solve_range(const Plan &p, int problem, int precision, long m0, long count, const double *f,
+                               double *u, cudaStream_t s) {
+    if (precision == SHEN_FP64) return launch_solve_fp64(p, problem, m0, count, f, u, s);
+    if (precision == SHEN_DF) return launch_solve_df(p, problem, m0, count, f, u, s);
+    return launch_helm_mixed(p, precision == SHEN_DF_R1, m0, count, f, u, s);
+}
+}  // namespace shen
+
+namespace {
+
 shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, const double *f, double *u,
                         int precision, void *stream) {
     if (!plan || !f || !u) return SHEN_ERR_ARG;
@@ -222,13 +236,7 @@ shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, cons
     shen_status ps = check_precision(p, problem, precision);
     if (ps != SHEN_OK) return ps;
     if (count == 0) return SHEN_OK;
-    if (precision == SHEN_FP64) {
-        SHEN_CUDA_TRY(launch_solve_fp64(p, problem, m0, count, f, u, as_stream(stream)));
-    } else if (precision == SHEN_DF) {
-        SHEN_CUDA_TRY(launch_solve_df(p, problem, m0, count, f, u, as_stream(stream)));
-    } else {
-        SHEN_CUDA_TRY(launch_helm_mixed(p, precision == SHEN_DF_R1, m0, count, f, u, as_stream(stream)));
-    }
+    SHEN_CUDA_TRY(launch_solve_range(p, problem, precision, m0, count, f, u, as_stream(stream)));
     return SHEN_OK;
 }
 
@@ -296,7 +304,7 @@ shen_status shen_plan_info(shen_plan_t plan, long *n_modes, long *n_classes, lon
     if (n_modes) *n_modes = plan->p.n_modes;
     if (n_classes) *n_classes = plan->p.n_classes;
     if (N) *N = plan->p.N;
-    if (device_bytes) *device_bytes = plan->p.device_bytes;
+    if (device_bytes) *device_bytes = plan->p.device_bytes + host_pipe_bytes(plan->host);
     return SHEN_OK;
 }
 
@@ -310,8 +318,21 @@ shen_status shen_plan_check(shen_plan_t plan, long *where) {
 
 void shen_plan_destroy(shen_plan_t plan) {
     if (!plan) return;
+    host_pipe_free(plan->host);
     free_plan(plan->p);
     delete plan;
+}
+
+shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
+                            void *stream) {
+    if (!plan || !f_host || !u_host) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    const long nd = 2 * plan->p.n_modes * (long)plan->p.N;
+    if (!overlap_ok(f_host, u_host, nd)) return SHEN_ERR_ARG;
+    const shen_status ps = check_precision(plan->p, problem, precision);
+    if (ps != SHEN_OK) return ps;
+    SHEN_CUDA_TRY(host_solve(plan->p, plan->host, problem, precision, f_host, u_host, as_stream(stream)));
+    return SHEN_OK;
 }
 
 const char *shen_status_string(int status) {

@@ -79,6 +79,15 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
 
 }  // namespace shen
 
+namespace shen {
+struct HostPipe;
+void host_pipe_free(HostPipe *h);
+long long host_pipe_bytes(const HostPipe *h);
+cudaError_t host_solve(Plan &p, HostPipe *&h, int problem, int precision, const double *f_host, double *u_host,
+                       cudaStream_t user);
+}  // namespace shen
+
 struct shen_plan_s {
     shen::Plan p;
+    shen::HostPipe *host = nullptr;   // staging for solves on host fields (created on first use)
 };
