@@ -233,14 +233,28 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
                 z[ix * d.Nz + iz] = {kx * kx + kz * kz, ix * d.Nz + iz};
             }
         std::sort(z.begin(), z.end());
+        std::vector<int> lc((size_t)b.n_modes);       // mode -> distinct-z2 group
+        std::vector<double> lz;
         for (long w = 0; w < b.n_modes; w++) {
-            if (w == 0 || z[w].first != z[w - 1].first) {
-                cls.push_back(BatchCls{z[w].first, i, fh, fb});
-                fh += 2L * b.rows_h;
-                fb += 2L * b.rows_b;
-            }
-            mode_inst[b.mode0 + z[w].second] = i;
-            mode_cls[b.mode0 + z[w].second] = (int)cls.size() - 1;
+            if (w == 0 || z[w].first != z[w - 1].first) lz.push_back(z[w].first);
+            lc[z[w].second] = (int)lz.size() - 1;
+        }
+        // classes numbered by first appearance in mode order (nearby modes, nearby factors)
+        std::vector<int> ren(lz.size(), -1);
+        int next = 0;
+        for (long m = 0; m < b.n_modes; m++)
+            if (ren[lc[m]] < 0) ren[lc[m]] = next++;
+        std::vector<double> cz(lz.size());
+        for (size_t c = 0; c < lz.size(); c++) cz[ren[c]] = lz[c];
+        const long cbase = (long)cls.size();
+        for (size_t c = 0; c < cz.size(); c++) {
+            cls.push_back(BatchCls{cz[c], i, fh, fb});
+            fh += 2L * b.rows_h;
+            fb += 2L * b.rows_b;
+        }
+        for (long m = 0; m < b.n_modes; m++) {
+            mode_inst[b.mode0 + m] = i;
+            mode_cls[b.mode0 + m] = (int)(cbase + ren[lc[m]]);
         }
     }
     // work order: decreasing N, then instance, then class

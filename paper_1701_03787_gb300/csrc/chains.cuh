@@ -350,22 +350,48 @@ __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, d
     }
 }
 
+// Tuning constants of the biharmonic float-float chain (compile-time; -D overrides):
+//   PBF / PBB  rows per register prefetch block in the forward / backward sweep (two
+//              blocks in flight)
+//   PFD        distance, in rows, of the L2 bulk prefetch ahead of the sweep (0: off)
+//   QSD        1: read the per-N (q, s) table at use (L1-resident) instead of prefetching
+#ifndef SHEN_BIH_DF_PBF
+#define SHEN_BIH_DF_PBF 4
+#endif
+#ifndef SHEN_BIH_DF_PBB
+#define SHEN_BIH_DF_PBB 2
+#endif
+#ifndef SHEN_BIH_DF_PFD
+#define SHEN_BIH_DF_PFD 0
+#endif
+#ifndef SHEN_BIH_DF_QSD
+#define SHEN_BIH_DF_QSD 1
+#endif
+
+// Bulk prefetch of [p, p + bytes) into L2 (no registers, no completion to wait for).
+// p 16-byte aligned, bytes a multiple of 16; callers pass ranges inside their arrays.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes));
+}
+
 // Biharmonic float-float chain.  Factors of the chain: Ff[i] = (L1, L2) for the forward
 // elimination and Fb[3 i .. 3 i + 2] = (1/U0, U1) (U2, ta) (tb, 0) for the back
 // substitution, each value as (hi, lo) (separate streams, so each sweep reads only the
 // bytes it uses); qs: per-N (q_k, s_k) float-float by k, zero beyond the unknowns.
 // Rows are fetched PB at a time into two register buffers, the next block's loads
 // issued before the current block is computed; all loads of a block precede its stores
-// (which may alias f when u == f).
-__device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
-                                          const float4 *Fb, const float4 *qs) {
+// (which may alias f when u == f).  With PFD > 0 the rows PFD ahead of each block are
+// also requested into L2, so that the register loads find them there.
+template <int PBF, int PBB, int PFD, bool QSD>
+__device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
+                                            const float4 *Fb, const float4 *qs) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
     const F2 zero{0.f, 0.f};
-    constexpr int PB = 4;
     // forward elimination y_i = f_i - L1_i y_{i-1} - L2_i y_{i-2}
     CF2 y1{zero, zero}, y2 = y1;
     {
+        constexpr int PB = PBF;
         double2 fa[PB], fb[PB];
         float4 la[PB], lb[PB];
         auto load = [&](double2 (&fx)[PB], float4 (&lx)[PB], int i0) {
@@ -382,16 +408,28 @@ __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, do
                 if (i0 + q < rows) {
                     const F2 L1{lx[q].x, lx[q].y}, L2{lx[q].z, lx[q].w};
                     CF2 y;
-                    y.re = fnma(L2, y2.re, fnma(L1, y1.re, df::from_f64(fx[q].x)));
-                    y.im = fnma(L2, y2.im, fnma(L1, y1.im, df::from_f64(fx[q].y)));
+                    // the y_{i-2} term first: only the last step waits for y_{i-1}
+                    y.re = fnma(L1, y1.re, fnma(L2, y2.re, df::from_f64(fx[q].x)));
+                    y.im = fnma(L1, y1.im, fnma(L2, y2.im, df::from_f64(fx[q].y)));
                     store_cf2(ucol, 2 * (i0 + q) + par, y);
                     y2 = y1;
                     y1 = y;
                 }
             }
         };
+        // chain rows [a, b): column rows [2a, 2b) (both parities) and Ff rows [a, b)
+        auto prefetch = [&](int a) {
+            const int b = min(a + 2 * PB, rows);
+            if (PFD > 0 && a < b) {
+                prefetch_l2(fcol + 4 * a, 32u * (b - a));
+                prefetch_l2(Ff + a, 16u * (b - a));
+            }
+        };
+        if (PFD > 0)
+            for (int a = 0; a < PFD; a += 2 * PB) prefetch(a);
         load(fa, la, 0);
         for (int i0 = 0; i0 < rows; i0 += 2 * PB) {
+            prefetch(i0 + PFD);
             load(fb, lb, i0 + PB);
             run(fa, la, i0);
             load(fa, la, i0 + 2 * PB);
@@ -402,8 +440,10 @@ __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, do
     // Sq = sum_{j >= i+3} q_j u_j, Ss = sum_{j >= i+3} s_j u_j
     CF2 u1{zero, zero}, u2 = u1, u3 = u1, Sq = u1, Ss = u1;
     {
-        float4 ya[PB], yb[PB], ba[PB], bb[PB], ca[PB], cb[PB], da[PB], db[PB], qa[PB], qb[PB];
-        auto load = [&](float4 (&yx)[PB], float4 (&bx)[PB], float4 (&cx)[PB], float4 (&dx)[PB], float4 (&qx)[PB],
+        constexpr int PB = PBB;
+        constexpr int NQ = QSD ? 1 : PB;
+        float4 ya[PB], yb[PB], ba[PB], bb[PB], ca[PB], cb[PB], da[PB], db[PB], qa[NQ], qb[NQ];
+        auto load = [&](float4 (&yx)[PB], float4 (&bx)[PB], float4 (&cx)[PB], float4 (&dx)[PB], float4 (&qx)[NQ],
                         int i0) {
 #pragma unroll
             for (int q = 0; q < PB; q++) {
@@ -412,17 +452,18 @@ __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, do
                 bx[q] = Fb[3 * i];
                 cx[q] = Fb[3 * i + 1];
                 dx[q] = Fb[3 * i + 2];
-                qx[q] = qs[2 * i + par + 6];
+                if (!QSD) qx[q < NQ ? q : 0] = qs[2 * i + par + 6];
             }
         };
         auto run = [&](const float4 (&yx)[PB], const float4 (&bx)[PB], const float4 (&cx)[PB],
-                       const float4 (&dx)[PB], const float4 (&qx)[PB], int i0) {
+                       const float4 (&dx)[PB], const float4 (&qx)[NQ], int i0) {
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = i0 - q;
                 if (i >= 0) {
                     if (i + 3 < rows) {
-                        const F2 qq{qx[q].x, qx[q].y}, ss{qx[q].z, qx[q].w};
+                        const float4 qv = QSD ? __ldg(qs + 2 * i + par + 6) : qx[q < NQ ? q : 0];
+                        const F2 qq{qv.x, qv.y}, ss{qv.z, qv.w};
                         Sq.re = df::add(Sq.re, df::mul(qq, u3.re));
                         Sq.im = df::add(Sq.im, df::mul(qq, u3.im));
                         Ss.re = df::add(Ss.re, df::mul(ss, u3.re));
@@ -431,9 +472,10 @@ __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, do
                     const F2 inv0{bx[q].x, bx[q].y}, U1{bx[q].z, bx[q].w}, U2{cx[q].x, cx[q].y};
                     const F2 ta{cx[q].z, cx[q].w}, tb{dx[q].x, dx[q].y};
                     const CF2 yi{F2{yx[q].x, yx[q].y}, F2{yx[q].z, yx[q].w}};
+                    // terms known before u_{i+1} first: only the last step waits for it
                     CF2 t;
-                    t.re = fnma(tb, Ss.re, fnma(ta, Sq.re, fnma(U2, u2.re, fnma(U1, u1.re, yi.re))));
-                    t.im = fnma(tb, Ss.im, fnma(ta, Sq.im, fnma(U2, u2.im, fnma(U1, u1.im, yi.im))));
+                    t.re = fnma(U1, u1.re, fnma(U2, u2.re, fnma(tb, Ss.re, fnma(ta, Sq.re, yi.re))));
+                    t.im = fnma(U1, u1.im, fnma(U2, u2.im, fnma(tb, Ss.im, fnma(ta, Sq.im, yi.im))));
                     CF2 ui;
                     ui.re = df::mul(inv0, t.re);
                     ui.im = df::mul(inv0, t.im);
@@ -446,8 +488,19 @@ __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, do
                 }
             }
         };
+        // chain rows (b - 2 PB, b]: column rows [2a, 2b + 2) and Fb rows [3a, 3b + 3)
+        auto prefetch = [&](int b) {
+            const int a = max(b - 2 * PB + 1, 0);
+            if (PFD > 0 && b >= 0 && a <= b) {
+                prefetch_l2(ucol + 4 * a, 32u * (b - a + 1));
+                prefetch_l2(Fb + 3 * a, 48u * (b - a + 1));
+            }
+        };
+        if (PFD > 0)
+            for (int b = rows - 1; b > rows - 1 - PFD; b -= 2 * PB) prefetch(b);
         load(ya, ba, ca, da, qa, rows - 1);
         for (int i0 = rows - 1; i0 >= 0; i0 -= 2 * PB) {
+            prefetch(i0 - PFD);
             load(yb, bb, cb, db, qb, i0 - PB);
             run(ya, ba, ca, da, qa, i0);
             load(ya, ba, ca, da, qa, i0 - 2 * PB);
@@ -456,6 +509,12 @@ __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, do
     }
     if (par == 0)
         for (int k = n; k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
+}
+
+__device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
+                                          const float4 *Fb, const float4 *qs) {
+    solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_PFD, SHEN_BIH_DF_QSD != 0>(
+        N, par, fcol, ucol, Ff, Fb, qs);
 }
 
 }  // namespace chains
