@@ -10,6 +10,8 @@ Prints one JSON line (rank 0).  `--impl reference` times the oracle's O(N) C cod
 (the paper's algorithms, OpenMP) on the host cores instead.
 """
 import argparse
+import ctypes
+import datetime
 import json
 import math
 import os
@@ -43,6 +45,43 @@ def n_modes_of(w):
     return (w["Nx"] // 2 + 1) * w["Nz"]
 
 
+def gpu_pci_id(dev):
+    """PCI bus id of CUDA device `dev` in NVML's format, or None."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    if not all(hasattr(p, a) for a in ("pci_domain_id", "pci_bus_id", "pci_device_id")):
+        return None
+    return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+
+
+def bind_gpu_local_cpus(pci):
+    """Run this process on the CPUs that NVML reports as local to the GPU (a read-only
+    query), so that pinned host buffers are first touched, and placed, next to it."""
+    try:
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            return None
+        try:
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(h)) != 0:
+                return None
+            words = 64
+            mask = (ctypes.c_ulong * words)()
+            if nv.nvmlDeviceGetCpuAffinity(h, words, mask) != 0:
+                return None
+        finally:
+            nv.nvmlShutdown()
+        bits = 8 * ctypes.sizeof(ctypes.c_ulong)
+        cpus = {w * bits + b for w in range(words) for b in range(bits) if (mask[w] >> b) & 1}
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return len(cpus)
+    except Exception:
+        return None
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -57,15 +96,17 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks / throttle reasons every 100 ms; only the samples whose
+    timestamps fall inside the timed region (mark_begin .. mark_end) are kept."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, gpu_id):
+        self.gpu = gpu_id
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -73,10 +114,16 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark_begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
@@ -95,6 +142,9 @@ class ClockSampler:
                 if len(parts) < 9:
                     continue
                 try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                    if self.t0 and self.t1 and not (self.t0 <= ts <= self.t1):
+                        continue
                     sm.append(float(parts[1]))
                     mx.append(float(parts[2]))
                 except ValueError:
@@ -192,7 +242,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n1024", choices=sorted(WORKLOADS))
@@ -213,6 +263,8 @@ def main():
     from paper_1701_03787_gb300 import Plan, inputs
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    pci = gpu_pci_id(local)
+    local_cpus = bind_gpu_local_cpus(pci) if pci else None
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -275,16 +327,19 @@ def main():
     stream.synchronize()
     # timed region: K whole steps, CUDA events on `stream`
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(pci or local)
+    clocks.start()
+    time.sleep(0.5)                        # let nvidia-smi start before the timed region
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_begin()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     # per-kernel durations, each kernel alone on `stream` (events on the launching stream)
@@ -369,19 +424,20 @@ def main():
         e2e_ms = a.elapsed_time(b) / k
         e2e = {"value": world * 2 * rows / (e2e_ms * 1e-3), "unit": "solves*N/s",
                "h2d_bytes_per_step": int(2 * rows * 16), "d2h_bytes_per_step": int(2 * rows * 16),
-               "ms_per_step": e2e_ms, "path": "device copies + solves" if batched else "shen_solve_host"}
+               "ms_per_step": e2e_ms, "path": "device copies + solves" if batched else "shen_solve_host",
+               "host_cpus_gpu_local": local_cpus}
         # host link ceiling: both fields copied in and out at once on two streams
         la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         fork.record(stream)
         s_h.wait_event(fork)
         s_b.wait_event(fork)
         la.record(stream)
-        with torch.cuda.stream(s_h):
-            f_h.copy_(hf_h, non_blocking=True)
-            f_b.copy_(hf_b, non_blocking=True)
-        with torch.cuda.stream(s_b):
-            hu.copy_(u_h, non_blocking=True)
-            hu2.copy_(u_b, non_blocking=True)
+        ce = 16 << 20                        # 256 MB copies (complex128 elements)
+        for dst, src, st in ((f_h, hf_h, s_h), (f_b, hf_b, s_h), (hu, u_h, s_b), (hu2, u_b, s_b)):
+            dv, sv = dst.view(-1), src.view(-1)
+            with torch.cuda.stream(st):
+                for e0_ in range(0, dv.numel(), ce):
+                    dv[e0_:e0_ + ce].copy_(sv[e0_:e0_ + ce], non_blocking=True)
         join_h.record(s_h)
         join_b.record(s_b)
         stream.wait_event(join_h)
