@@ -45,6 +45,28 @@ def n_modes_of(w):
     return (w["Nx"] // 2 + 1) * w["Nz"]
 
 
+def measured_traffic(kind, rows):
+    """DRAM bytes of one launch of `kind` ("problem:precision") over `rows` complex rows,
+    scaled from the per-row figure of an ncu capture (profiles/traffic.json); None if the
+    CUDA sources have changed since that capture."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        t = json.load(fh)
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1701_03787_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    if h.hexdigest() != t.get("sources_sha1") or kind not in t.get("bytes_per_row", {}):
+        return None
+    return t["bytes_per_row"][kind] * rows
+
+
 def gpu_pci_id(dev):
     """PCI bus id of CUDA device `dev` in NVML's format, or None."""
     import torch
@@ -480,8 +502,9 @@ def main():
     dom = "biharmonic" if t_b >= t_h else "helmholtz"
     t_dom = max(t_b, t_h)
     achieved = rows * BYTES_PER_ROW / (t_dom * 1e-3) / 1e9
+    traffic = None if batched else measured_traffic(f"{dom}:{prec[dom]}", rows)
     roofline = {"bound": "hbm", "kernel": f"solve_{dom}_{prec[dom]}", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind, "bytes_per_row": BYTES_PER_ROW}
     line = {"metric": METRIC, "value": value, "unit": "solves*N/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
