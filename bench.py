@@ -76,32 +76,59 @@ def gpu_pci_id(dev):
     return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
 
 
-def bind_gpu_local_cpus(pci):
-    """Run this process on the CPUs that NVML reports as local to the GPU (a read-only
-    query), so that pinned host buffers are first touched, and placed, next to it."""
+def _mask_bits(mask):
+    bits = 8 * ctypes.sizeof(ctypes.c_ulong)
+    return {w * bits + b for w in range(len(mask)) for b in range(bits) if (mask[w] >> b) & 1}
+
+
+def bind_gpu_local_host(pci):
+    """Place this process next to the GPU: run it on the CPUs NVML reports as local to the
+    GPU, and prefer the GPU's NUMA node for its host memory (so that pinned buffers land
+    there).  NVML is only queried; the binding affects this process alone.  Returns a
+    description of the host topology seen."""
+    info = {"cpus_allowed": len(os.sched_getaffinity(0))}
+    try:
+        with open("/proc/self/status") as fh:
+            for line in fh:
+                if line.startswith("Mems_allowed_list"):
+                    info["mems_allowed"] = line.split(":", 1)[1].strip()
+        info["numa_nodes"] = sorted(int(d[4:]) for d in os.listdir("/sys/devices/system/node")
+                                    if d.startswith("node") and d[4:].isdigit())
+    except Exception:
+        pass
     try:
         nv = ctypes.CDLL("libnvidia-ml.so.1")
         if nv.nvmlInit_v2() != 0:
-            return None
+            return info
         try:
             h = ctypes.c_void_p()
             if nv.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(h)) != 0:
-                return None
-            words = 64
-            mask = (ctypes.c_ulong * words)()
-            if nv.nvmlDeviceGetCpuAffinity(h, words, mask) != 0:
-                return None
+                return info
+            cmask = (ctypes.c_ulong * 64)()
+            cpus = _mask_bits(cmask) if nv.nvmlDeviceGetCpuAffinity(h, 64, cmask) == 0 else set()
+            nmask = (ctypes.c_ulong * 4)()
+            nodes = _mask_bits(nmask) if nv.nvmlDeviceGetMemoryAffinity(h, 4, nmask, 0) == 0 else set()
         finally:
             nv.nvmlShutdown()
-        bits = 8 * ctypes.sizeof(ctypes.c_ulong)
-        cpus = {w * bits + b for w in range(words) for b in range(bits) if (mask[w] >> b) & 1}
         cpus &= os.sched_getaffinity(0)
-        if not cpus:
-            return None
-        os.sched_setaffinity(0, cpus)
-        return len(cpus)
-    except Exception:
-        return None
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            info["cpus_gpu_local"] = len(cpus)
+        if nodes:
+            info["gpu_numa_nodes"] = sorted(nodes)
+            # set_mempolicy(MPOL_PREFERRED, node): later first touches prefer the GPU's node
+            libc = ctypes.CDLL(None, use_errno=True)
+            node = min(nodes)
+            m = (ctypes.c_ulong * 16)()
+            m[node // 64] = 1 << (node % 64)
+            import platform
+            nr = {"aarch64": 237, "x86_64": 238}.get(platform.machine())    # set_mempolicy
+            if nr is not None:
+                ok = libc.syscall(nr, 1, m, ctypes.c_ulong(16 * 64 + 1)) == 0
+                info["mempolicy_preferred_node"] = node if ok else None
+    except Exception as ex:
+        info["error"] = type(ex).__name__
+    return info
 
 
 def dist_env():
@@ -276,6 +303,8 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--streams", type=int, default=1, choices=[1, 2],
                     help="2: run the two solves concurrently on two streams")
+    ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
+                    help="replay the step as a captured CUDA graph (auto: on for the batch workload)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -286,7 +315,7 @@ def main():
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     pci = gpu_pci_id(local)
-    local_cpus = bind_gpu_local_cpus(pci) if pci else None
+    host_info = bind_gpu_local_host(pci) if pci else None
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -322,6 +351,16 @@ def main():
     if batched:
         plan.helmholtz_solve = lambda f, u, precision, stream: plan.solve("helmholtz", f, u, precision, stream)
         plan.biharmonic_solve = lambda f, u, precision, stream: plan.solve("biharmonic", f, u, precision, stream)
+    tuned = None
+    if args.precision == "auto":
+        # the library's autotuner times every path that meets the 1e-10 bar (and the
+        # row-block shapes of the float-float kernels) on these fields and keeps the fastest
+        tuned = {}
+        for problem, f, u in (("helmholtz", f_h, u_h), ("biharmonic", f_b, u_b)):
+            name, t = plan.autotune(problem, f, u, stream=stream)
+            tuned[problem] = {"chosen": name, "ms": t}
+            prec[problem] = name
+        stream.synchronize()
 
     # The two solves are independent: run them on two streams that fork from and join
     # back into `stream` (the Helmholtz float32/float-float kernels and the float64
@@ -347,6 +386,23 @@ def main():
     for _ in range(args.warmup):
         step()
     stream.synchronize()
+    use_graph = args.graph == "on" or (args.graph == "auto" and batched)
+    if use_graph:
+        # the step's launches (and the batch queue resets) captured once, replayed per step
+        graph = torch.cuda.CUDAGraph()
+        eager_step = step
+        with torch.cuda.graph(graph, stream=stream):
+            eager_step()
+        stream.synchronize()
+
+        def step(ph=None, pb=None):
+            if ph is not None or pb is not None:
+                return eager_step(ph or prec["helmholtz"], pb or prec["biharmonic"])
+            with torch.cuda.stream(stream):
+                graph.replay()
+        for _ in range(2):
+            step()
+        stream.synchronize()
     # timed region: K whole steps, CUDA events on `stream`
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(pci or local)
@@ -447,7 +503,7 @@ def main():
         e2e = {"value": world * 2 * rows / (e2e_ms * 1e-3), "unit": "solves*N/s",
                "h2d_bytes_per_step": int(2 * rows * 16), "d2h_bytes_per_step": int(2 * rows * 16),
                "ms_per_step": e2e_ms, "path": "device copies + solves" if batched else "shen_solve_host",
-               "host_cpus_gpu_local": local_cpus}
+               "host": host_info}
         # host link ceiling: both fields copied in and out at once on two streams
         la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         fork.record(stream)
@@ -512,9 +568,10 @@ def main():
             "dtype": "f64" if set(prec.values()) == {"fp64"} else "f32 sweeps + refinement (io f64)",
             "data": "synthetic", "precision": prec,
             "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes, "rows": rows,
-                       "streams": args.streams,
+                       "streams": args.streams, "cuda_graph": use_graph, "plan_device_bytes": plan.info()[3]
+                       if not batched else plan.device_bytes,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
-            "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
+            "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e,
             "rhs_matvec": mv}
     if rank == 0 and not args.no_check and not batched:

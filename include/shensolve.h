@@ -81,6 +81,8 @@ typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
  *   SHEN_DF         forward elimination and back substitution themselves in
  *                   float-float arithmetic (~48 significant bits) with the factors
  *                   as float-float pairs; no refinement.
+ *   SHEN_AUTO       the path recorded for the plan and problem by shen_plan_autotune
+ *                   / shen_batch_autotune (SHEN_DF until then).
  * A solve returns SHEN_ERR_UNSUPPORTED for a (problem, precision) pair that is not
  * built: the float32-sweep variants exist for the Helmholtz problem, N <= 2048, one
  * refinement step. */
@@ -90,7 +92,8 @@ typedef enum {
     SHEN_FP32_R2 = 2,
     SHEN_DF_R1 = 3,
     SHEN_DF_R2 = 4,
-    SHEN_DF = 5
+    SHEN_DF = 5,
+    SHEN_AUTO = 6
 } shen_precision;
 
 /* Create a plan for one channel: N Chebyshev modes (8 <= N <= 4096), Fourier grid
@@ -138,6 +141,24 @@ shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, lon
  * device solves. */
 shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
                             void *stream);
+
+/* Time the candidate paths of `problem` on this plan and record the fastest for
+ * SHEN_AUTO.  The candidates are the paths that meet a 1e-10 per-mode relative error
+ * bar against the float64 oracle in the library's parity tests:
+ *   Helmholtz:  SHEN_FP64, SHEN_DF, SHEN_DF_R1, SHEN_FP32_R1;
+ *   biharmonic: SHEN_FP64, SHEN_DF.
+ * Each float-float candidate is timed in both of its row-block shapes (rows each
+ * thread keeps in flight; the shapes give identical results).  The chosen shape then
+ * serves every float-float solve of the plan and problem.  No candidate changes the
+ * method or its accuracy class beyond that bar.
+ *
+ * f, u: DEVICE fields of the plan (n_modes * N complex values); they are solved in
+ * place of a real workload and u is overwritten; u must not overlap f.  Synchronous:
+ * returns after the timing (CUDA events on `stream`).  *chosen (may be NULL) receives
+ * the chosen shen_precision, *ms (may be NULL) its time per solve in milliseconds.
+ * Errors as the solves. */
+shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, double *u, int *chosen,
+                               float *ms, void *stream);
 
 /* Right-hand-side operator: out = R x + beta * y for every mode (R = R_h or R_b by
  * `problem`).  y may be NULL (then beta is ignored).  x, y, out: DEVICE fields;
@@ -192,10 +213,17 @@ shen_status shen_batch_info(shen_batch_t batch, long *n_modes, long *field_elems
 shen_status shen_batch_offsets(shen_batch_t batch, long *offsets);
 
 /* Solve every mode of every instance: problem SHEN_HELMHOLTZ or SHEN_BIHARMONIC,
- * precision SHEN_FP64 or SHEN_DF (others: SHEN_ERR_UNSUPPORTED).  f, u: DEVICE batched
+ * precision SHEN_FP64, SHEN_DF or SHEN_AUTO (others: SHEN_ERR_UNSUPPORTED).  f, u: DEVICE batched
  * fields (u == f allowed).  Layout and zeroed trailing entries as for single plans. */
 shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, double *u, int precision,
                              void *stream);
+
+/* Autotuning for batched plans, as shen_plan_autotune: candidates SHEN_FP64 and
+ * SHEN_DF, the latter in both row-block shapes, each launched on a persistent grid
+ * sized to that kernel's residency.  f, u: DEVICE batched fields (u must not overlap f;
+ * u is overwritten).  Synchronous. */
+shen_status shen_batch_autotune(shen_batch_t batch, int problem, const double *f, double *u, int *chosen,
+                                float *ms, void *stream);
 
 /* Device-side error state of the batched plan (SHEN_OK or SHEN_ERR_SINGULAR). */
 shen_status shen_batch_check(shen_batch_t batch);
@@ -204,9 +232,8 @@ shen_status shen_batch_check(shen_batch_t batch);
 void shen_batch_destroy(shen_batch_t batch);
 
 /* Same solve as shen_batch_solve, for callers that cannot allocate device memory when
- * they solve -- for example code running while a stream is captured into a CUDA graph,
- * where cudaMalloc is not a permitted call, or an application whose device memory is
- * carved up in advance by its own pool allocator.  The paper has no counterpart: this
+ * they solve -- for example an application whose device memory is carved up in
+ * advance by its own pool allocator.  The paper has no counterpart: this
  * is a property of the library, not of the method.
  *
  * It allocates nothing and uses none of the plan's scratch: its work-queue counter

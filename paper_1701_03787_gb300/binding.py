@@ -15,7 +15,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "shensolve.h")
 
 SHEN_OK, SHEN_ERR_ARG, SHEN_ERR_ALLOC, SHEN_ERR_CUDA, SHEN_ERR_SINGULAR, SHEN_ERR_UNSUPPORTED = range(6)
 SHEN_HELMHOLTZ, SHEN_BIHARMONIC = 0, 1
-PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5}
+PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5, "auto": 6}
+PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
 
 _lib = None
@@ -53,6 +54,8 @@ def lib():
         "shen_batch_solve": ([P, I, P, P, I, P], I),
         "shen_batch_check": ([P], I),
         "shen_batch_solve_noalloc": ([P, I, P, P, I, P], I),
+        "shen_batch_autotune": ([P, I, P, P, P, P, P], I),
+        "shen_plan_autotune": ([P, I, P, P, P, P, P], I),
         "shen_batch_destroy": ([P], None),
         "shen_status_string": ([I], ctypes.c_char_p),
         "shen_version": ([], I),
@@ -232,6 +235,19 @@ class Plan:
                                     _stream(stream)), "shen_rhs_matvec")
         return out
 
+    def autotune(self, problem, f, u=None, stream=None):
+        """Time the candidate paths of `problem` on the fields f (read) and u (overwritten)
+        and record the fastest for precision "auto".  Returns (precision name, ms)."""
+        import torch
+        _field_ok(f, self.n_modes, self.N, "f")
+        if u is None:
+            u = torch.empty_like(f)
+        _field_ok(u, self.n_modes, self.N, "u")
+        chosen, ms = ctypes.c_int(), ctypes.c_float()
+        check(lib().shen_plan_autotune(self._h, _problem(problem), _ptr(f), _ptr(u), ctypes.byref(chosen),
+                                       ctypes.byref(ms), _stream(stream)), "shen_plan_autotune")
+        return PRECISION_NAMES[chosen.value], ms.value
+
     def check_device(self):
         where = ctypes.c_long()
         check(lib().shen_plan_check(self._h, ctypes.byref(where)), "shen_plan_check")
@@ -298,6 +314,18 @@ class BatchPlan:
         check(lib().shen_batch_solve(self._h, _problem(problem), _ptr(f), _ptr(u), _prec(precision),
                                      _stream(stream)), "shen_batch_solve")
         return u
+
+    def autotune(self, problem, f, u=None, stream=None):
+        """As Plan.autotune, for the batched field."""
+        import torch
+        if f.dtype != torch.complex128 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.field_elems:
+            raise ValueError(f"f must be a contiguous complex128 CUDA tensor of {self.field_elems} entries")
+        if u is None:
+            u = torch.empty_like(f)
+        chosen, ms = ctypes.c_int(), ctypes.c_float()
+        check(lib().shen_batch_autotune(self._h, _problem(problem), _ptr(f), _ptr(u), ctypes.byref(chosen),
+                                        ctypes.byref(ms), _stream(stream)), "shen_batch_autotune")
+        return PRECISION_NAMES[chosen.value], ms.value
 
     def check_device(self):
         check(lib().shen_batch_check(self._h), "shen_batch_check")

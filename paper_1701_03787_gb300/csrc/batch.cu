@@ -100,7 +100,8 @@ __global__ void batch_pack_qs_kernel(BatchDev b, int n_tabs, const int *tab_N) {
 }
 
 // precision: 0 float64, 1 float-float.  problem: SHEN_HELMHOLTZ / SHEN_BIHARMONIC.
-template <int PREC, int PROBLEM>
+// V: row-block shape of the float-float chains (identical results).
+template <int PREC, int PROBLEM, int V>
 __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const double *f, double *u) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                   b.fac_h + (cl.fh + (long)par * in.rows_h) * kHelmF64,
                                                   (cl.z2 + in.c) * kPi / 2);
                 } else {
-                    chains::solve_helm_df_chain(in.N, par, f + off, u + off,
+                    chains::solve_helm_df_chain<V>(in.N, par, f + off, u + off,
                                                 b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2,
                                                 df::from_f64((cl.z2 + in.c) * (kPi / 2)));
                 }
@@ -132,12 +133,22 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                  b.tabs[in.tab].qk, b.tabs[in.tab].sk);
                 } else {
                     const float4 *F = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
-                    chains::solve_bih_df_chain(in.N, par, f + off, u + off, F, F + in.rows_b,
+                    chains::solve_bih_df_chain<V>(in.N, par, f + off, u + off, F, F + in.rows_b,
                                                b.qs_df + (size_t)in.tab * b.qs_stride);
                 }
             }
         }
     }
+}
+
+using BatchKernel = void (*)(BatchDev, const double *, double *);
+
+BatchKernel batch_kernel(int prec, int problem, int v) {
+    if (prec == 0) return problem == SHEN_HELMHOLTZ ? batch_solve_kernel<0, SHEN_HELMHOLTZ, 0>
+                                                    : batch_solve_kernel<0, SHEN_BIHARMONIC, 0>;
+    if (problem == SHEN_HELMHOLTZ) return v ? batch_solve_kernel<1, SHEN_HELMHOLTZ, 1>
+                                            : batch_solve_kernel<1, SHEN_HELMHOLTZ, 0>;
+    return v ? batch_solve_kernel<1, SHEN_BIHARMONIC, 1> : batch_solve_kernel<1, SHEN_BIHARMONIC, 0>;
 }
 
 }  // namespace
@@ -156,7 +167,9 @@ struct shen_batch_s {
     std::vector<void *> allocs;
     RowTables *d_tabs = nullptr;
     long long device_bytes = 0;
-    int grid = 0;                                // persistent grid
+    int grid[2][2][2] = {};                      // persistent grid per [precision][problem][shape]
+    int auto_prec[2] = {SHEN_DF, SHEN_DF};       // SHEN_AUTO per problem (autotuned)
+    int df_variant[2] = {0, 0};                  // float-float shape per problem (autotuned)
     ~shen_batch_s() {
         for (void *p : allocs) cudaFree(p);
     }
@@ -353,12 +366,17 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
     B_TRY(cudaMemcpyAsync(err_host, D.err, sizeof(err_host), cudaMemcpyDeviceToHost, s));
     B_TRY(cudaStreamSynchronize(s));
     if (err_host[0]) return fail(SHEN_ERR_SINGULAR);
-    // persistent grid: resident blocks of the largest solve kernel
-    int dev = 0, sms = 0, per_sm = 0;
+    // persistent grids: the resident blocks of each solve kernel
+    int dev = 0, sms = 0;
     B_TRY(cudaGetDevice(&dev));
     B_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    B_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_solve_kernel<1, SHEN_BIHARMONIC>, 128, 0));
-    b->grid = std::max(1, sms * std::max(per_sm, 1));
+    for (int pr = 0; pr < 2; pr++)
+        for (int pb = 0; pb < 2; pb++)
+            for (int v = 0; v < 2; v++) {
+                int per_sm = 0;
+                B_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(pr, pb, v), 128, 0));
+                b->grid[pr][pb][v] = std::max(1, sms * std::max(per_sm, 1));
+            }
 #undef B_TRY
     *out = b;
     return SHEN_OK;
@@ -385,10 +403,24 @@ shen_status shen_batch_offsets(shen_batch_t batch, long *offsets) {
     return SHEN_OK;
 }
 
-shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, double *u, int precision,
-                             void *stream) {
+namespace {
+// One persistent launch of the solve kernel of (problem, precision) with the plan's
+// float-float shape for that problem, on the grid sized for that kernel.
+cudaError_t launch_batch(const shen_batch_s *batch, const BatchDev &D, int problem, int precision, const double *f,
+                         double *u, cudaStream_t s) {
+    const int pr = precision == SHEN_FP64 ? 0 : 1;
+    const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
+    const int v = pr ? batch->df_variant[pb] : 0;
+    batch_kernel(pr, problem, v)<<<batch->grid[pr][pb][v], 128, 0, s>>>(D, f, u);
+    return cudaGetLastError();
+}
+}  // namespace
+
+extern "C" shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, double *u, int precision,
+                                        void *stream) {
     if (!batch || !f || !u) return SHEN_ERR_ARG;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (precision == SHEN_AUTO) precision = batch->auto_prec[problem];
     if (precision != SHEN_FP64 && precision != SHEN_DF) {
         if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
         return SHEN_ERR_ARG;
@@ -402,14 +434,7 @@ shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, d
     D.queue = batch->d.queue + problem;        // separate counters: a Helmholtz and a biharmonic
     cudaError_t e = cudaMemsetAsync(D.queue, 0, sizeof(int), s);   // solve may overlap
     if (e != cudaSuccess) return cuda_status(e);
-    if (problem == SHEN_HELMHOLTZ) {
-        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
-        else batch_solve_kernel<1, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
-    } else {
-        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
-        else batch_solve_kernel<1, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
-    }
-    e = cudaGetLastError();
+    e = launch_batch(batch, D, problem, precision, f, u, s);
     return e == cudaSuccess ? SHEN_OK : cuda_status(e);
 }
 
@@ -421,6 +446,64 @@ shen_status shen_batch_check(shen_batch_t batch) {
     return err_host[0] ? SHEN_ERR_SINGULAR : SHEN_OK;
 }
 
+shen_status shen_batch_autotune(shen_batch_t batch, int problem, const double *f, double *u, int *chosen, float *ms,
+                                void *stream) {
+    if (!batch || !f || !u) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(f) & 15u) || (reinterpret_cast<uintptr_t>(u) & 15u)) return SHEN_ERR_ARG;
+    long elems = 0;
+    shen_batch_info(batch, nullptr, &elems, nullptr, nullptr);
+    if (f == u || !(f + 2 * elems <= u || u + 2 * elems <= f)) return SHEN_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BatchDev D = batch->d;
+    D.queue = batch->d.queue + problem;
+    const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
+    const int v0 = batch->df_variant[pb];
+    const int cands[3][2] = {{SHEN_FP64, 0}, {SHEN_DF, 0}, {SHEN_DF, 1}};
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return cuda_status(cudaErrorUnknown);
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_status(cudaErrorUnknown);
+    }
+    float best = 0.f, best_df = 0.f;
+    int pick = SHEN_DF, pick_df = v0;
+    cudaError_t e = cudaSuccess;
+    for (const auto &c : cands) {
+        batch->df_variant[pb] = c[1];
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int r = -1; r < 3 && e == cudaSuccess; r++) {     // r = -1: untimed
+            e = cudaEventRecord(ev[0], s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(D.queue, 0, sizeof(int), s);
+            if (e == cudaSuccess) e = launch_batch(batch, D, problem, c[0], f, u, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess && r >= 0) e = cudaEventElapsedTime(&t[r], ev[0], ev[1]);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(t, t + 3);
+        if (best == 0.f || t[1] < best) {
+            best = t[1];
+            pick = c[0];
+        }
+        if (c[0] == SHEN_DF && (best_df == 0.f || t[1] < best_df)) {
+            best_df = t[1];
+            pick_df = c[1];
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) {
+        batch->df_variant[pb] = v0;
+        return cuda_status(e);
+    }
+    batch->auto_prec[problem] = pick;
+    batch->df_variant[pb] = pick_df;
+    if (chosen) *chosen = pick;
+    if (ms) *ms = best;
+    return SHEN_OK;
+}
+
 void shen_batch_destroy(shen_batch_t batch) { delete batch; }
 
 }  // extern "C"
@@ -428,11 +511,10 @@ void shen_batch_destroy(shen_batch_t batch) { delete batch; }
 // ---------------------------------------------------------------------------------
 // No-allocation variant of the batched solve.
 //
-// Some callers cannot allocate device memory when they solve: code that runs while a
-// stream is being captured into a CUDA graph (cudaMalloc is not a permitted call
-// there and breaks the capture), or an application whose device memory is divided up
-// in advance by its own pool allocator, which must not see allocations it did not
-// make during a time step.  For them, shen_batch_solve_noalloc keeps the only scratch
+// Some callers cannot allocate device memory when they solve, for example an
+// application whose device memory is divided up in advance by its own pool allocator,
+// which must not see allocations it did not make during a time step.  For them,
+// shen_batch_solve_noalloc keeps the only scratch
 // the batched solve needs -- its work-queue counter -- in the fixed device array
 // below instead of in memory owned by the plan.  The array is 256 bytes; every GPU
 // that loads the library holds it until the process exits.
@@ -473,6 +555,7 @@ extern "C" shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem,
                                                 int precision, void *stream) {
     if (!batch || !f || !u) return SHEN_ERR_ARG;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (precision == SHEN_AUTO) precision = batch->auto_prec[problem];
     if (precision != SHEN_FP64 && precision != SHEN_DF) {
         if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
         return SHEN_ERR_ARG;
@@ -491,13 +574,6 @@ extern "C" shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem,
     if (e != cudaSuccess) return cuda_status(e);
     BatchDev D = batch->d;
     D.queue = scratch;
-    if (problem == SHEN_HELMHOLTZ) {
-        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
-        else batch_solve_kernel<1, SHEN_HELMHOLTZ><<<batch->grid, 128, 0, s>>>(D, f, u);
-    } else {
-        if (precision == SHEN_FP64) batch_solve_kernel<0, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
-        else batch_solve_kernel<1, SHEN_BIHARMONIC><<<batch->grid, 128, 0, s>>>(D, f, u);
-    }
-    e = cudaGetLastError();
+    e = launch_batch(batch, D, problem, precision, f, u, s);
     return e == cudaSuccess ? SHEN_OK : cuda_status(e);
 }

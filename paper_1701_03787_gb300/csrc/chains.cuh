@@ -265,15 +265,15 @@ __device__ __forceinline__ void store_f64(double *col, int k, CF2 v) {
 __device__ __forceinline__ F2 fnma(F2 a, F2 y, F2 x) { return df::add(x, neg(df::mul(a, y))); }
 
 // Helmholtz: F rows of two float4 (1/U0, U2) (l, 0) as (hi, lo); h = alpha pi / 2.
-__device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *F,
-                                           F2 h) {
+template <int PB>
+__device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol, double *ucol, const float4 *F,
+                                             F2 h) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
     // Forward elimination y_i = f_i - l_i y_{i-1}.  Rows are fetched PB at a time into two
     // register buffers: the next block's loads are issued before the current block is
     // computed (software pipelining), and all loads of a block precede its stores (which
     // may alias f when u == f).
-    constexpr int PB = 8;
     CF2 y{F2{0.f, 0.f}, F2{0.f, 0.f}};
     {
         double2 fa[PB], fb[PB];
@@ -511,10 +511,26 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
         for (int k = n; k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
 }
 
+// Row-block shapes of the float-float chains, chosen per plan by the autotuner.  They
+// change only how many rows each thread keeps in flight (and so its registers and the
+// warps resident per SM), never the arithmetic: every shape gives the same bits.
+//   Helmholtz  V0: 8 rows per block (154 registers);  V1: 4 rows per block
+//   biharmonic V0: the tuning constants above (124 registers, 16 warps per SM);
+//              V1: 4 + 4 rows, (q, s) prefetched (204 registers, 8 warps per SM)
+template <int V>
+__device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *F,
+                                           F2 h) {
+    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h);
+}
+
+template <int V>
 __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
                                           const float4 *Fb, const float4 *qs) {
-    solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_PFD, SHEN_BIH_DF_QSD != 0>(
-        N, par, fcol, ucol, Ff, Fb, qs);
+    if (V == 0)
+        solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_PFD, SHEN_BIH_DF_QSD != 0>(
+            N, par, fcol, ucol, Ff, Fb, qs);
+    else
+        solve_bih_df_chain_t<4, 4, 0, false>(N, par, fcol, ucol, Ff, Fb, qs);
 }
 
 }  // namespace chains

@@ -33,15 +33,18 @@ __device__ __forceinline__ bool work_item(const Plan &p, const int *order, long 
     return true;
 }
 
+template <int V>
 __global__ void __launch_bounds__(128) helm_df_kernel(Plan p, const int *order, long m0, long count,
                                                       const double *f, double *u, const float4 *fac) {
     WorkItem w;
     if (!work_item(p, order, m0, count, w)) return;
     const long off = 2 * w.col * p.N;
     const F2 h = df::from_f64((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
-    chains::solve_helm_df_chain(p.N, w.par, f + off, u + off, fac + ((size_t)w.cls * 2 + w.par) * p.rows_h * 2, h);
+    chains::solve_helm_df_chain<V>(p.N, w.par, f + off, u + off, fac + ((size_t)w.cls * 2 + w.par) * p.rows_h * 2,
+                                   h);
 }
 
+template <int V>
 __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, long m0, long count,
                                                      const double *f, double *u, const float4 *fac,
                                                      const float4 *qs) {
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, l
     if (!work_item(p, order, m0, count, w)) return;
     const long off = 2 * w.col * p.N;
     const float4 *F = fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4;   // rows_b (L1, L2), then 3 rows_b
-    chains::solve_bih_df_chain(p.N, w.par, f + off, u + off, F, F + p.rows_b, qs);
+    chains::solve_bih_df_chain<V>(p.N, w.par, f + off, u + off, F, F + p.rows_b, qs);
 }
 
 __device__ __forceinline__ float2 split2(double x) {
@@ -118,10 +121,15 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
     const float4 *h = reinterpret_cast<const float4 *>(p.d_fac_df);
     const float4 *b = h + (size_t)p.n_classes * 2 * p.rows_h * 2;
     const float4 *q = b + (size_t)p.n_classes * 2 * p.rows_b * 4;
-    if (problem == SHEN_HELMHOLTZ)
-        helm_df_kernel<<<nblocks(2 * count, 128), 128, 0, s>>>(p, order, m0, count, f, u, h);
-    else
-        bih_df_kernel<<<nblocks(2 * count, 128), 128, 0, s>>>(p, order, m0, count, f, u, b, q);
+    const unsigned g = nblocks(2 * count, 128);
+    const int v = p.df_variant[problem == SHEN_HELMHOLTZ ? 0 : 1];
+    if (problem == SHEN_HELMHOLTZ) {
+        if (v == 0) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h);
+        else helm_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h);
+    } else {
+        if (v == 0) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q);
+        else bih_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q);
+    }
     return cudaGetLastError();
 }
 

@@ -257,6 +257,7 @@ shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, cons
     if (m0 < 0 || count < 0 || m0 + count > p.n_modes) return SHEN_ERR_ARG;
     if (!aligned16(f) || !aligned16(u)) return SHEN_ERR_ARG;
     if (!overlap_ok(f, u, 2 * count * (long)p.N)) return SHEN_ERR_ARG;
+    if (precision == SHEN_AUTO) precision = p.auto_prec[problem];
     shen_status ps = check_precision(p, problem, precision);
     if (ps != SHEN_OK) return ps;
     if (count == 0) return SHEN_OK;
@@ -353,9 +354,75 @@ shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host,
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     const long nd = 2 * plan->p.n_modes * (long)plan->p.N;
     if (!overlap_ok(f_host, u_host, nd)) return SHEN_ERR_ARG;
+    if (precision == SHEN_AUTO) precision = plan->p.auto_prec[problem];
     const shen_status ps = check_precision(plan->p, problem, precision);
     if (ps != SHEN_OK) return ps;
     SHEN_CUDA_TRY(host_solve(plan->p, plan->host, problem, precision, f_host, u_host, as_stream(stream)));
+    return SHEN_OK;
+}
+
+shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, double *u, int *chosen, float *ms,
+                               void *stream) {
+    if (!plan || !f || !u) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    Plan &p = plan->p;
+    const long nd = 2 * p.n_modes * (long)p.N;
+    if (!aligned16(f) || !aligned16(u) || f == u || !overlap_ok(f, u, nd)) return SHEN_ERR_ARG;
+    struct Cand {
+        int prec, variant;
+    };
+    std::vector<Cand> cands = {{SHEN_FP64, 0}, {SHEN_DF, 0}, {SHEN_DF, 1}};
+    if (problem == SHEN_HELMHOLTZ && check_precision(p, problem, SHEN_DF_R1) == SHEN_OK) {
+        cands.push_back({SHEN_DF_R1, 0});
+        cands.push_back({SHEN_FP32_R1, 0});
+    }
+    cudaStream_t s = as_stream(stream);
+    cudaEvent_t ev[4];
+    for (int i = 0; i < 4; i++)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; j++) cudaEventDestroy(ev[j]);
+            (void)cudaGetLastError();
+            return SHEN_ERR_CUDA;
+        }
+    const int v0 = p.df_variant[problem];
+    float best = 0.f, best_df = 0.f;
+    Cand pick{SHEN_DF, v0};
+    int pick_df = v0;
+    cudaError_t e = cudaSuccess;
+    for (const Cand &c : cands) {
+        p.df_variant[problem] = c.variant;
+        // one untimed solve, then the median of three timed ones
+        e = launch_solve_range(p, problem, c.prec, 0, p.n_modes, f, u, s);
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int r = 0; r < 3 && e == cudaSuccess; r++) {
+            e = cudaEventRecord(ev[0], s);
+            if (e == cudaSuccess) e = launch_solve_range(p, problem, c.prec, 0, p.n_modes, f, u, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t[r], ev[0], ev[1]);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(t, t + 3);
+        if (best == 0.f || t[1] < best) {
+            best = t[1];
+            pick = c;
+        }
+        if (c.prec == SHEN_DF && (best_df == 0.f || t[1] < best_df)) {
+            best_df = t[1];
+            pick_df = c.variant;
+        }
+    }
+    for (int i = 0; i < 4; i++) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) {
+        p.df_variant[problem] = v0;
+        (void)cudaGetLastError();
+        return SHEN_ERR_CUDA;
+    }
+    // the faster float-float shape serves every float-float solve of this problem
+    p.auto_prec[problem] = pick.prec;
+    p.df_variant[problem] = pick_df;
+    if (chosen) *chosen = pick.prec;
+    if (ms) *ms = best;
     return SHEN_OK;
 }
 

@@ -53,6 +53,10 @@ struct Plan {
     int *d_err = nullptr;                 // [2]: flag, first bad class
     int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
     float *d_fac_df = nullptr;            // float-float factor tables (Helmholtz, biharmonic, per-N q/s)
+    // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
+    // runs, and the row-block shape of the float-float kernels
+    int auto_prec[2] = {5, 5};            // SHEN_DF until tuned
+    int df_variant[2] = {0, 0};
 
     long long device_bytes = 0;
 };

@@ -60,6 +60,8 @@ def test_null_plan_and_pointers_rejected(L):
     assert L.shen_biharmonic_solve(None, None, None, 0, None) == 1
     assert L.shen_rhs_matvec(None, 0, None, None, 0.0, None, None) == 1
     assert L.shen_solve_host(None, 0, None, None, 0, None) == 1
+    assert L.shen_plan_autotune(None, 0, None, None, None, None, None) == 1
+    assert L.shen_batch_autotune(None, 0, None, None, None, None, None) == 1
     assert L.shen_plan_info(None, None, None, None, None) == 1
     L.shen_plan_destroy(None)
     z = (ctypes.c_double * 2)(0.0, -1.0)

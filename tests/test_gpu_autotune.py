@@ -1,0 +1,70 @@
+"""GPU tests of the autotuner and of precision "auto".
+
+The autotuner picks among paths that all meet the 1e-10 bar, and its row-block shapes
+never change the arithmetic; so after tuning, an "auto" solve must equal the solve
+with the chosen precision bit for bit, and the float-float result must be the same
+bits as before tuning.
+"""
+import pytest
+
+from oracle import on
+from oracle import solve as so
+from paper_1701_03787_gb300 import BatchPlan, Plan, ShenError, inputs
+
+pytestmark = pytest.mark.gpu
+
+CANDIDATES = {"helmholtz": {"fp64", "df", "df_r1", "fp32_r1"}, "biharmonic": {"fp64", "df"}}
+
+
+@pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
+def test_plan_autotune_and_auto_precision(problem):
+    import torch
+    with Plan(384, 48, 32, 1 / 2000, 1e-4) as plan:
+        f = inputs.rhs_torch(plan.n_modes, plan.N, seed=41)
+        before = plan.solve(problem, f, precision="df")
+        u_default = plan.solve(problem, f, precision="auto")          # SHEN_DF until tuned
+        torch.cuda.synchronize()
+        assert torch.equal(u_default, before)
+        name, ms = plan.autotune(problem, f)
+        assert name in CANDIDATES[problem] and ms > 0
+        u_auto = plan.solve(problem, f, precision="auto")
+        u_named = plan.solve(problem, f, precision=name)
+        after = plan.solve(problem, f, precision="df")
+        torch.cuda.synchronize()
+        assert torch.equal(u_auto, u_named)
+        assert torch.equal(after, before)                              # shapes keep the bits
+        # the tuned result still meets the bar against the O(N) oracle
+        z2 = so.mode_z2(48, 32)
+        modes = [0, 5, plan.n_modes // 2, plan.n_modes - 1]
+        F = f[modes].cpu().numpy()
+        R = on.solve_modes(problem, 384, z2[modes], so.c_of(1 / 2000, 1e-4), F)
+        U = u_auto[modes].cpu().numpy()
+        n = so.n_unknowns(problem, 384)
+        assert max(so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))) < 1e-10
+
+
+@pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
+def test_batch_autotune_and_auto_precision(problem):
+    import torch
+    insts = inputs.batch_instances(64, seed=13)
+    with BatchPlan(insts) as bp:
+        f = inputs.batch_rhs_torch(bp.offsets, insts, seed=42)
+        before = bp.solve(problem, f, precision="df")
+        name, ms = bp.autotune(problem, f)
+        assert name in {"fp64", "df"} and ms > 0
+        u_auto = bp.solve(problem, f, precision="auto")
+        u_named = bp.solve(problem, f, precision=name)
+        after = bp.solve(problem, f, precision="df")
+        torch.cuda.synchronize()
+        bp.check_device()
+        assert torch.equal(u_auto, u_named)
+        assert torch.equal(after, before)
+
+
+def test_autotune_rejects_in_place_and_bad_problem():
+    with Plan(64, 8, 8, 1 / 180, 1e-3) as plan:
+        f = inputs.rhs_torch(plan.n_modes, plan.N, seed=43)
+        with pytest.raises(ShenError):
+            plan.autotune("helmholtz", f, f)
+        with pytest.raises(KeyError):
+            plan.autotune("poisson", f)
