@@ -131,6 +131,16 @@ def bind_gpu_local_host(pci):
     return info
 
 
+def max_over_ranks(values, pg, device):
+    """Element-wise maximum of a list of floats over all ranks (the list itself at one rank)."""
+    if pg is None:
+        return list(values)
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -237,6 +247,33 @@ def cpu_baseline(w, precision_note, seconds_target=8.0, seed=0):
                       f"{reps} repetitions, O(N) C oracle (Sec. 4 algorithms), float64"}
 
 
+def cpu_baseline_batch(w, seconds_target=8.0, seed=0):
+    """The oracle's O(N) C solvers on a bounded sample of the batching workload: every
+    mode of evenly spaced instances, until about `seconds_target` of solving."""
+    from oracle import on
+    from oracle import solve as so
+    from paper_1701_03787_gb300 import inputs
+    insts = inputs.batch_instances(w["n_inst"], seed=w["seed"])
+    picks = insts[::max(1, len(insts) // 256)]
+    rows, t_total, n_done = 0, 0.0, 0
+    t0 = time.perf_counter()
+    for inst in picks:
+        z2 = so.mode_z2(inst["Nx"], inst["Nz"], inst.get("Lx", 2 * math.pi), inst.get("Lz", math.pi))
+        F = inputs.rhs_numpy(z2.size, inst["N"], seed + n_done)
+        c = so.c_of(inst["nu"], inst["dt"])
+        t = time.perf_counter()
+        on.solve_modes("helmholtz", inst["N"], z2, c, F)
+        on.solve_modes("biharmonic", inst["N"], z2, c, F)
+        t_total += time.perf_counter() - t
+        rows += 2 * z2.size * inst["N"]
+        n_done += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    return {"value": rows / t_total, "unit": "solves*N/s", "cores": on.max_threads(), "kind": "oracle",
+            "sample": f"all modes of {n_done} of {len(insts)} instances (evenly spaced), Helmholtz + biharmonic, "
+                      f"O(N) C oracle (Sec. 4 algorithms), float64"}
+
+
 def oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined_modes):
     """Error of the GPU result vs the oracle: O(N) C oracle on `modes`, refined dense
     reference on `refined_modes` (both sets of mode indices)."""
@@ -276,12 +313,18 @@ def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    base = cpu_baseline(w, "reference", seconds_target=max(2.0, 2.0 * args.steps))
+    if "n_inst" in w:
+        base = cpu_baseline_batch(w, seconds_target=min(60.0, max(5.0, 0.5 * args.steps)))
+        from paper_1701_03787_gb300 import inputs
+        rows = sum((d["Nx"] // 2 + 1) * d["Nz"] * d["N"] for d in inputs.batch_instances(w["n_inst"], w["seed"]))
+    else:
+        base = cpu_baseline(w, "reference", seconds_target=max(2.0, 2.0 * args.steps))
+        rows = n_modes_of(w) * w["N"]
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": base["unit"],
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 2 * n_modes_of(w) * w["N"] / base["value"] * 1e3,
+            "ms_per_step": 2 * rows / base["value"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, **w, "n_modes": n_modes_of(w)},
+            "data": "synthetic", "config": {"workload": args.workload, **w, "rows": rows},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": base["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -454,10 +497,7 @@ def main():
               "frac_hbm": {"helmholtz": rows * 48 / (mh * 1e-3) / 1e9 / pk,
                            "biharmonic": rows * 48 / (mb * 1e-3) / 1e9 / pk}}
         del out
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, = max_over_ranks([ms], pg, "cuda")
     value = world * 2 * rows / (ms * 1e-3)
 
     # end to end through the public API with pinned host buffers
@@ -494,12 +534,15 @@ def main():
         stream.synchronize()
         k = max(1, min(args.steps, 3))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
         a.record(stream)
         for _ in range(k):
             e2e_step()
         b.record(stream)
         stream.synchronize()
-        e2e_ms = a.elapsed_time(b) / k
+        e2e_ms, = max_over_ranks([a.elapsed_time(b) / k], pg, "cuda")
         e2e = {"value": world * 2 * rows / (e2e_ms * 1e-3), "unit": "solves*N/s",
                "h2d_bytes_per_step": int(2 * rows * 16), "d2h_bytes_per_step": int(2 * rows * 16),
                "ms_per_step": e2e_ms, "path": "device copies + solves" if batched else "shen_solve_host",
@@ -583,8 +626,8 @@ def main():
         F_h, U_h = f_h[idx].cpu().numpy(), u_h[idx].cpu().numpy()
         F_b, U_b = f_b[idx].cpu().numpy(), u_b[idx].cpu().numpy()
         line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
-    if rank == 0 and not args.no_cpu and not batched:
-        line["cpu_baseline"] = cpu_baseline(w, args.precision)
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_batch(w) if batched else cpu_baseline(w, args.precision)
     if rank == 0:
         print(json.dumps(line))
     plan.close()
