@@ -38,6 +38,7 @@ WORKLOADS = {
     "batch": dict(n_inst=4096, seed=5),
 }
 METRIC = "Shen solves*N/s (Helmholtz + biharmonic, all modes)"
+LEAN_WORKLOADS = {"large"}
 BYTES_PER_ROW = 32          # algorithmic bytes per complex row of one solve: read f + write u
 
 
@@ -365,6 +366,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     prec = resolve_precision(args.precision)
+    # the large mixed workload (38.7 GB per field) runs lean: a plan with float-float
+    # factors only, the two mean-flow Helmholtz solves at mode (0, 0) in the step, and
+    # the end-to-end loop in place on two pinned host fields
+    lean = args.workload in LEAN_WORKLOADS
     stream = torch.cuda.Stream()
     batched = args.workload == "batch"
     t_plan = time.perf_counter()
@@ -377,7 +382,7 @@ def main():
         rows = plan.field_elems
     else:
         N = w["N"]
-        plan = Plan(N, w["Nx"], w["Nz"], w["nu"], w["dt"], stream=stream)
+        plan = Plan(N, w["Nx"], w["Nz"], w["nu"], w["dt"], stream=stream, df_only=lean)
         nm = plan.n_modes
         rows = nm * N
     t_plan = time.perf_counter() - t_plan
@@ -390,6 +395,9 @@ def main():
             f_b = inputs.rhs_torch(nm, N, seed=200 + rank)
         u_h = torch.empty_like(f_h)
         u_b = torch.empty_like(f_b)
+        if lean:
+            f_m = inputs.rhs_torch(2, N, seed=300 + rank)       # mean-flow loads (two components)
+            u_m = torch.empty_like(f_m)
     stream.synchronize()
     if batched:
         plan.helmholtz_solve = lambda f, u, precision, stream: plan.solve("helmholtz", f, u, precision, stream)
@@ -412,6 +420,9 @@ def main():
     fork, join_h, join_b = (torch.cuda.Event() for _ in range(3))
 
     def step(ph=prec["helmholtz"], pb=prec["biharmonic"]):
+        if lean:                               # mean flow: Helmholtz at z = 0, mode 0 only
+            plan.solve_modes("helmholtz", 0, f_m[0:1], u_m[0:1], precision=ph, stream=stream)
+            plan.solve_modes("helmholtz", 0, f_m[1:2], u_m[1:2], precision=ph, stream=stream)
         if args.streams == 1:
             plan.helmholtz_solve(f_h, u_h, precision=ph, stream=stream)
             plan.biharmonic_solve(f_b, u_b, precision=pb, stream=stream)
@@ -498,15 +509,38 @@ def main():
                            "biharmonic": rows * 48 / (mb * 1e-3) / 1e9 / pk}}
         del out
     ms, = max_over_ranks([ms], pg, "cuda")
-    value = world * 2 * rows / (ms * 1e-3)
+    step_rows = 2 * rows + (2 * N if lean else 0)            # complex rows solved per step
+    value = world * step_rows / (ms * 1e-3)
+
+    # oracle-check samples, gathered now (later phases may reuse the device fields)
+    sample = None
+    if rank == 0 and not args.no_check and not batched:
+        special = list(inputs.grid_modes(w["Nx"], w["Nz"]).values())
+        modes = inputs.sample_modes(nm, 0.01 if nm * N <= 1e9 else 0.002, 3, must_include=special)
+        refined = sorted(set(special) | set(modes[:: max(1, len(modes) // 8)]))
+        idx = torch.as_tensor(modes, device="cuda")
+        sample = (modes, refined, f_h[idx].cpu().numpy(), u_h[idx].cpu().numpy(),
+                  f_b[idx].cpu().numpy(), u_b[idx].cpu().numpy())
 
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hf_h = f_h.cpu().pin_memory()
-        hf_b = f_b.cpu().pin_memory()
-        hu = torch.empty_like(hf_h).pin_memory()
-        hu2 = torch.empty_like(hf_h).pin_memory()
+        def refill(h, t):                        # device -> pinned host, 256 MB copies
+            hv, tv = h.view(-1), t.view(-1)
+            for a0 in range(0, tv.numel(), 16 << 20):
+                hv[a0:a0 + (16 << 20)].copy_(tv[a0:a0 + (16 << 20)], non_blocking=True)
+            torch.cuda.synchronize()
+
+        def pinned_copy(t):
+            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            refill(h, t)
+            return h
+        hf_h, hf_b = pinned_copy(f_h), pinned_copy(f_b)
+        if lean:
+            hu, hu2 = hf_h, hf_b                 # in place: each step solves the previous result
+        else:
+            hu = torch.empty_like(hf_h).pin_memory()
+            hu2 = torch.empty_like(hf_b).pin_memory()
 
         if batched:
             def e2e_step():
@@ -546,15 +580,33 @@ def main():
         e2e = {"value": world * 2 * rows / (e2e_ms * 1e-3), "unit": "solves*N/s",
                "h2d_bytes_per_step": int(2 * rows * 16), "d2h_bytes_per_step": int(2 * rows * 16),
                "ms_per_step": e2e_ms, "path": "device copies + solves" if batched else "shen_solve_host",
-               "host": host_info}
-        # host link ceiling: both fields copied in and out at once on two streams
+               "in_place": lean, "host": host_info}
+        if not batched:
+            # the host results must be the device path's bit for bit: fresh inputs in the
+            # host buffers, one more step through the host path
+            if lean:
+                refill(hf_h, f_h)
+                refill(hf_b, f_b)
+            else:
+                hu.zero_()
+                hu2.zero_()
+            e2e_step()
+            stream.synchronize()
+            pick = torch.as_tensor(np.linspace(0, nm - 1, 257).astype(np.int64))
+            e2e["matches_device"] = bool(torch.equal(hu[pick], u_h[pick.cuda()].cpu())
+                                         and torch.equal(hu2[pick], u_b[pick.cuda()].cpu()))
+        # host link ceiling: plain copies of the same bytes in and out at once, 256 MB each
         la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         fork.record(stream)
         s_h.wait_event(fork)
         s_b.wait_event(fork)
         la.record(stream)
-        ce = 16 << 20                        # 256 MB copies (complex128 elements)
-        for dst, src, st in ((f_h, hf_h, s_h), (f_b, hf_b, s_h), (hu, u_h, s_b), (hu2, u_b, s_b)):
+        ce = 16 << 20
+        if lean:                                 # H2D of one field while the other comes back
+            pairs = ((f_h, hf_h, s_h), (hf_b, u_b, s_b))
+        else:
+            pairs = ((f_h, hf_h, s_h), (f_b, hf_b, s_h), (hu, u_h, s_b), (hu2, u_b, s_b))
+        for dst, src, st in pairs:
             dv, sv = dst.view(-1), src.view(-1)
             with torch.cuda.stream(st):
                 for e0_ in range(0, dv.numel(), ce):
@@ -565,25 +617,17 @@ def main():
         stream.wait_event(join_b)
         lb.record(stream)
         stream.synchronize()
-        link_gbs = 4 * rows * 16 / (la.elapsed_time(lb) * 1e-3) / 1e9
+        link_bytes = sum(d.numel() for d, _, _ in pairs) * 16
+        link_gbs = link_bytes / (la.elapsed_time(lb) * 1e-3) / 1e9
         e2e_gbs = 4 * rows * 16 / (e2e_ms * 1e-3) / 1e9
         e2e["roofline"] = {"bound": "host link (H2D + D2H concurrently)", "achieved": e2e_gbs, "peak": link_gbs,
                            "unit": "GB/s", "frac": e2e_gbs / link_gbs,
-                           "peak_kind": "measured in this run: plain copies of the same bytes"}
-        if not batched:
-            # the host results must be the device path's bit for bit (the link test left
-            # device copies in hu, hu2: clear them and solve once more through the host path)
-            hu.zero_()
-            hu2.zero_()
-            e2e_step()
-            stream.synchronize()
-            pick = torch.as_tensor(np.linspace(0, nm - 1, 257).astype(np.int64))
-            e2e["matches_device"] = bool(torch.equal(hu[pick], u_h[pick.cuda()].cpu())
-                                         and torch.equal(hu2[pick], u_b[pick.cuda()].cpu()))
+                           "peak_kind": "measured in this run: plain copies, both directions at once"}
+        del hf_h, hf_b, hu, hu2
 
     # the float64 path on the same fields, for the precision comparison
     fp64_ms = None
-    if not args.no_fp64_compare and (prec["helmholtz"] != "fp64" or prec["biharmonic"] != "fp64"):
+    if not args.no_fp64_compare and not lean and (prec["helmholtz"] != "fp64" or prec["biharmonic"] != "fp64"):
         for _ in range(2):
             step("fp64", "fp64")
         a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -615,16 +659,10 @@ def main():
                        if not batched else plan.device_bytes,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
-            "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk, "e2e": e2e,
+            "roofline": roofline, "gpu_launches": (4 if lean else 2) * args.steps, "clocks": clk, "e2e": e2e,
             "rhs_matvec": mv}
-    if rank == 0 and not args.no_check and not batched:
-        z2 = plan.n_modes
-        special = list(inputs.grid_modes(w["Nx"], w["Nz"]).values())
-        modes = inputs.sample_modes(nm, 0.01, 3, must_include=special)
-        refined = sorted(set(special) | set(modes[:: max(1, len(modes) // 8)]))
-        idx = torch.as_tensor(modes, device="cuda")
-        F_h, U_h = f_h[idx].cpu().numpy(), u_h[idx].cpu().numpy()
-        F_b, U_b = f_b[idx].cpu().numpy(), u_b[idx].cpu().numpy()
+    if sample is not None:
+        modes, refined, F_h, U_h, F_b, U_b = sample
         line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_batch(w) if batched else cpu_baseline(w, args.precision)

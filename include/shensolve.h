@@ -67,6 +67,9 @@ typedef enum {
 
 typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
 
+/* Plan creation flags. */
+#define SHEN_PLAN_DF_ONLY 1u
+
 /* Arithmetic of a solve.  All variants read and write float64 (complex128) fields and
  * use the same float64 LU factors (built once per plan); they differ in how the
  * sweeps run:
@@ -101,7 +104,11 @@ typedef enum {
  * (the paper's Re_tau = 2000 box is Lx = 2 pi, Lz = pi).  Builds the per-N tables,
  * groups modes by z2 (modes with equal z2 share one factorisation) and computes the
  * float64 LU factors of both systems for every distinct z2 on the device, on
- * `stream`.  Blocks until the plan is ready.  flags: must be 0.
+ * `stream`.  Blocks until the plan is ready.  flags: 0, or SHEN_PLAN_DF_ONLY to keep
+ * only the float-float factor tables (about half the device memory: the float64 factors
+ * are computed, converted and freed at creation); solves of such a plan accept
+ * SHEN_DF and SHEN_AUTO only (others: SHEN_ERR_UNSUPPORTED); shen_rhs_matvec, which
+ * uses no factors, is unaffected.
  * Errors: SHEN_ERR_ARG on bad sizes/parameters; SHEN_ERR_ALLOC; SHEN_ERR_CUDA;
  * SHEN_ERR_SINGULAR if a pivot is zero or not finite. */
 shen_status shen_plan_create(shen_plan_t *plan, int N, int Nx, int Nz, double nu, double dt,

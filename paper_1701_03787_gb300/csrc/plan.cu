@@ -95,7 +95,8 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
                            unsigned flags, void *stream) {
     if (!out) return SHEN_ERR_ARG;
     *out = nullptr;
-    if (flags != 0 || N < 8 || N > 4096 || n_modes < 1 || n_modes > (1L << 30) || !z2) return SHEN_ERR_ARG;
+    if ((flags & ~SHEN_PLAN_DF_ONLY) != 0 || N < 8 || N > 4096 || n_modes < 1 || n_modes > (1L << 30) || !z2)
+        return SHEN_ERR_ARG;
     if (!(nu > 0) || !(dt > 0) || !std::isfinite(nu) || !std::isfinite(dt)) return SHEN_ERR_ARG;
     const double c = 2.0 / (nu * dt);
     if (!std::isfinite(c)) return SHEN_ERR_ARG;
@@ -202,7 +203,8 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(dalloc(&p.d_fac_df, df_table_floats(p), B));
     PLAN_TRY(pack_df(p, s));
     // float32 factors in the lane layout of the warp-per-mode kernels
-    p.R_h = helm_mixed_R(N);
+    p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
+    p.R_h = p.df_only ? 0 : helm_mixed_R(N);
     if (p.R_h > 0) {
         PLAN_TRY(dalloc(&p.d_fac_h32, (size_t)p.n_classes * 2 * p.R_h * 16 * 2, B));
         PLAN_TRY(pack_helm_f32(p, p.R_h, reinterpret_cast<float2 *>(p.d_fac_h32), s));
@@ -212,6 +214,12 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(cudaMemcpyAsync(err_host, p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost, s));
     PLAN_TRY(cudaStreamSynchronize(s));
     if (err_host[0]) return fail(SHEN_ERR_SINGULAR);
+    if (p.df_only) {                     // the float-float tables are built: drop the float64 ones
+        cudaFree(p.d_fac_h);
+        cudaFree(p.d_fac_b);
+        p.d_fac_h = p.d_fac_b = nullptr;
+        B -= (long long)sizeof(double) * p.n_classes * 2 * ((long long)p.rows_h * kHelmF64 + (long long)p.rows_b * kBiF64);
+    }
 #undef PLAN_TRY
     *out = plan;
     return SHEN_OK;
@@ -227,6 +235,8 @@ bool overlap_ok(const double *a, const double *b, long n_doubles) {
 }
 
 shen_status check_precision(const Plan &p, int problem, int precision) {
+    if (p.df_only && precision != SHEN_DF)
+        return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
     if (precision == SHEN_FP64 || precision == SHEN_DF) return SHEN_OK;
     if (precision < SHEN_FP32_R1 || precision > SHEN_DF_R2) return SHEN_ERR_ARG;
     const bool r1 = precision == SHEN_FP32_R1 || precision == SHEN_DF_R1;
@@ -371,11 +381,10 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
     struct Cand {
         int prec, variant;
     };
-    std::vector<Cand> cands = {{SHEN_FP64, 0}, {SHEN_DF, 0}, {SHEN_DF, 1}};
-    if (problem == SHEN_HELMHOLTZ && check_precision(p, problem, SHEN_DF_R1) == SHEN_OK) {
-        cands.push_back({SHEN_DF_R1, 0});
-        cands.push_back({SHEN_FP32_R1, 0});
-    }
+    std::vector<Cand> cands;
+    for (Cand c : {Cand{SHEN_FP64, 0}, Cand{SHEN_DF, 0}, Cand{SHEN_DF, 1}, Cand{SHEN_DF_R1, 0},
+                   Cand{SHEN_FP32_R1, 0}})
+        if (check_precision(p, problem, c.prec) == SHEN_OK) cands.push_back(c);
     cudaStream_t s = as_stream(stream);
     cudaEvent_t ev[4];
     for (int i = 0; i < 4; i++)

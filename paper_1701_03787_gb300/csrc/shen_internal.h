@@ -55,6 +55,7 @@ struct Plan {
     float *d_fac_df = nullptr;            // float-float factor tables (Helmholtz, biharmonic, per-N q/s)
     // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
     // runs, and the row-block shape of the float-float kernels
+    bool df_only = false;                 // SHEN_PLAN_DF_ONLY: float64 factors freed after conversion
     int auto_prec[2] = {5, 5};            // SHEN_DF until tuned
     int df_variant[2] = {0, 0};
 

@@ -163,3 +163,25 @@ def test_error_statuses():
             plan.rhs_matvec("helmholtz", f, out=f)           # out aliases x
         assert e.value.status == 1
         plan.check_device()
+
+
+@pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
+def test_df_only_plan_gives_the_same_bits_with_less_memory(problem):
+    """A SHEN_PLAN_DF_ONLY plan keeps only the float-float factors: same float-float
+    result bit for bit, about half the device memory, other precisions unsupported."""
+    import torch
+    from paper_1701_03787_gb300 import Plan, ShenError, inputs
+    with Plan(300, 24, 20, 1 / 2000, 1e-4) as full, Plan(300, 24, 20, 1 / 2000, 1e-4, df_only=True) as lean:
+        f = inputs.rhs_torch(full.n_modes, full.N, seed=61)
+        a = full.solve(problem, f, precision="df")
+        b = lean.solve(problem, f, precision="df")
+        c = lean.solve(problem, f, precision="auto")
+        torch.cuda.synchronize()
+        assert torch.equal(a, b) and torch.equal(a, c)
+        assert lean.info()[3] < 0.6 * full.info()[3]
+        for prec in ("fp64", "df_r1", "fp32_r1"):
+            with pytest.raises(ShenError) as e:
+                lean.solve(problem, f, precision=prec)
+            assert e.value.status == 5
+        name, _ = lean.autotune(problem, f)
+        assert name == "df"
