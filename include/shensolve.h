@@ -120,7 +120,13 @@ shen_status shen_plan_create_z2(shen_plan_t *plan, int N, long n_modes, const do
                                 double nu, double dt, unsigned flags, void *stream);
 
 /* Helmholtz solve (alpha B - A) u = f for every mode of the plan. f, u: DEVICE
- * fields of n_modes * N complex values. */
+ * fields of n_modes * N complex values.
+ *
+ * Concurrency (all solve entry points of a plan): the float-float sweeps (SHEN_DF, and
+ * SHEN_AUTO when it resolves to it) spill their forward results to a scratch the plan
+ * holds per problem, so two float-float solves of the SAME problem on one plan must
+ * not run at the same time (issue them on one stream, or order the streams).  A
+ * Helmholtz and a biharmonic solve may overlap; other precisions use no scratch. */
 shen_status shen_helmholtz_solve(shen_plan_t plan, const double *f, double *u, int precision,
                                  void *stream);
 

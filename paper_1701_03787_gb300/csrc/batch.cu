@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                   (cl.z2 + in.c) * kPi / 2);
                 } else {
                     chains::solve_helm_df_chain<V>(in.N, par, f + off, u + off,
-                                                b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2,
-                                                df::from_f64((cl.z2 + in.c) * (kPi / 2)));
+                                                   b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2,
+                                                   df::from_f64((cl.z2 + in.c) * (kPi / 2)),
+                                                   chains::column_spill(u + off, par), 2);
                 }
             } else {
                 if (PREC == 0) {
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                 } else {
                     const float4 *F = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
                     chains::solve_bih_df_chain<V>(in.N, par, f + off, u + off, F, F + in.rows_b,
-                                               b.qs_df + (size_t)in.tab * b.qs_stride);
+                                                  b.qs_df + (size_t)in.tab * b.qs_stride,
+                                                  chains::column_spill(u + off, par), 2);
                 }
             }
         }

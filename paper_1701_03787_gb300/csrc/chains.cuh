@@ -267,7 +267,7 @@ __device__ __forceinline__ F2 fnma(F2 a, F2 y, F2 x) { return df::add(x, neg(df:
 // Helmholtz: F rows of two float4 (1/U0, U2) (l, 0) as (hi, lo); h = alpha pi / 2.
 template <int PB>
 __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol, double *ucol, const float4 *F,
-                                             F2 h) {
+                                             F2 h, float4 *ys, int ystride) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
     // Forward elimination y_i = f_i - l_i y_{i-1}.  Rows are fetched PB at a time into two
@@ -293,7 +293,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
                     const F2 l{lx[q].x, lx[q].y};
                     y.re = fnma(l, y.re, df::from_f64(fx[q].x));
                     y.im = fnma(l, y.im, df::from_f64(fx[q].y));
-                    store_cf2(ucol, 2 * (i0 + q) + par, y);
+                    ys[(long)(i0 + q) * ystride] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
                 }
             }
         };
@@ -313,7 +313,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = max(i0 - q, 0);
-                yx[q] = reinterpret_cast<const float4 *>(ucol)[2 * i + par];
+                yx[q] = ys[(long)i * ystride];
                 ax[q] = F[2 * i];
             }
         };
@@ -384,7 +384,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // also requested into L2, so that the register loads find them there.
 template <int PBF, int PBB, int PFD, bool QSD>
 __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
-                                            const float4 *Fb, const float4 *qs) {
+                                            const float4 *Fb, const float4 *qs, float4 *ys, int ystride) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
     const F2 zero{0.f, 0.f};
@@ -411,7 +411,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
                     // the y_{i-2} term first: only the last step waits for y_{i-1}
                     y.re = fnma(L1, y1.re, fnma(L2, y2.re, df::from_f64(fx[q].x)));
                     y.im = fnma(L1, y1.im, fnma(L2, y2.im, df::from_f64(fx[q].y)));
-                    store_cf2(ucol, 2 * (i0 + q) + par, y);
+                    ys[(long)(i0 + q) * ystride] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
                     y2 = y1;
                     y1 = y;
                 }
@@ -448,7 +448,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = max(i0 - q, 0);
-                yx[q] = reinterpret_cast<const float4 *>(ucol)[2 * i + par];
+                yx[q] = ys[(long)i * ystride];
                 bx[q] = Fb[3 * i];
                 cx[q] = Fb[3 * i + 1];
                 dx[q] = Fb[3 * i + 2];
@@ -491,7 +491,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
         // chain rows (b - 2 PB, b]: column rows [2a, 2b + 2) and Fb rows [3a, 3b + 3)
         auto prefetch = [&](int b) {
             const int a = max(b - 2 * PB + 1, 0);
-            if (PFD > 0 && b >= 0 && a <= b) {
+            if (PFD > 0 && b >= 0 && a <= b && ystride == 2) {
                 prefetch_l2(ucol + 4 * a, 32u * (b - a + 1));
                 prefetch_l2(Fb + 3 * a, 48u * (b - a + 1));
             }
@@ -517,20 +517,30 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
 //   Helmholtz  V0: 8 rows per block (154 registers);  V1: 4 rows per block
 //   biharmonic V0: the tuning constants above (124 registers, 16 warps per SM);
 //              V1: 4 + 4 rows, (q, s) prefetched (204 registers, 8 warps per SM)
+//
+// The forward result y (float-float, 16 bytes per complex row) is spilled to ys[i * ystride]
+// for chain row i: either the chain's own rows of the output column (ys = column + par,
+// ystride = 2; no scratch memory) or a scratch laid out [row][lane] per warp (ystride =
+// 32), where each warp's spill of a row is 512 contiguous bytes.
 template <int V>
 __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *F,
-                                           F2 h) {
-    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h);
+                                           F2 h, float4 *ys, int ystride) {
+    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride);
 }
 
 template <int V>
 __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
-                                          const float4 *Fb, const float4 *qs) {
+                                          const float4 *Fb, const float4 *qs, float4 *ys, int ystride) {
     if (V == 0)
         solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_PFD, SHEN_BIH_DF_QSD != 0>(
-            N, par, fcol, ucol, Ff, Fb, qs);
+            N, par, fcol, ucol, Ff, Fb, qs, ys, ystride);
     else
-        solve_bih_df_chain_t<4, 4, 0, false>(N, par, fcol, ucol, Ff, Fb, qs);
+        solve_bih_df_chain_t<4, 4, 0, false>(N, par, fcol, ucol, Ff, Fb, qs, ys, ystride);
+}
+
+// The output column's own rows of chain `par`, as a spill target (ystride 2).
+__device__ __forceinline__ float4 *column_spill(double *ucol, int par) {
+    return reinterpret_cast<float4 *>(ucol) + par;
 }
 
 }  // namespace chains

@@ -10,6 +10,8 @@
 // side by side.  The forward sweep writes y (float-float, 16 bytes per complex row)
 // into the output column and the back substitution reads it back in reverse and
 // overwrites it with u (float64), so the kernels use no scratch memory and u == f works.
+#include <algorithm>
+
 #include "chains.cuh"
 
 namespace shen {
@@ -22,8 +24,8 @@ struct WorkItem {
     int cls, par;
 };
 
-__device__ __forceinline__ bool work_item(const Plan &p, const int *order, long m0, long count, WorkItem &w) {
-    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ bool work_item(const Plan &p, const int *order, long m0, long count, long tid,
+                                          WorkItem &w) {
     if (tid >= 2 * count) return false;
     const long item = tid >> 1;
     w.par = (int)(tid & 1);
@@ -33,26 +35,41 @@ __device__ __forceinline__ bool work_item(const Plan &p, const int *order, long 
     return true;
 }
 
+// Both kernels run a fixed grid of resident blocks.  Warp slot w (one per resident warp)
+// takes the warp-sized groups of chains w, w + W, w + 2 W, ... (W slots) and spills its
+// forward results to its own [row][lane] slice of the plan's scratch.
 template <int V>
 __global__ void __launch_bounds__(128) helm_df_kernel(Plan p, const int *order, long m0, long count,
-                                                      const double *f, double *u, const float4 *fac) {
-    WorkItem w;
-    if (!work_item(p, order, m0, count, w)) return;
-    const long off = 2 * w.col * p.N;
-    const F2 h = df::from_f64((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
-    chains::solve_helm_df_chain<V>(p.N, w.par, f + off, u + off, fac + ((size_t)w.cls * 2 + w.par) * p.rows_h * 2,
-                                   h);
+                                                      const double *f, double *u, const float4 *fac, float4 *scr) {
+    const int lane = threadIdx.x & 31;
+    const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
+    float4 *ys = scr + slot * (long)p.rows_h * 32 + lane;
+    for (long t0 = slot * 32; t0 < 2 * count; t0 += nslots * 32) {
+        WorkItem w;
+        if (!work_item(p, order, m0, count, t0 + lane, w)) continue;
+        const long off = 2 * w.col * p.N;
+        const F2 h = df::from_f64((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
+        chains::solve_helm_df_chain<V>(p.N, w.par, f + off, u + off,
+                                       fac + ((size_t)w.cls * 2 + w.par) * p.rows_h * 2, h, ys, 32);
+    }
 }
 
 template <int V>
 __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, long m0, long count,
                                                      const double *f, double *u, const float4 *fac,
-                                                     const float4 *qs) {
-    WorkItem w;
-    if (!work_item(p, order, m0, count, w)) return;
-    const long off = 2 * w.col * p.N;
-    const float4 *F = fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4;   // rows_b (L1, L2), then 3 rows_b
-    chains::solve_bih_df_chain<V>(p.N, w.par, f + off, u + off, F, F + p.rows_b, qs);
+                                                     const float4 *qs, float4 *scr) {
+    const int lane = threadIdx.x & 31;
+    const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
+    float4 *ys = scr + slot * (long)p.rows_b * 32 + lane;
+    for (long t0 = slot * 32; t0 < 2 * count; t0 += nslots * 32) {
+        WorkItem w;
+        if (!work_item(p, order, m0, count, t0 + lane, w)) continue;
+        const long off = 2 * w.col * p.N;
+        const float4 *F = fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4;   // rows_b (L1, L2), then 3 rows_b
+        chains::solve_bih_df_chain<V>(p.N, w.par, f + off, u + off, F, F + p.rows_b, qs, ys, 32);
+    }
 }
 
 __device__ __forceinline__ float2 split2(double x) {
@@ -121,16 +138,44 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
     const float4 *h = reinterpret_cast<const float4 *>(p.d_fac_df);
     const float4 *b = h + (size_t)p.n_classes * 2 * p.rows_h * 2;
     const float4 *q = b + (size_t)p.n_classes * 2 * p.rows_b * 4;
-    const unsigned g = nblocks(2 * count, 128);
-    const int v = p.df_variant[problem == SHEN_HELMHOLTZ ? 0 : 1];
+    const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
+    const int v = p.df_variant[pb];
+    // never more blocks than the scratch has warp slots for (df_setup sized it for this grid)
+    const unsigned g = (unsigned)std::min<long>(nblocks(2 * count, 128), p.df_grid[pb][v]);
     if (problem == SHEN_HELMHOLTZ) {
-        if (v == 0) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h);
-        else helm_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h);
+        if (v == 0) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h, p.d_ys[0]);
+        else helm_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h, p.d_ys[0]);
     } else {
-        if (v == 0) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q);
-        else bih_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q);
+        if (v == 0) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q, p.d_ys[1]);
+        else bih_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q, p.d_ys[1]);
     }
     return cudaGetLastError();
+}
+
+cudaError_t df_setup(Plan &p, long long &bytes) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const void *kern[2][2] = {{(const void *)helm_df_kernel<0>, (const void *)helm_df_kernel<1>},
+                              {(const void *)bih_df_kernel<0>, (const void *)bih_df_kernel<1>}};
+    // a launch covers at most all the plan's chains: no more blocks than that
+    const int needed = (int)std::min<long>(nblocks(2 * p.n_modes, 128), 1L << 30);
+    for (int pb = 0; pb < 2; pb++) {
+        int most = 1;
+        for (int v = 0; v < 2; v++) {
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[pb][v], 128, 0);
+            if (e != cudaSuccess) return e;
+            p.df_grid[pb][v] = std::min(std::max(1, per_sm) * sms, needed);
+            most = std::max(most, p.df_grid[pb][v]);
+        }
+        const size_t n = (size_t)most * 4 * (pb == 0 ? p.rows_h : p.rows_b) * 32;   // float4
+        bytes += (long long)(n * sizeof(float4));
+        e = cudaMalloc((void **)&p.d_ys[pb], n * sizeof(float4));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace shen

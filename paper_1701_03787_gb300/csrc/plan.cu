@@ -82,6 +82,8 @@ void free_plan(Plan &p) {
     cudaFree(p.d_fac_b32);
     cudaFree(p.d_err);
     cudaFree(p.d_fac_df);
+    cudaFree(p.d_ys[0]);
+    cudaFree(p.d_ys[1]);
     p = Plan{};
 }
 
@@ -202,6 +204,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     // float-float copies of the factors for the float-float sweeps
     PLAN_TRY(dalloc(&p.d_fac_df, df_table_floats(p), B));
     PLAN_TRY(pack_df(p, s));
+    PLAN_TRY(df_setup(p, B));
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);

@@ -56,6 +56,10 @@ struct Plan {
     // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
     // runs, and the row-block shape of the float-float kernels
     bool df_only = false;                 // SHEN_PLAN_DF_ONLY: float64 factors freed after conversion
+    // float-float kernels: fixed grid of resident blocks per [problem][shape], and the
+    // per-problem spill scratch of the forward result, [warp slot][chain row][lane]
+    int df_grid[2][2] = {{0, 0}, {0, 0}};
+    float4 *d_ys[2] = {nullptr, nullptr};
     int auto_prec[2] = {5, 5};            // SHEN_DF until tuned
     int df_variant[2] = {0, 0};
 
@@ -81,6 +85,7 @@ size_t df_table_floats(const Plan &p);
 cudaError_t pack_df(const Plan &p, cudaStream_t s);
 cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                             cudaStream_t s);
+cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of the float-float kernels
 
 }  // namespace shen
 
