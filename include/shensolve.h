@@ -226,6 +226,9 @@ shen_status shen_batch_info(shen_batch_t batch, long *n_modes, long *field_elems
 shen_status shen_batch_offsets(shen_batch_t batch, long *offsets);
 
 /* Solve every mode of every instance: problem SHEN_HELMHOLTZ or SHEN_BIHARMONIC,
+ * (float-float solves spill their forward results to a scratch the plan holds per
+ * problem; like the per-problem work queue, this allows a Helmholtz and a biharmonic
+ * solve to overlap, but not two solves of the same problem on one plan) 
  * precision SHEN_FP64, SHEN_DF or SHEN_AUTO (others: SHEN_ERR_UNSUPPORTED).  f, u: DEVICE batched
  * fields (u == f allowed).  Layout and zeroed trailing entries as for single plans. */
 shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, double *u, int precision,

@@ -45,6 +45,10 @@ struct BatchDev {
     float4 *fdf_h, *fdf_b;          // float-float factors, 2 / 4 float4 per row
     int *queue;
     int *err;
+    // float-float spill scratch per problem, [warp slot][row][lane] (ys_rows rows per
+    // slot); null: spill through the output column instead
+    float4 *ys[2];
+    int ys_rows[2];
 };
 
 namespace {
@@ -104,6 +108,11 @@ __global__ void batch_pack_qs_kernel(BatchDev b, int n_tabs, const int *tab_N) {
 template <int PREC, int PROBLEM, int V>
 __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const double *f, double *u) {
     const int lane = threadIdx.x & 31;
+    const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    float4 *const scr = b.ys[PROBLEM == SHEN_HELMHOLTZ ? 0 : 1];
+    float4 *const ys_slot = (PREC == 1 && scr)
+                                ? scr + slot * (long)b.ys_rows[PROBLEM == SHEN_HELMHOLTZ ? 0 : 1] * 32 + lane
+                                : nullptr;
     for (;;) {
         int base = 0;
         if (lane == 0) base = atomicAdd(b.queue, 16);
@@ -125,7 +134,8 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                     chains::solve_helm_df_chain<V>(in.N, par, f + off, u + off,
                                                    b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2,
                                                    df::from_f64((cl.z2 + in.c) * (kPi / 2)),
-                                                   chains::column_spill(u + off, par), 2);
+                                                   ys_slot ? ys_slot : chains::column_spill(u + off, par),
+                                                   ys_slot ? 32 : 2);
                 }
             } else {
                 if (PREC == 0) {
@@ -136,7 +146,8 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                     const float4 *F = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
                     chains::solve_bih_df_chain<V>(in.N, par, f + off, u + off, F, F + in.rows_b,
                                                   b.qs_df + (size_t)in.tab * b.qs_stride,
-                                                  chains::column_spill(u + off, par), 2);
+                                                  ys_slot ? ys_slot : chains::column_spill(u + off, par),
+                                                  ys_slot ? 32 : 2);
                 }
             }
         }
@@ -379,6 +390,18 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
                 B_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(pr, pb, v), 128, 0));
                 b->grid[pr][pb][v] = std::max(1, sms * std::max(per_sm, 1));
             }
+    // float-float spill scratch per problem: one [row][lane] slice per warp slot of the
+    // larger float-float grid, rows of the largest instance
+    int rows_max[2] = {1, 1};
+    for (const BatchInst &in : inst) {
+        rows_max[0] = std::max(rows_max[0], in.rows_h);
+        rows_max[1] = std::max(rows_max[1], in.rows_b);
+    }
+    for (int pb = 0; pb < 2; pb++) {
+        const long slots = 4L * std::max(b->grid[1][pb][0], b->grid[1][pb][1]);
+        B_TRY(balloc(b, &b->d.ys[pb], (size_t)slots * rows_max[pb] * 32));
+        b->d.ys_rows[pb] = rows_max[pb];
+    }
 #undef B_TRY
     *out = b;
     return SHEN_OK;
@@ -575,6 +598,7 @@ extern "C" shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem,
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_status(e);
     BatchDev D = batch->d;
+    D.ys[0] = D.ys[1] = nullptr;              // spill through the output column: no plan scratch
     D.queue = scratch;
     e = launch_batch(batch, D, problem, precision, f, u, s);
     return e == cudaSuccess ? SHEN_OK : cuda_status(e);
