@@ -179,6 +179,15 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
 shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y,
                             double beta, double *out, void *stream);
 
+/* Same operator with a choice of arithmetic: precision SHEN_FP64 (as shen_rhs_matvec)
+ * or SHEN_DF (SHEN_AUTO means SHEN_DF): each row's terms summed in float-float
+ * arithmetic from float-float row tables, the running sums of the upper-triangular
+ * parts carried in float-float, and + beta y as one float64 fused multiply-add.
+ * Relative error of order 1e-14 against the float64 operator.  Other precisions:
+ * SHEN_ERR_UNSUPPORTED.  Arguments and errors as shen_rhs_matvec. */
+shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
+                               double *out, int precision, void *stream);
+
 /* Plan facts: number of modes, number of distinct z2 (factorisations), device bytes
  * held by the plan.  Any output pointer may be NULL. */
 shen_status shen_plan_info(shen_plan_t plan, long *n_modes, long *n_classes, long *N,

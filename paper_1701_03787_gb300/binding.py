@@ -45,6 +45,7 @@ def lib():
         "shen_biharmonic_solve": ([P, P, P, I, P], I),
         "shen_solve_modes": ([P, I, Lg, Lg, P, P, I, P], I),
         "shen_rhs_matvec": ([P, I, P, P, D, P, P], I),
+        "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_solve_host": ([P, I, P, P, I, P], I),
         "shen_plan_info": ([P, P, P, P, P], I),
         "shen_plan_check": ([P, P], I),
@@ -226,7 +227,7 @@ class Plan:
                                     _stream(stream)), "shen_solve_host")
         return u
 
-    def rhs_matvec(self, problem, x, y=None, beta=0.0, out=None, stream=None):
+    def rhs_matvec(self, problem, x, y=None, beta=0.0, out=None, stream=None, precision="fp64"):
         import torch
         _field_ok(x, self.n_modes, self.N, "x")
         if y is not None:
@@ -234,8 +235,8 @@ class Plan:
         if out is None:
             out = torch.empty_like(x)
         _field_ok(out, self.n_modes, self.N, "out")
-        check(lib().shen_rhs_matvec(self._h, _problem(problem), _ptr(x), _ptr(y), float(beta), _ptr(out),
-                                    _stream(stream)), "shen_rhs_matvec")
+        check(lib().shen_rhs_matvec_ex(self._h, _problem(problem), _ptr(x), _ptr(y), float(beta), _ptr(out),
+                                       _prec(precision), _stream(stream)), "shen_rhs_matvec_ex")
         return out
 
     def autotune(self, problem, f, u=None, stream=None):

@@ -82,6 +82,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_fac_b32);
     cudaFree(p.d_err);
     cudaFree(p.d_fac_df);
+    cudaFree(p.d_mv_df);
     cudaFree(p.d_ys[0]);
     cudaFree(p.d_ys[1]);
     p = Plan{};
@@ -205,6 +206,8 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(dalloc(&p.d_fac_df, df_table_floats(p), B));
     PLAN_TRY(pack_df(p, s));
     PLAN_TRY(df_setup(p, B));
+    PLAN_TRY(dalloc(&p.d_mv_df, matvec_df_floats(p), B));
+    PLAN_TRY(pack_matvec_df(p, p.d_mv_df, s));
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);
@@ -321,6 +324,24 @@ shen_status shen_biharmonic_solve(shen_plan_t plan, const double *f, double *u, 
 shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, long mode_count, const double *f,
                              double *u, int precision, void *stream) {
     return solve_range(plan, problem, mode_begin, mode_count, f, u, precision, stream);
+}
+
+shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
+                               double *out, int precision, void *stream) {
+    if (precision == SHEN_AUTO) precision = SHEN_DF;
+    if (precision != SHEN_FP64 && precision != SHEN_DF)
+        return precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2 ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
+    if (precision == SHEN_FP64) return shen_rhs_matvec(plan, problem, x, y, beta, out, stream);
+    if (!plan || !x || !out) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
+    const long nd = 2 * p.n_modes * (long)p.N;
+    if (x == out || (y && y == out)) return SHEN_ERR_ARG;
+    if (!overlap_ok(x, out, nd) || !overlap_ok(y, out, nd)) return SHEN_ERR_ARG;
+    if (y && !std::isfinite(beta)) return SHEN_ERR_ARG;
+    SHEN_CUDA_TRY(launch_matvec_df(p, problem, x, y, beta, out, as_stream(stream)));
+    return SHEN_OK;
 }
 
 shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,

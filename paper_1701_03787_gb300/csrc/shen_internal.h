@@ -53,6 +53,7 @@ struct Plan {
     int *d_err = nullptr;                 // [2]: flag, first bad class
     int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
     float *d_fac_df = nullptr;            // float-float factor tables (Helmholtz, biharmonic, per-N q/s)
+    float *d_mv_df = nullptr;             // float-float row tables of the rhs_matvec operators
     // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
     // runs, and the row-block shape of the float-float kernels
     bool df_only = false;                 // SHEN_PLAN_DF_ONLY: float64 factors freed after conversion
@@ -86,6 +87,12 @@ cudaError_t pack_df(const Plan &p, cudaStream_t s);
 cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                             cudaStream_t s);
 cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of the float-float kernels
+
+// matvec_df.cu
+size_t matvec_df_floats(const Plan &p);
+cudaError_t pack_matvec_df(const Plan &p, float *T, cudaStream_t s);
+cudaError_t launch_matvec_df(const Plan &p, int problem, const double *x, const double *y, double beta,
+                             double *out, cudaStream_t s);
 
 }  // namespace shen
 

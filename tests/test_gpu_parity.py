@@ -104,24 +104,51 @@ def test_in_place_and_shards(problem):
         assert np.array_equal(np.concatenate(parts), full)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
 @pytest.mark.parametrize("problem", PROBLEMS)
-def test_rhs_matvec(problem):
-    """out = R x + beta y against the dense right-hand-side operators of Eqs. gfin / ufin."""
-    N, Nx, Nz, nu, dt = 64, 16, 16, 1 / 180, 1e-3
+@pytest.mark.parametrize("N,Nx,Nz,nu,dt", [(64, 16, 16, 1 / 180, 1e-3), (257, 12, 10, 1 / 2000, 1e-4),
+                                          (9, 4, 4, 1e-2, 1e-2)])
+def test_rhs_matvec(problem, precision, N, Nx, Nz, nu, dt):
+    """out = R x + beta y against the dense right-hand-side operators of Eqs. gfin / ufin,
+    in float64 and float-float arithmetic (inputs beyond the unknowns are ignored)."""
     c = so.c_of(nu, dt)
     z2 = so.mode_z2(Nx, Nz)
     X = inputs.rhs_numpy(z2.size, N, seed=6)
     Y = inputs.rhs_numpy(z2.size, N, seed=7)
     n = so.n_unknowns(problem, N)
     with Plan(N, Nx, Nz, nu, dt) as plan:
-        O1 = to_host(plan.rhs_matvec(problem, to_dev(X)))
-        O2 = to_host(plan.rhs_matvec(problem, to_dev(X), to_dev(Y), beta=-0.75))
+        O1 = to_host(plan.rhs_matvec(problem, to_dev(X), precision=precision))
+        O2 = to_host(plan.rhs_matvec(problem, to_dev(X), to_dev(Y), beta=-0.75, precision=precision))
     for m in range(z2.size):
         r1 = so.matvec_mode(problem, N, z2[m], c, X[m])
         r2 = so.matvec_mode(problem, N, z2[m], c, X[m], Y[m], -0.75)
         assert so.rel_l2(O1[m, :n], r1) <= 1e-13, m
         assert so.rel_l2(O2[m, :n], r2) <= 1e-13, m
         assert np.all(O1[m, n:] == 0)
+
+
+@pytest.mark.parametrize("problem", PROBLEMS)
+def test_rhs_matvec_df_full_size_sampled(problem):
+    """Float-float operator at N = 1024 against the float64 operator (all modes) and the
+    dense oracle operator (sampled modes, including the largest z2)."""
+    import torch
+    N, Nx, Nz, nu, dt = 1024, 64, 64, 1 / 2000, 1e-4
+    c = so.c_of(nu, dt)
+    z2 = so.mode_z2(Nx, Nz)
+    n = so.n_unknowns(problem, N)
+    with Plan(N, Nx, Nz, nu, dt) as plan:
+        x = inputs.rhs_torch(plan.n_modes, N, seed=71)
+        y = inputs.rhs_torch(plan.n_modes, N, seed=72)
+        a = plan.rhs_matvec(problem, x, y, beta=0.5, precision="df")
+        b = plan.rhs_matvec(problem, x, y, beta=0.5, precision="fp64")
+        torch.cuda.synchronize()
+        d = torch.linalg.vector_norm(a - b, dim=1) / torch.linalg.vector_norm(b, dim=1)
+        assert float(d.max()) < 1e-13
+        modes = sorted({0, int(np.argmax(z2)), plan.n_modes // 3, plan.n_modes - 1})
+        A, X, Y = a[modes].cpu().numpy(), x[modes].cpu().numpy(), y[modes].cpu().numpy()
+    for i, m in enumerate(modes):
+        r = so.matvec_mode(problem, N, z2[m], c, X[i], Y[i], 0.5)
+        assert so.rel_l2(A[i, :n], r) <= 1e-13, m
 
 
 @pytest.mark.parametrize("problem", PROBLEMS)
