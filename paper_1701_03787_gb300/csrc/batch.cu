@@ -42,7 +42,11 @@ struct BatchDev {
     const float4 *qs_df;            // per table set: N_max + 8 entries each
     int qs_stride;
     double *fac_h, *fac_b;          // float64 factors, kHelmF64 / kBiF64 doubles per row
-    float4 *fdf_h, *fdf_b;          // float-float factors, 2 / 4 float4 per row
+    // float-float factor streams, one block of rows per chain (stride 1), indexed by the
+    // chain-row offsets of the float64 factors: Helmholtz hb (1/U0, U2), hf l;
+    // biharmonic bf (L1, L2), bb0 (1/U0, U1), bb1 (U2, ta), bb2 tb
+    float4 *df_hb, *df_bf, *df_bb0, *df_bb1;
+    float2 *df_hf, *df_bb2;
     int *queue;
     int *err;
     // float-float spill scratch per problem, [warp slot][row][lane] (ys_rows rows per
@@ -66,26 +70,25 @@ __global__ void batch_factor_kernel(BatchDev b) {
     chains::factor_helm_chain(T, in.N, cl.z2, in.c, par, Fh, in.rows_h, b.err, c);
     chains::factor_bih_chain(T, in.N, cl.z2, in.c, par, Fb, in.rows_b, b.err, c);
     // float-float copies (hi, lo) of the same rows
-    float4 *Dh = b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2;
-    float4 *Db = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
+    const long oh = cl.fh + (long)par * in.rows_h, ob = cl.fb + (long)par * in.rows_b;
     auto split = [](double x) {
         const float hi = (float)x;
         return make_float2(hi, (float)(x - (double)hi));
     };
     for (int i = 0; i < in.rows_h; i++) {
         const double *r = Fh + i * kHelmF64;
-        const float2 a = split(r[0]), bb = split(r[1]), l = split(r[2]);
-        Dh[2 * i] = make_float4(a.x, a.y, bb.x, bb.y);
-        Dh[2 * i + 1] = make_float4(l.x, l.y, 0.f, 0.f);
+        const float2 a = split(r[0]), bb = split(r[1]);
+        b.df_hb[oh + i] = make_float4(a.x, a.y, bb.x, bb.y);
+        b.df_hf[oh + i] = split(r[2]);
     }
-    for (int i = 0; i < in.rows_b; i++) {          // rows_b (L1, L2), then 3 rows_b float4
+    for (int i = 0; i < in.rows_b; i++) {
         const double *r = Fb + i * kBiF64;
         float2 v[7];
         for (int q = 0; q < 7; q++) v[q] = split(r[q]);
-        Db[i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-        Db[in.rows_b + 3 * i] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-        Db[in.rows_b + 3 * i + 1] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
-        Db[in.rows_b + 3 * i + 2] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
+        b.df_bf[ob + i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        b.df_bb0[ob + i] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+        b.df_bb1[ob + i] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
+        b.df_bb2[ob + i] = v[6];
     }
 }
 
@@ -131,8 +134,9 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                   b.fac_h + (cl.fh + (long)par * in.rows_h) * kHelmF64,
                                                   (cl.z2 + in.c) * kPi / 2);
                 } else {
+                    const long oh = cl.fh + (long)par * in.rows_h;
                     chains::solve_helm_df_chain<V>(in.N, par, f + off, u + off,
-                                                   b.fdf_h + (cl.fh + (long)par * in.rows_h) * 2,
+                                                   chains::HelmDF{b.df_hb + oh, b.df_hf + oh, 1},
                                                    df::from_f64((cl.z2 + in.c) * (kPi / 2)),
                                                    ys_slot ? ys_slot : chains::column_spill(u + off, par),
                                                    ys_slot ? 32 : 2);
@@ -143,8 +147,10 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                  b.fac_b + (cl.fb + (long)par * in.rows_b) * kBiF64,
                                                  b.tabs[in.tab].qk, b.tabs[in.tab].sk);
                 } else {
-                    const float4 *F = b.fdf_b + (cl.fb + (long)par * in.rows_b) * 4;
-                    chains::solve_bih_df_chain<V>(in.N, par, f + off, u + off, F, F + in.rows_b,
+                    const long ob = cl.fb + (long)par * in.rows_b;
+                    chains::solve_bih_df_chain<V>(in.N, par, f + off, u + off,
+                                                  chains::BihDF{b.df_bf + ob, b.df_bb0 + ob, b.df_bb1 + ob,
+                                                                b.df_bb2 + ob, 1},
                                                   b.qs_df + (size_t)in.tab * b.qs_stride,
                                                   ys_slot ? ys_slot : chains::column_spill(u + off, par),
                                                   ys_slot ? 32 : 2);
@@ -350,8 +356,12 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
     B_TRY(balloc(b, &d_qs, (size_t)n_tabs * D.qs_stride));
     B_TRY(balloc(b, &D.fac_h, (size_t)fh * kHelmF64));
     B_TRY(balloc(b, &D.fac_b, (size_t)fb * kBiF64));
-    B_TRY(balloc(b, &D.fdf_h, (size_t)fh * 2));
-    B_TRY(balloc(b, &D.fdf_b, (size_t)fb * 4));
+    B_TRY(balloc(b, &D.df_hb, (size_t)fh));
+    B_TRY(balloc(b, &D.df_hf, (size_t)fh));
+    B_TRY(balloc(b, &D.df_bf, (size_t)fb));
+    B_TRY(balloc(b, &D.df_bb0, (size_t)fb));
+    B_TRY(balloc(b, &D.df_bb1, (size_t)fb));
+    B_TRY(balloc(b, &D.df_bb2, (size_t)fb));
     B_TRY(balloc(b, &D.queue, 2));                   // one work-queue counter per problem
     B_TRY(balloc(b, &D.err, 2));
     B_TRY(cudaMemcpyAsync(d_tabs, tabs_h.data(), tabs_h.size() * sizeof(RowTables), cudaMemcpyHostToDevice, s));

@@ -265,9 +265,24 @@ __device__ __forceinline__ void store_f64(double *col, int k, CF2 v) {
 __device__ __forceinline__ F2 fnma(F2 a, F2 y, F2 x) { return df::add(x, neg(df::mul(a, y))); }
 
 // Helmholtz: F rows of two float4 (1/U0, U2) (l, 0) as (hi, lo); h = alpha pi / 2.
+// Float-float factor streams of one chain, row i at [i * s]: Helmholtz b = (1/U0, U2),
+// f = l; biharmonic f = (L1, L2), b0 = (1/U0, U1), b1 = (U2, ta), b2 = tb (each value as
+// hi, lo).  s = 1 for a chain stored as one block; s = the number of chains when rows
+// are interleaved across chains (a warp's lanes then read adjacent entries).
+struct HelmDF {
+    const float4 *b;
+    const float2 *f;
+    long s;
+};
+struct BihDF {
+    const float4 *f, *b0, *b1;
+    const float2 *b2;
+    long s;
+};
+
 template <int PB>
-__device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol, double *ucol, const float4 *F,
-                                             F2 h, float4 *ys, int ystride) {
+__device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
+                                             float4 *ys, int ystride) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
     // Forward elimination y_i = f_i - l_i y_{i-1}.  Rows are fetched PB at a time into two
@@ -277,16 +292,16 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
     CF2 y{F2{0.f, 0.f}, F2{0.f, 0.f}};
     {
         double2 fa[PB], fb[PB];
-        float4 la[PB], lb[PB];
-        auto load = [&](double2 (&fx)[PB], float4 (&lx)[PB], int i0) {
+        float2 la[PB], lb[PB];
+        auto load = [&](double2 (&fx)[PB], float2 (&lx)[PB], int i0) {
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = min(i0 + q, rows - 1);
                 fx[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
-                lx[q] = F[2 * i + 1];
+                lx[q] = F.f[(long)i * F.s];
             }
         };
-        auto run = [&](const double2 (&fx)[PB], const float4 (&lx)[PB], int i0) {
+        auto run = [&](const double2 (&fx)[PB], const float2 (&lx)[PB], int i0) {
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 if (i0 + q < rows) {
@@ -314,7 +329,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
             for (int q = 0; q < PB; q++) {
                 const int i = max(i0 - q, 0);
                 yx[q] = ys[(long)i * ystride];
-                ax[q] = F[2 * i];
+                ax[q] = F.b[(long)i * F.s];
             }
         };
         auto run = [&](const float4 (&yx)[PB], const float4 (&ax)[PB], int i0) {
@@ -353,7 +368,6 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 // Tuning constants of the biharmonic float-float chain (compile-time; -D overrides):
 //   PBF / PBB  rows per register prefetch block in the forward / backward sweep (two
 //              blocks in flight)
-//   PFD        distance, in rows, of the L2 bulk prefetch ahead of the sweep (0: off)
 //   QSD        1: read the per-N (q, s) table at use (L1-resident) instead of prefetching
 #ifndef SHEN_BIH_DF_PBF
 #define SHEN_BIH_DF_PBF 4
@@ -361,30 +375,18 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 #ifndef SHEN_BIH_DF_PBB
 #define SHEN_BIH_DF_PBB 2
 #endif
-#ifndef SHEN_BIH_DF_PFD
-#define SHEN_BIH_DF_PFD 0
-#endif
 #ifndef SHEN_BIH_DF_QSD
 #define SHEN_BIH_DF_QSD 1
 #endif
 
-// Bulk prefetch of [p, p + bytes) into L2 (no registers, no completion to wait for).
-// p 16-byte aligned, bytes a multiple of 16; callers pass ranges inside their arrays.
-__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes));
-}
-
-// Biharmonic float-float chain.  Factors of the chain: Ff[i] = (L1, L2) for the forward
-// elimination and Fb[3 i .. 3 i + 2] = (1/U0, U1) (U2, ta) (tb, 0) for the back
-// substitution, each value as (hi, lo) (separate streams, so each sweep reads only the
-// bytes it uses); qs: per-N (q_k, s_k) float-float by k, zero beyond the unknowns.
-// Rows are fetched PB at a time into two register buffers, the next block's loads
-// issued before the current block is computed; all loads of a block precede its stores
-// (which may alias f when u == f).  With PFD > 0 the rows PFD ahead of each block are
-// also requested into L2, so that the register loads find them there.
-template <int PBF, int PBB, int PFD, bool QSD>
-__device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
-                                            const float4 *Fb, const float4 *qs, float4 *ys, int ystride) {
+// Biharmonic float-float chain (Algorithm LUSolveBiharmonic with the Eq. ab tail).
+// qs: per-N (q_k, s_k) float-float by k, zero beyond the unknowns.  Rows are fetched PB
+// at a time into two register buffers, the next block's loads issued before the
+// current block is computed; all loads of a block precede its stores (which may alias f
+// when u == f).
+template <int PBF, int PBB, bool QSD>
+__device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, double *ucol, BihDF F,
+                                            const float4 *qs, float4 *ys, int ystride) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
     const F2 zero{0.f, 0.f};
@@ -399,7 +401,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
             for (int q = 0; q < PB; q++) {
                 const int i = min(i0 + q, rows - 1);
                 fx[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
-                lx[q] = Ff[i];
+                lx[q] = F.f[(long)i * F.s];
             }
         };
         auto run = [&](const double2 (&fx)[PB], const float4 (&lx)[PB], int i0) {
@@ -417,19 +419,8 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
                 }
             }
         };
-        // chain rows [a, b): column rows [2a, 2b) (both parities) and Ff rows [a, b)
-        auto prefetch = [&](int a) {
-            const int b = min(a + 2 * PB, rows);
-            if (PFD > 0 && a < b) {
-                prefetch_l2(fcol + 4 * a, 32u * (b - a));
-                prefetch_l2(Ff + a, 16u * (b - a));
-            }
-        };
-        if (PFD > 0)
-            for (int a = 0; a < PFD; a += 2 * PB) prefetch(a);
         load(fa, la, 0);
         for (int i0 = 0; i0 < rows; i0 += 2 * PB) {
-            prefetch(i0 + PFD);
             load(fb, lb, i0 + PB);
             run(fa, la, i0);
             load(fa, la, i0 + 2 * PB);
@@ -442,21 +433,23 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
     {
         constexpr int PB = PBB;
         constexpr int NQ = QSD ? 1 : PB;
-        float4 ya[PB], yb[PB], ba[PB], bb[PB], ca[PB], cb[PB], da[PB], db[PB], qa[NQ], qb[NQ];
-        auto load = [&](float4 (&yx)[PB], float4 (&bx)[PB], float4 (&cx)[PB], float4 (&dx)[PB], float4 (&qx)[NQ],
+        float4 ya[PB], yb[PB], ba[PB], bb[PB], ca[PB], cb[PB], qa[NQ], qb[NQ];
+        float2 da[PB], db[PB];
+        auto load = [&](float4 (&yx)[PB], float4 (&bx)[PB], float4 (&cx)[PB], float2 (&dx)[PB], float4 (&qx)[NQ],
                         int i0) {
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = max(i0 - q, 0);
+                const long r = (long)i * F.s;
                 yx[q] = ys[(long)i * ystride];
-                bx[q] = Fb[3 * i];
-                cx[q] = Fb[3 * i + 1];
-                dx[q] = Fb[3 * i + 2];
+                bx[q] = F.b0[r];
+                cx[q] = F.b1[r];
+                dx[q] = F.b2[r];
                 if (!QSD) qx[q < NQ ? q : 0] = qs[2 * i + par + 6];
             }
         };
         auto run = [&](const float4 (&yx)[PB], const float4 (&bx)[PB], const float4 (&cx)[PB],
-                       const float4 (&dx)[PB], const float4 (&qx)[NQ], int i0) {
+                       const float2 (&dx)[PB], const float4 (&qx)[NQ], int i0) {
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = i0 - q;
@@ -488,19 +481,8 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
                 }
             }
         };
-        // chain rows (b - 2 PB, b]: column rows [2a, 2b + 2) and Fb rows [3a, 3b + 3)
-        auto prefetch = [&](int b) {
-            const int a = max(b - 2 * PB + 1, 0);
-            if (PFD > 0 && b >= 0 && a <= b && ystride == 2) {
-                prefetch_l2(ucol + 4 * a, 32u * (b - a + 1));
-                prefetch_l2(Fb + 3 * a, 48u * (b - a + 1));
-            }
-        };
-        if (PFD > 0)
-            for (int b = rows - 1; b > rows - 1 - PFD; b -= 2 * PB) prefetch(b);
         load(ya, ba, ca, da, qa, rows - 1);
         for (int i0 = rows - 1; i0 >= 0; i0 -= 2 * PB) {
-            prefetch(i0 - PFD);
             load(yb, bb, cb, db, qb, i0 - PB);
             run(ya, ba, ca, da, qa, i0);
             load(ya, ba, ca, da, qa, i0 - 2 * PB);
@@ -523,19 +505,19 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
 // ystride = 2; no scratch memory) or a scratch laid out [row][lane] per warp (ystride =
 // 32), where each warp's spill of a row is 512 contiguous bytes.
 template <int V>
-__device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *F,
-                                           F2 h, float4 *ys, int ystride) {
+__device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
+                                           float4 *ys, int ystride) {
     solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride);
 }
 
 template <int V>
-__device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, const float4 *Ff,
-                                          const float4 *Fb, const float4 *qs, float4 *ys, int ystride) {
+__device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, BihDF F,
+                                          const float4 *qs, float4 *ys, int ystride) {
     if (V == 0)
-        solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_PFD, SHEN_BIH_DF_QSD != 0>(
-            N, par, fcol, ucol, Ff, Fb, qs, ys, ystride);
+        solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_QSD != 0>(N, par, fcol, ucol, F, qs, ys,
+                                                                                    ystride);
     else
-        solve_bih_df_chain_t<4, 4, 0, false>(N, par, fcol, ucol, Ff, Fb, qs, ys, ystride);
+        solve_bih_df_chain_t<4, 4, false>(N, par, fcol, ucol, F, qs, ys, ystride);
 }
 
 // The output column's own rows of chain `par`, as a spill target (ystride 2).

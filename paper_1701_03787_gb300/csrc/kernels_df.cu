@@ -40,7 +40,7 @@ __device__ __forceinline__ bool work_item(const Plan &p, const int *order, long 
 // forward results to its own [row][lane] slice of the plan's scratch.
 template <int V>
 __global__ void __launch_bounds__(128) helm_df_kernel(Plan p, const int *order, long m0, long count,
-                                                      const double *f, double *u, const float4 *fac, float4 *scr) {
+                                                      const double *f, double *u, float4 *scr) {
     const int lane = threadIdx.x & 31;
     const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
     const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
@@ -50,15 +50,15 @@ __global__ void __launch_bounds__(128) helm_df_kernel(Plan p, const int *order, 
         if (!work_item(p, order, m0, count, t0 + lane, w)) continue;
         const long off = 2 * w.col * p.N;
         const F2 h = df::from_f64((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
-        chains::solve_helm_df_chain<V>(p.N, w.par, f + off, u + off,
-                                       fac + ((size_t)w.cls * 2 + w.par) * p.rows_h * 2, h, ys, 32);
+        const long ch = 2L * w.cls + w.par, nch = 2 * p.n_classes;
+        chains::solve_helm_df_chain<V>(p.N, w.par, f + off, u + off, chains::HelmDF{p.df_hb + ch, p.df_hf + ch, nch},
+                                       h, ys, 32);
     }
 }
 
 template <int V>
 __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, long m0, long count,
-                                                     const double *f, double *u, const float4 *fac,
-                                                     const float4 *qs, float4 *scr) {
+                                                     const double *f, double *u, float4 *scr) {
     const int lane = threadIdx.x & 31;
     const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
     const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, l
         WorkItem w;
         if (!work_item(p, order, m0, count, t0 + lane, w)) continue;
         const long off = 2 * w.col * p.N;
-        const float4 *F = fac + ((size_t)w.cls * 2 + w.par) * p.rows_b * 4;   // rows_b (L1, L2), then 3 rows_b
-        chains::solve_bih_df_chain<V>(p.N, w.par, f + off, u + off, F, F + p.rows_b, qs, ys, 32);
+        const long ch = 2L * w.cls + w.par, nch = 2 * p.n_classes;
+        chains::solve_bih_df_chain<V>(p.N, w.par, f + off, u + off,
+                                      chains::BihDF{p.df_bf + ch, p.df_bb0 + ch, p.df_bb1 + ch, p.df_bb2 + ch, nch},
+                                      p.df_qs, ys, 32);
     }
 }
 
@@ -77,29 +79,32 @@ __device__ __forceinline__ float2 split2(double x) {
     return make_float2(hi, (float)(x - (double)hi));
 }
 
-__global__ void pack_helm_df_kernel(Plan p, float4 *out) {
-    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;      // row of all chains
-    if (t >= p.n_classes * 2 * (long)p.rows_h) return;
+// Float-float factor streams from the float64 factors, rows interleaved across chains:
+// row i of chain ch = 2 class + parity goes to [i * nch + ch], nch = 2 n_classes.
+__global__ void pack_helm_df_kernel(Plan p, float4 *hb, float2 *hf) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;      // chain-major row index
+    const long nch = 2 * p.n_classes;
+    if (t >= nch * p.rows_h) return;
+    const long ch = t / p.rows_h, i = t % p.rows_h;
     const double *row = p.d_fac_h + t * kHelmF64;                    // 1/U0, U2, l
-    const float2 a = split2(row[0]), b = split2(row[1]), c = split2(row[2]);
-    out[2 * t] = make_float4(a.x, a.y, b.x, b.y);
-    out[2 * t + 1] = make_float4(c.x, c.y, 0.f, 0.f);
+    const float2 a = split2(row[0]), b = split2(row[1]);
+    hb[i * nch + ch] = make_float4(a.x, a.y, b.x, b.y);
+    hf[i * nch + ch] = split2(row[2]);
 }
 
-// Per chain: rows_b float4 (L1, L2) for the forward elimination, then 3 rows_b float4
-// (1/U0, U1) (U2, ta) (tb, 0) for the back substitution, each value as (hi, lo).
-__global__ void pack_bih_df_kernel(Plan p, float4 *out) {
+__global__ void pack_bih_df_kernel(Plan p, float4 *bf, float4 *bb0, float4 *bb1, float2 *bb2) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (t >= p.n_classes * 2 * (long)p.rows_b) return;
-    const long chain = t / p.rows_b, i = t % p.rows_b;
+    const long nch = 2 * p.n_classes;
+    if (t >= nch * p.rows_b) return;
+    const long ch = t / p.rows_b, i = t % p.rows_b;
     const double *row = p.d_fac_b + t * kBiF64;                      // L1 L2 1/U0 U1 U2 ta tb
     float2 v[7];
     for (int q = 0; q < 7; q++) v[q] = split2(row[q]);
-    float4 *Ff = out + chain * p.rows_b * 4, *Fb = Ff + p.rows_b;
-    Ff[i] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    Fb[3 * i] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-    Fb[3 * i + 1] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
-    Fb[3 * i + 2] = make_float4(v[6].x, v[6].y, 0.f, 0.f);
+    const long o = i * nch + ch;
+    bf[o] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    bb0[o] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    bb1[o] = make_float4(v[4].x, v[4].y, v[5].x, v[5].y);
+    bb2[o] = v[6];
 }
 
 __global__ void pack_qs_df_kernel(Plan p, float4 *out) {
@@ -117,17 +122,32 @@ inline unsigned nblocks(long threads, int bs) { return (unsigned)((threads + bs 
 
 }  // namespace
 
+// Backing store: float4 streams first (16-byte aligned), then the float2 streams.
 size_t df_table_floats(const Plan &p) {
-    return (size_t)p.n_classes * 2 * ((size_t)p.rows_h * 8 + (size_t)p.rows_b * 16) + (size_t)(p.N + 8) * 4;
+    const size_t nch = 2 * (size_t)p.n_classes;
+    return nch * ((size_t)p.rows_h * 4 + (size_t)p.rows_b * 12) + (size_t)(p.N + 8) * 4 +
+           nch * ((size_t)p.rows_h * 2 + (size_t)p.rows_b * 2);
 }
 
-cudaError_t pack_df(const Plan &p, cudaStream_t s) {
-    float4 *h = reinterpret_cast<float4 *>(p.d_fac_df);
-    float4 *b = h + (size_t)p.n_classes * 2 * p.rows_h * 2;
-    float4 *q = b + (size_t)p.n_classes * 2 * p.rows_b * 4;
-    pack_helm_df_kernel<<<nblocks(p.n_classes * 2 * (long)p.rows_h, 256), 256, 0, s>>>(p, h);
-    pack_bih_df_kernel<<<nblocks(p.n_classes * 2 * (long)p.rows_b, 256), 256, 0, s>>>(p, b);
-    pack_qs_df_kernel<<<nblocks(p.N + 8, 256), 256, 0, s>>>(p, q);
+cudaError_t pack_df(Plan &p, cudaStream_t s) {
+    const size_t nch = 2 * (size_t)p.n_classes;
+    float4 *hb = reinterpret_cast<float4 *>(p.d_fac_df);
+    float4 *bf = hb + nch * p.rows_h;
+    float4 *bb0 = bf + nch * p.rows_b;
+    float4 *bb1 = bb0 + nch * p.rows_b;
+    float4 *qs = bb1 + nch * p.rows_b;
+    float2 *hf = reinterpret_cast<float2 *>(qs + p.N + 8);
+    float2 *bb2 = hf + nch * p.rows_h;
+    p.df_hb = hb;
+    p.df_hf = hf;
+    p.df_bf = bf;
+    p.df_bb0 = bb0;
+    p.df_bb1 = bb1;
+    p.df_bb2 = bb2;
+    p.df_qs = qs;
+    pack_helm_df_kernel<<<nblocks((long)nch * p.rows_h, 256), 256, 0, s>>>(p, hb, hf);
+    pack_bih_df_kernel<<<nblocks((long)nch * p.rows_b, 256), 256, 0, s>>>(p, bf, bb0, bb1, bb2);
+    pack_qs_df_kernel<<<nblocks(p.N + 8, 256), 256, 0, s>>>(p, qs);
     return cudaGetLastError();
 }
 
@@ -135,19 +155,16 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
                             cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int *order = (m0 == 0 && count == p.n_modes) ? p.d_order : nullptr;
-    const float4 *h = reinterpret_cast<const float4 *>(p.d_fac_df);
-    const float4 *b = h + (size_t)p.n_classes * 2 * p.rows_h * 2;
-    const float4 *q = b + (size_t)p.n_classes * 2 * p.rows_b * 4;
     const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
     const int v = p.df_variant[pb];
     // never more blocks than the scratch has warp slots for (df_setup sized it for this grid)
     const unsigned g = (unsigned)std::min<long>(nblocks(2 * count, 128), p.df_grid[pb][v]);
     if (problem == SHEN_HELMHOLTZ) {
-        if (v == 0) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h, p.d_ys[0]);
-        else helm_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, h, p.d_ys[0]);
+        if (v == 0) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[0]);
+        else helm_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[0]);
     } else {
-        if (v == 0) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q, p.d_ys[1]);
-        else bih_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, b, q, p.d_ys[1]);
+        if (v == 0) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[1]);
+        else bih_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[1]);
     }
     return cudaGetLastError();
 }

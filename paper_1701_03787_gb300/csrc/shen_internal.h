@@ -52,7 +52,11 @@ struct Plan {
     float *d_fac_h32 = nullptr, *d_fac_b32 = nullptr;
     int *d_err = nullptr;                 // [2]: flag, first bad class
     int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
-    float *d_fac_df = nullptr;            // float-float factor tables (Helmholtz, biharmonic, per-N q/s)
+    float *d_fac_df = nullptr;            // backing store of the float-float factor streams below
+    // float-float factor streams, row i of chain ch = 2 class + parity at [i * 2 n_classes + ch]
+    const float4 *df_hb = nullptr, *df_bf = nullptr, *df_bb0 = nullptr, *df_bb1 = nullptr;
+    const float2 *df_hf = nullptr, *df_bb2 = nullptr;
+    const float4 *df_qs = nullptr;        // per-N (q_k, s_k), N + 8 entries
     float *d_mv_df = nullptr;             // float-float row tables of the rhs_matvec operators
     // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
     // runs, and the row-block shape of the float-float kernels
@@ -83,7 +87,7 @@ cudaError_t launch_helm_mixed(const Plan &p, bool dfres, long m0, long count, co
 
 // kernels_df.cu
 size_t df_table_floats(const Plan &p);
-cudaError_t pack_df(const Plan &p, cudaStream_t s);
+cudaError_t pack_df(Plan &p, cudaStream_t s);
 cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                             cudaStream_t s);
 cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of the float-float kernels
