@@ -509,7 +509,9 @@ def main():
             mb = float(np.mean([e[1].elapsed_time(e[2]) for e in evm]))
             mv[mprec] = {"helmholtz_ms": mh, "biharmonic_ms": mb,
                          "frac_hbm": {"helmholtz": rows * 48 / (mh * 1e-3) / 1e9 / pk,
-                                      "biharmonic": rows * 48 / (mb * 1e-3) / 1e9 / pk}}
+                                      "biharmonic": rows * 48 / (mb * 1e-3) / 1e9 / pk},
+                         "traffic": {"helmholtz": measured_traffic(f"matvec_helmholtz:{mprec}", rows),
+                                     "biharmonic": measured_traffic(f"matvec_biharmonic:{mprec}", rows)}}
         del out
     ms, = max_over_ranks([ms], pg, "cuda")
     step_rows = 2 * rows + (2 * N if lean else 0)            # complex rows solved per step
