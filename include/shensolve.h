@@ -155,6 +155,25 @@ shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, lon
 shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
                             void *stream);
 
+/* A posteriori check of a solve: for every mode, the relative residual
+ * ||f - H u||_2 / ||f||_2 over the unknowns, H the Helmholtz or biharmonic system
+ * matrix of the plan (Eqs. Helmholtz_matrix, Biharmonic_matrix in the scaled form of
+ * shen_helmholtz_solve / shen_biharmonic_solve).  H u is evaluated in float-float
+ * arithmetic, the difference and the norms in float64; relative residuals are resolved
+ * down to about 1e-14 (Helmholtz) and 1e-12 (biharmonic, whose Q tail p_k q_j + r_k s_j
+ * cancels between its two terms).  f, u: DEVICE fields of the plan; rel: DEVICE array of n_modes
+ * doubles, or NULL.  The largest value is also kept by the plan for
+ * shen_last_error_detail.  Asynchronous on `stream`. */
+shen_status shen_residual(shen_plan_t plan, int problem, const double *f, const double *u, double *rel,
+                          void *stream);
+
+/* Synchronous error detail of the plan: *max_rel_residual (may be NULL) = the largest
+ * relative residual found by the plan's last shen_residual (0 before any), and
+ * *n_singular (may be NULL) = the number of (class, parity) factorisations that met a
+ * zero or non-finite pivot when the plan was built (such a plan is refused at creation
+ * with SHEN_ERR_SINGULAR, so this is 0 for every plan a caller holds). */
+shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, long *n_singular);
+
 /* Time the candidate paths of `problem` on this plan and record the fastest for
  * SHEN_AUTO.  The candidates are the paths that meet a 1e-10 per-mode relative error
  * bar against the float64 oracle in the library's parity tests:

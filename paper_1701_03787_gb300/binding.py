@@ -46,6 +46,8 @@ def lib():
         "shen_solve_modes": ([P, I, Lg, Lg, P, P, I, P], I),
         "shen_rhs_matvec": ([P, I, P, P, D, P, P], I),
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
+        "shen_residual": ([P, I, P, P, P, P], I),
+        "shen_last_error_detail": ([P, P, P], I),
         "shen_solve_host": ([P, I, P, P, I, P], I),
         "shen_plan_info": ([P, P, P, P, P], I),
         "shen_plan_check": ([P, P], I),
@@ -251,6 +253,25 @@ class Plan:
         check(lib().shen_plan_autotune(self._h, _problem(problem), _ptr(f), _ptr(u), ctypes.byref(chosen),
                                        ctypes.byref(ms), _stream(stream)), "shen_plan_autotune")
         return PRECISION_NAMES[chosen.value], ms.value
+
+    def residual(self, problem, f, u, rel=None, stream=None):
+        """Per-mode relative residual ||f - H u|| / ||f|| (float64 CUDA tensor of n_modes)."""
+        import torch
+        _field_ok(f, self.n_modes, self.N, "f")
+        _field_ok(u, self.n_modes, self.N, "u")
+        if rel is None:
+            rel = torch.empty(self.n_modes, dtype=torch.float64, device=f.device)
+        if rel.dtype != torch.float64 or not rel.is_cuda or not rel.is_contiguous() or rel.numel() != self.n_modes:
+            raise ValueError("rel must be a contiguous float64 CUDA tensor of n_modes entries")
+        check(lib().shen_residual(self._h, _problem(problem), _ptr(f), _ptr(u), _ptr(rel), _stream(stream)),
+              "shen_residual")
+        return rel
+
+    def error_detail(self):
+        """(largest relative residual of the last residual(), factorisations with a bad pivot)."""
+        mx, ns = ctypes.c_double(), ctypes.c_long()
+        check(lib().shen_last_error_detail(self._h, ctypes.byref(mx), ctypes.byref(ns)), "shen_last_error_detail")
+        return mx.value, ns.value
 
     def check_device(self):
         where = ctypes.c_long()

@@ -363,7 +363,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
     B_TRY(balloc(b, &D.df_bb1, (size_t)fb));
     B_TRY(balloc(b, &D.df_bb2, (size_t)fb));
     B_TRY(balloc(b, &D.queue, 2));                   // one work-queue counter per problem
-    B_TRY(balloc(b, &D.err, 2));
+    B_TRY(balloc(b, &D.err, 4));
     B_TRY(cudaMemcpyAsync(d_tabs, tabs_h.data(), tabs_h.size() * sizeof(RowTables), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemcpyAsync(d_inst, inst.data(), inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemcpyAsync(d_cls, cls.data(), cls.size() * sizeof(BatchCls), cudaMemcpyHostToDevice, s));
@@ -371,7 +371,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
     B_TRY(cudaMemcpyAsync(d_mc, mode_cls.data(), mode_cls.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemcpyAsync(d_work, work.data(), work.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemcpyAsync(d_tabN, b->tab_N.data(), b->tab_N.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    const int err_init[2] = {0, 0x7fffffff};
+    const int err_init[4] = {0, 0x7fffffff, 0, 0};
     B_TRY(cudaMemcpyAsync(D.err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, s));
     D.inst = d_inst;
     D.cls = d_cls;

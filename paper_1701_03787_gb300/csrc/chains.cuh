@@ -11,6 +11,7 @@
 namespace shen {
 namespace chains {
 
+// err[0]: any bad pivot; err[1]: smallest class with one; err[2]: number of chains with one
 __device__ __forceinline__ void flag_error(int *err, long cls) {
     atomicExch(err, 1);
     atomicMin(err + 1, (int)cls);
@@ -38,6 +39,7 @@ __device__ inline void factor_helm_chain(const RowTables &T, int N, double z2, d
     const double alpha = z2 + c;
     const double h = alpha * kPi / 2;
     double U0 = 0, U2 = 0;
+    bool bad = false;
     for (int i = 0; i < rows; i++) {
         const int k = 2 * i + par;
         const double t = -T.adt[k];
@@ -52,7 +54,10 @@ __device__ inline void factor_helm_chain(const RowTables &T, int N, double z2, d
             U0 = Mii - l * U1prev;
             U2 = t - l * U2;
         }
-        if (bad_pivot(U0)) flag_error(err, cls);
+        if (bad_pivot(U0)) {
+            flag_error(err, cls);
+            bad = true;
+        }
         F[i * kHelmF64 + 0] = 1.0 / U0;
         F[i * kHelmF64 + 1] = U2;
         F[i * kHelmF64 + 2] = l;
@@ -60,6 +65,7 @@ __device__ inline void factor_helm_chain(const RowTables &T, int N, double z2, d
     }
     for (int i = rows; i < rows_max; i++)
         for (int v = 0; v < kHelmF64; v++) F[i * kHelmF64 + v] = 0.0;
+    if (bad) atomicAdd(err + 2, 1);
 }
 
 // Biharmonic, per parity chain (k = 2i + p), H = Q + ca A + cb B:
@@ -78,6 +84,7 @@ __device__ inline void factor_bih_chain(const RowTables &T, int N, double z2, do
     // state of rows i-1 (suffix 1) and i-2 (suffix 2)
     double U0_1 = 0, U1_1 = 0, U2_1 = 0, ta_1 = 0, tb_1 = 0;
     double U0_2 = 0, U1_2 = 0, U2_2 = 0, ta_2 = 0, tb_2 = 0;
+    bool bad = false;
     for (int i = 0; i < rows; i++) {
         const int k = 2 * i + par;
         auto q = [&](int kk) { return T.qk[kk]; };
@@ -108,7 +115,10 @@ __device__ inline void factor_bih_chain(const RowTables &T, int N, double z2, do
         double ta = T.pk[k], tb = T.rk[k];
         if (i >= 1) { ta -= L1 * ta_1; tb -= L1 * tb_1; }
         if (i >= 2) { ta -= L2 * ta_2; tb -= L2 * tb_2; }
-        if (bad_pivot(U0)) flag_error(err, cls);
+        if (bad_pivot(U0)) {
+            flag_error(err, cls);
+            bad = true;
+        }
         double *row = F + i * kBiF64;
         row[0] = L1; row[1] = L2; row[2] = 1.0 / U0; row[3] = U1;
         row[4] = U2; row[5] = (i + 3 < rows) ? ta : 0.0; row[6] = (i + 3 < rows) ? tb : 0.0; row[7] = 0.0;
@@ -117,6 +127,7 @@ __device__ inline void factor_bih_chain(const RowTables &T, int N, double z2, do
     }
     for (int i = rows; i < rows_max; i++)
         for (int v = 0; v < kBiF64; v++) F[i * kBiF64 + v] = 0.0;
+    if (bad) atomicAdd(err + 2, 1);
 }
 
 // ------------------------------------------------------------- float64 sweeps

@@ -9,6 +9,11 @@
 //                           ga = c - 2 z2, gb = z2 (z2 - c)
 // (sums over the same parity; entries beyond the unknowns are zero), then out = R x + beta y.
 //
+// The same kernels also evaluate the system operators of the solves (MODE 1):
+//   H_h = (z2 + c) B - A      and      H_b = Q - (2 z2 + c) A + z2 (z2 + c) B,
+// i.e. the RHS structure with other scalars, for the a posteriori residual
+// ||f - H u|| / ||f|| of each mode (no vector written, only the per-mode norms).
+//
 // One thread per (mode, parity) chain walks its rows from the top down, carrying the
 // running sums of the upper-triangular parts (the suffix sums of Sec. 4) and a window
 // of five neighbouring x values in registers; x is read once, y once, out written once.
@@ -78,18 +83,46 @@ __device__ __forceinline__ bool chain_of(const Plan &p, long tid, Chain &c) {
     return true;
 }
 
+// Residual accumulation of one chain: sum |f_k - (H u)_k|^2 and sum |f_k|^2 over its rows
+// (float64); the two chains of a mode (adjacent lanes) are combined at the end.
+struct Res {
+    double rr = 0.0, ff = 0.0;
+    __device__ __forceinline__ void add(const double *f, int k, CF2 hu) {
+        const double2 fk = reinterpret_cast<const double2 *>(f)[k];
+        const double dr = fk.x - df::to_f64(hu.re), di = fk.y - df::to_f64(hu.im);
+        rr = fma(dr, dr, fma(di, di, rr));
+        ff = fma(fk.x, fk.x, fma(fk.y, fk.y, ff));
+    }
+    // lane pair (2j, 2j + 1) = both chains of one mode; both are always active together
+    __device__ __forceinline__ void finish(const Plan &p, const Chain &c, double *rel) {
+        const unsigned pair = 3u << ((threadIdx.x & 31) & ~1u);
+        const double r2 = rr + __shfl_xor_sync(pair, rr, 1);
+        const double f2 = ff + __shfl_xor_sync(pair, ff, 1);
+        if (c.par == 0) {
+            const double q = f2 > 0.0 ? sqrt(r2 / f2) : (r2 > 0.0 ? INFINITY : 0.0);
+            if (rel) rel[c.col / (2 * p.N)] = q;
+            // non-negative doubles order like their bit patterns
+            atomicMax(p.d_resmax, (unsigned long long)__double_as_longlong(q));
+        }
+    }
+};
+
 // Helmholtz table row k: T[2k] = (B_kk, A_kk), T[2k + 1] = (A_tail(k), 0), each (hi, lo).
+template <int MODE>
 __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const float4 *T, const double *x,
-                                                                  const double *y, double beta, double *out) {
+                                                                  const double *y, double beta, double *out,
+                                                                  double *rel) {
     Chain c;
     if (!chain_of(p, blockIdx.x * (long)blockDim.x + threadIdx.x, c)) return;
     const int N = p.N, n = N - 2, par = c.par;
     const int rows = (n - par + 1) / 2;
     const double *xc_ = x + c.col;
     const double *yc_ = y ? y + c.col : nullptr;
-    double *oc = out + c.col;
-    const F2 g = df::from_f64(p.c - c.z2);
-    const F2 gm = df::from_f64(-(p.c - c.z2) * (kPi / 2));      // g B_{k,k+-2}
+    double *oc = MODE == 0 ? out + c.col : nullptr;
+    const double gd = MODE == 0 ? p.c - c.z2 : p.c + c.z2;       // coefficient of B
+    const F2 g = df::from_f64(gd);
+    const F2 gm = df::from_f64(-gd * (kPi / 2));                 // g B_{k,k+-2}
+    Res res;
     const F2 zero{0.f, 0.f};
     CF2 S{zero, zero};                                           // sum_{j >= i+1} x_j (chain rows)
     CF2 xn{zero, zero};                                          // x_{i+1}
@@ -100,11 +133,11 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
         S.im = df::add(S.im, xn.im);
         const CF2 xp = i > 0 ? ld_cf2(xc_, k - 2) : CF2{zero, zero};
         const float4 t0 = T[2 * k], t1 = T[2 * k + 1];
-        // coefficient of x_k: g B_kk + A_kk
-        Acc a0 = acc_of(ff(t0, 1));
+        // coefficient of x_k: g B_kk +- A_kk (+ for R_h, - for H_h)
+        Acc a0 = acc_of(MODE == 0 ? ff(t0, 1) : chains::neg(ff(t0, 1)));
         acc_mad(a0, g, ff(t0, 0));
         const F2 c0 = acc_done(a0);
-        const F2 at = ff(t1, 0);
+        const F2 at = MODE == 0 ? ff(t1, 0) : chains::neg(ff(t1, 0));
         CF2 r;
         Acc ar{0.f, 0.f}, ai{0.f, 0.f};
         acc_mad(ar, at, S.re);
@@ -117,11 +150,14 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
         acc_mad(ai, c0, xc.im);
         r.re = acc_done(ar);
         r.im = acc_done(ai);
-        st_out(oc, yc_, beta, k, r);
+        if (MODE == 0) st_out(oc, yc_, beta, k, r);
+        else res.add(yc_, k, r);
         xn = xc;
         xc = xp;
     }
-    if (par == 0) {
+    if (MODE == 1) {
+        res.finish(p, c, rel);
+    } else if (par == 0) {
         reinterpret_cast<double2 *>(oc)[n] = make_double2(0.0, 0.0);
         reinterpret_cast<double2 *>(oc)[n + 1] = make_double2(0.0, 0.0);
     }
@@ -129,16 +165,21 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
 
 // Biharmonic table row k (6 float4): (Q_kk, p_k) (r_k, A_kk) (A_{k,k+2}, A_{k,k-2})
 // (B_kk, B_{k,k+2}) (B_{k,k+4}, q_{k+2}) (s_{k+2}, 0).
+template <int MODE>
 __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const float4 *T, const double *x,
-                                                                   const double *y, double beta, double *out) {
+                                                                   const double *y, double beta, double *out,
+                                                                   double *rel) {
     Chain c;
     if (!chain_of(p, blockIdx.x * (long)blockDim.x + threadIdx.x, c)) return;
     const int N = p.N, n = N - 4, par = c.par;
     const int rows = (n - par + 1) / 2;
     const double *xc_ = x + c.col;
     const double *yc_ = y ? y + c.col : nullptr;
-    double *oc = out + c.col;
-    const F2 ga = df::from_f64(p.c - 2.0 * c.z2), gb = df::from_f64(c.z2 * (c.z2 - p.c));
+    double *oc = MODE == 0 ? out + c.col : nullptr;
+    // coefficients of A and B: R_b (c - 2 z2, z2 (z2 - c)) or H_b (-(2 z2 + c), z2 (z2 + c))
+    const F2 ga = df::from_f64(MODE == 0 ? p.c - 2.0 * c.z2 : -(2.0 * c.z2 + p.c));
+    const F2 gb = df::from_f64(MODE == 0 ? c.z2 * (c.z2 - p.c) : c.z2 * (c.z2 + p.c));
+    Res res;
     const F2 zero{0.f, 0.f};
     const CF2 z{zero, zero};
     auto X = [&](int i) { return (i >= 0 && i < rows) ? ld_cf2(xc_, 2 * i + par) : z; };
@@ -204,15 +245,19 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
         acc_mad(ai, c0, xc.im);
         r.re = acc_done(ar);
         r.im = acc_done(ai);
-        st_out(oc, yc_, beta, k, r);
+        if (MODE == 0) st_out(oc, yc_, beta, k, r);
+        else res.add(yc_, k, r);
         xp2 = xp1;
         xp1 = xc;
         xc = xm1;
         xm1 = xm2;
         xm2 = X(i - 3);
     }
-    if (par == 0)
+    if (MODE == 1) {
+        res.finish(p, c, rel);
+    } else if (par == 0) {
         for (int k = n; k < N; k++) reinterpret_cast<double2 *>(oc)[k] = make_double2(0.0, 0.0);
+    }
 }
 
 __device__ __forceinline__ float4 pair4(double a, double b) {
@@ -256,9 +301,23 @@ cudaError_t launch_matvec_df(const Plan &p, int problem, const double *x, const 
     if (p.n_modes <= 0) return cudaSuccess;
     const float4 *T = reinterpret_cast<const float4 *>(p.d_mv_df);
     if (problem == SHEN_HELMHOLTZ)
-        matvec_helmholtz_df_kernel<<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T, x, y, beta, out);
+        matvec_helmholtz_df_kernel<0><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T, x, y, beta, out, nullptr);
     else
-        matvec_biharmonic_df_kernel<<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T + 2 * p.N, x, y, beta, out);
+        matvec_biharmonic_df_kernel<0><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T + 2 * p.N, x, y, beta, out,
+                                                                                nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_df(const Plan &p, int problem, const double *f, const double *u, double *rel,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p.d_resmax, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || p.n_modes <= 0) return e;
+    const float4 *T = reinterpret_cast<const float4 *>(p.d_mv_df);
+    if (problem == SHEN_HELMHOLTZ)
+        matvec_helmholtz_df_kernel<1><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T, u, f, 0.0, nullptr, rel);
+    else
+        matvec_biharmonic_df_kernel<1><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T + 2 * p.N, u, f, 0.0,
+                                                                                nullptr, rel);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_fac_h32);
     cudaFree(p.d_fac_b32);
     cudaFree(p.d_err);
+    cudaFree(p.d_resmax);
     cudaFree(p.d_fac_df);
     cudaFree(p.d_mv_df);
     cudaFree(p.d_ys[0]);
@@ -181,7 +182,9 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(dalloc(&p.d_tab32, tab32.size(), B));
     PLAN_TRY(dalloc(&p.d_fac_h, (size_t)p.n_classes * 2 * p.rows_h * kHelmF64, B));
     PLAN_TRY(dalloc(&p.d_fac_b, (size_t)p.n_classes * 2 * p.rows_b * kBiF64, B));
-    PLAN_TRY(dalloc(&p.d_err, 2, B));
+    PLAN_TRY(dalloc(&p.d_err, 4, B));
+    PLAN_TRY(dalloc(&p.d_resmax, 1, B));
+    PLAN_TRY(cudaMemsetAsync(p.d_resmax, 0, sizeof(unsigned long long), s));
 
     PLAN_TRY(cudaMemcpyAsync(p.d_class_z2, class_z2.data(), class_z2.size() * sizeof(double),
                              cudaMemcpyHostToDevice, s));
@@ -190,7 +193,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(cudaMemcpyAsync(p.d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     PLAN_TRY(cudaMemcpyAsync(p.d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     PLAN_TRY(cudaMemcpyAsync(p.d_tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-    const int err_init[2] = {0, 0x7fffffff};
+    const int err_init[4] = {0, 0x7fffffff, 0, 0};
     PLAN_TRY(cudaMemcpyAsync(p.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, s));
     const double *t = p.d_tab;
     p.tab.bd0 = t + 0 * stride; p.tab.ad0 = t + 1 * stride; p.tab.adt = t + 2 * stride;
@@ -341,6 +344,30 @@ shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, c
     if (!overlap_ok(x, out, nd) || !overlap_ok(y, out, nd)) return SHEN_ERR_ARG;
     if (y && !std::isfinite(beta)) return SHEN_ERR_ARG;
     SHEN_CUDA_TRY(launch_matvec_df(p, problem, x, y, beta, out, as_stream(stream)));
+    return SHEN_OK;
+}
+
+shen_status shen_residual(shen_plan_t plan, int problem, const double *f, const double *u, double *rel,
+                          void *stream) {
+    if (!plan || !f || !u) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (!aligned16(f) || !aligned16(u) || (rel && (reinterpret_cast<uintptr_t>(rel) & 7u))) return SHEN_ERR_ARG;
+    SHEN_CUDA_TRY(launch_residual_df(plan->p, problem, f, u, rel, as_stream(stream)));
+    return SHEN_OK;
+}
+
+shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, long *n_singular) {
+    if (!plan) return SHEN_ERR_ARG;
+    int err_host[4];
+    unsigned long long bits = 0;
+    SHEN_CUDA_TRY(cudaMemcpy(err_host, plan->p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost));
+    SHEN_CUDA_TRY(cudaMemcpy(&bits, plan->p.d_resmax, sizeof(bits), cudaMemcpyDeviceToHost));
+    if (max_rel_residual) {
+        double v;
+        std::memcpy(&v, &bits, sizeof(v));
+        *max_rel_residual = v;
+    }
+    if (n_singular) *n_singular = err_host[2];
     return SHEN_OK;
 }
 

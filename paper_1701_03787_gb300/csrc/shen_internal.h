@@ -50,7 +50,8 @@ struct Plan {
     double *d_fac_h = nullptr;            // Helmholtz factors
     double *d_fac_b = nullptr;            // biharmonic factors
     float *d_fac_h32 = nullptr, *d_fac_b32 = nullptr;
-    int *d_err = nullptr;                 // [2]: flag, first bad class
+    int *d_err = nullptr;                 // [4]: flag, first bad class, chains with a bad pivot, 0
+    unsigned long long *d_resmax = nullptr;   // largest relative residual of the last shen_residual (bits)
     int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
     float *d_fac_df = nullptr;            // backing store of the float-float factor streams below
     // float-float factor streams, row i of chain ch = 2 class + parity at [i * 2 n_classes + ch]
@@ -97,6 +98,8 @@ size_t matvec_df_floats(const Plan &p);
 cudaError_t pack_matvec_df(const Plan &p, float *T, cudaStream_t s);
 cudaError_t launch_matvec_df(const Plan &p, int problem, const double *x, const double *y, double beta,
                              double *out, cudaStream_t s);
+cudaError_t launch_residual_df(const Plan &p, int problem, const double *f, const double *u, double *rel,
+                               cudaStream_t s);
 
 }  // namespace shen
 
