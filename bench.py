@@ -512,7 +512,21 @@ def main():
                                       "biharmonic": rows * 48 / (mb * 1e-3) / 1e9 / pk},
                          "traffic": {"helmholtz": measured_traffic(f"matvec_helmholtz:{mprec}", rows),
                                      "biharmonic": measured_traffic(f"matvec_biharmonic:{mprec}", rows)}}
-        del out
+        # velocity recovery (f from u, then v and w): reads u, g, writes v, w (64 B per row)
+        vv, ww = torch.empty_like(f_h), torch.empty_like(f_h)
+        for _ in range(2):
+            plan.velocity(u_b, u_h, vv, ww, stream=stream)
+        nrep = min(args.steps, 10)
+        ev_v = [torch.cuda.Event(enable_timing=True) for _ in range(nrep + 1)]
+        for s in range(nrep):
+            ev_v[s].record(stream)
+            plan.velocity(u_b, u_h, vv, ww, stream=stream)
+        ev_v[nrep].record(stream)
+        torch.cuda.synchronize()
+        mvel = float(np.mean([ev_v[s].elapsed_time(ev_v[s + 1]) for s in range(nrep)]))
+        mv["velocity"] = {"ms": mvel, "bytes_per_row": 64, "frac_hbm": rows * 64 / (mvel * 1e-3) / 1e9 / pk,
+                          "precision": "df"}
+        del out, vv, ww
     ms, = max_over_ranks([ms], pg, "cuda")
     step_rows = 2 * rows + (2 * N if lean else 0)            # complex rows solved per step
     value = world * step_rows / (ms * 1e-3)
@@ -646,6 +660,7 @@ def main():
         step()                                   # leave the headline results in u_h, u_b
         stream.synchronize()
 
+    velocity = mv.pop("velocity", None) if mv else None
     peak, peak_kind = peaks()
     dom = "biharmonic" if t_b >= t_h else "helmholtz"
     t_dom = max(t_b, t_h)
@@ -665,7 +680,7 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": (4 if lean else 2) * args.steps, "clocks": clk, "e2e": e2e,
-            "rhs_matvec": mv}
+            "rhs_matvec": mv, "velocity": velocity}
     if sample is not None:
         modes, refined, F_h, U_h, F_b, U_b = sample
         line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)

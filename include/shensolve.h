@@ -155,6 +155,24 @@ shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, lon
 shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
                             void *stream);
 
+/* Velocity recovery of the linear step (Sec. 3).  From the wall-normal velocity u
+ * (biharmonic coefficients, the solution of shen_biharmonic_solve) and g (Dirichlet
+ * coefficients, the solution of shen_helmholtz_solve) of every mode:
+ *   f = -du/dx projected on the Dirichlet space, B_D f = -C u with
+ *       C_kj = (psi_j', phi_k) (Eq. ffin; the sign is that of Eq. f, f + du/dx = 0),
+ *   v = i (n g - m f) / z2,  w = -i (n f + m g) / z2  (Eqs. f3, g3 solved for v, w),
+ * with m = 2 pi ix / Lx and n = 2 pi kz / Lz the mode's wavenumbers (ix, kz as in the
+ * mode layout), z2 = m^2 + n^2.  The mode m = n = 0 is left untouched: its v and w come
+ * from the mean-flow Helmholtz solves (Eqs. v00, w00).  Float-float arithmetic
+ * (precision SHEN_DF or SHEN_AUTO; others SHEN_ERR_UNSUPPORTED).
+ *
+ * u, g: DEVICE fields of the plan (u's entries N-4.. and g's N-2.. are ignored);
+ * v, w: DEVICE outputs (entries N-2.. written 0); f: DEVICE output or NULL.  Outputs
+ * must not overlap the inputs or each other (SHEN_ERR_ARG).  Plans built from an
+ * explicit z2 list carry no (m, n): SHEN_ERR_UNSUPPORTED. */
+shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, double *v, double *w, double *f,
+                          int precision, void *stream);
+
 /* A posteriori check of a solve: for every mode, the relative residual
  * ||f - H u||_2 / ||f||_2 over the unknowns, H the Helmholtz or biharmonic system
  * matrix of the plan (Eqs. Helmholtz_matrix, Biharmonic_matrix in the scaled form of

@@ -47,6 +47,7 @@ def lib():
         "shen_rhs_matvec": ([P, I, P, P, D, P, P], I),
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_residual": ([P, I, P, P, P, P], I),
+        "shen_velocity": ([P, P, P, P, P, P, I, P], I),
         "shen_last_error_detail": ([P, P, P], I),
         "shen_solve_host": ([P, I, P, P, I, P], I),
         "shen_plan_info": ([P, P, P, P, P], I),
@@ -253,6 +254,24 @@ class Plan:
         check(lib().shen_plan_autotune(self._h, _problem(problem), _ptr(f), _ptr(u), ctypes.byref(chosen),
                                        ctypes.byref(ms), _stream(stream)), "shen_plan_autotune")
         return PRECISION_NAMES[chosen.value], ms.value
+
+    def velocity(self, u, g, v=None, w=None, f=None, precision="df", stream=None):
+        """(v, w) from the wall-normal velocity u and g (Sec. 3, Eqs. ffin, f3, g3); f is
+        written too when given.  Mode (0, 0) of v and w is left as passed in."""
+        import torch
+        _field_ok(u, self.n_modes, self.N, "u")
+        _field_ok(g, self.n_modes, self.N, "g")
+        if v is None:
+            v = torch.zeros_like(u)
+        if w is None:
+            w = torch.zeros_like(u)
+        _field_ok(v, self.n_modes, self.N, "v")
+        _field_ok(w, self.n_modes, self.N, "w")
+        if f is not None:
+            _field_ok(f, self.n_modes, self.N, "f")
+        check(lib().shen_velocity(self._h, _ptr(u), _ptr(g), _ptr(v), _ptr(w), _ptr(f), _prec(precision),
+                                  _stream(stream)), "shen_velocity")
+        return v, w
 
     def residual(self, problem, f, u, rel=None, stream=None):
         """Per-mode relative residual ||f - H u|| / ||f|| (float64 CUDA tensor of n_modes)."""

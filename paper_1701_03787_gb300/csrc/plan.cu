@@ -84,6 +84,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_resmax);
     cudaFree(p.d_fac_df);
     cudaFree(p.d_mv_df);
+    cudaFree(p.d_vel_df);
     cudaFree(p.d_ys[0]);
     cudaFree(p.d_ys[1]);
     p = Plan{};
@@ -211,6 +212,10 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(df_setup(p, B));
     PLAN_TRY(dalloc(&p.d_mv_df, matvec_df_floats(p), B));
     PLAN_TRY(pack_matvec_df(p, p.d_mv_df, s));
+    std::vector<float4> vel;
+    build_velocity_table(N, vel);
+    PLAN_TRY(dalloc(&p.d_vel_df, vel.size() * 4, B));
+    PLAN_TRY(cudaMemcpyAsync(p.d_vel_df, vel.data(), vel.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);
@@ -306,7 +311,15 @@ shen_status shen_plan_create(shen_plan_t *plan, int N, int Nx, int Nz, double nu
             z2[ix * Nz + iz] = kx * kx + kz * kz;
         }
     }
-    return create_from_z2(plan, N, n_modes, z2.data(), nu, dt, flags, stream);
+    const shen_status st = create_from_z2(plan, N, n_modes, z2.data(), nu, dt, flags, stream);
+    if (st == SHEN_OK) {
+        Plan &p = (*plan)->p;
+        p.grid_Nx = Nx;
+        p.grid_Nz = Nz;
+        p.grid_Lx = Lx;
+        p.grid_Lz = Lz;
+    }
+    return st;
 }
 
 shen_status shen_plan_create_z2(shen_plan_t *plan, int N, long n_modes, const double *z2_host, double nu,
@@ -344,6 +357,30 @@ shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, c
     if (!overlap_ok(x, out, nd) || !overlap_ok(y, out, nd)) return SHEN_ERR_ARG;
     if (y && !std::isfinite(beta)) return SHEN_ERR_ARG;
     SHEN_CUDA_TRY(launch_matvec_df(p, problem, x, y, beta, out, as_stream(stream)));
+    return SHEN_OK;
+}
+
+shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, double *v, double *w, double *f,
+                          int precision, void *stream) {
+    if (!plan || !u || !g || !v || !w) return SHEN_ERR_ARG;
+    if (precision == SHEN_AUTO) precision = SHEN_DF;
+    if (precision != SHEN_DF)
+        return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (p.grid_Nz <= 0) return SHEN_ERR_UNSUPPORTED;            // explicit z2 list: no (m, n)
+    for (const void *q : {(const void *)u, (const void *)g, (const void *)v, (const void *)w, (const void *)f})
+        if (q && !aligned16(q)) return SHEN_ERR_ARG;
+    const long nd = 2 * p.n_modes * (long)p.N;
+    // outputs disjoint from the inputs and from each other
+    const double *outs[3] = {v, w, f};
+    for (int a = 0; a < 3; a++) {
+        if (!outs[a]) continue;
+        for (const double *in : {u, g})
+            if (outs[a] == in || !overlap_ok(outs[a], in, nd)) return SHEN_ERR_ARG;
+        for (int b = a + 1; b < 3; b++)
+            if (outs[b] && (outs[a] == outs[b] || !overlap_ok(outs[a], outs[b], nd))) return SHEN_ERR_ARG;
+    }
+    SHEN_CUDA_TRY(launch_velocity_df(p, u, g, v, w, f, as_stream(stream)));
     return SHEN_OK;
 }
 

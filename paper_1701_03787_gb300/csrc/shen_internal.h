@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 #include "../../include/shensolve.h"
 
@@ -59,6 +60,10 @@ struct Plan {
     const float2 *df_hf = nullptr, *df_bb2 = nullptr;
     const float4 *df_qs = nullptr;        // per-N (q_k, s_k), N + 8 entries
     float *d_mv_df = nullptr;             // float-float row tables of the rhs_matvec operators
+    float *d_vel_df = nullptr;            // float-float per-N table of the velocity recovery
+    // grid of the modes (plans from shen_plan_create; zero for explicit z2 lists)
+    int grid_Nx = 0, grid_Nz = 0;
+    double grid_Lx = 0, grid_Lz = 0;
     // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
     // runs, and the row-block shape of the float-float kernels
     bool df_only = false;                 // SHEN_PLAN_DF_ONLY: float64 factors freed after conversion
@@ -92,6 +97,11 @@ cudaError_t pack_df(Plan &p, cudaStream_t s);
 cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                             cudaStream_t s);
 cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of the float-float kernels
+
+// velocity.cu
+void build_velocity_table(int N, std::vector<float4> &T);
+cudaError_t launch_velocity_df(const Plan &p, const double *u, const double *g, double *v, double *w, double *f,
+                               cudaStream_t s);
 
 // matvec_df.cu
 size_t matvec_df_floats(const Plan &p);
