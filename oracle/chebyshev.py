@@ -136,3 +136,18 @@ def gc_quadrature_f64(u_coeffs, v_coeffs, N):
     uu = np.polynomial.chebyshev.chebval(x, np.array([float(c) for c in u_coeffs]))
     vv = np.polynomial.chebyshev.chebval(x, np.array([float(c) for c in v_coeffs]))
     return float(np.sum(uu * vv) * np.pi / N)
+
+
+def gl_points_weights_mp(N, mp):
+    """Chebyshev-Gauss-Lobatto points x_i = cos(i pi / N_x), i = 0..N_x (N_x = N - 1),
+    with weights pi / (c_i N_x), c_0 = c_{N_x} = 2 (Sec. 2)."""
+    Nx = N - 1
+    xs = [mp.cos(i * mp.pi / Nx) for i in range(N)]
+    ws = [mp.pi / ((2 if i in (0, Nx) else 1) * Nx) for i in range(N)]
+    return xs, ws
+
+
+def gl_quadrature_mp(u_coeffs, v_coeffs, N, mp):
+    """(u, v)_sigma by the N-point GL point sum, in mpmath."""
+    xs, ws = gl_points_weights_mp(N, mp)
+    return mp.fsum(cheb_eval_mp(u_coeffs, x, mp) * cheb_eval_mp(v_coeffs, x, mp) * w for x, w in zip(xs, ws))

@@ -11,6 +11,12 @@ stiffness matrix here is therefore the plain inner product (phi_j'', phi_k).
 Each entry is computed as an exact rational multiple of pi (``chebyshev``) and
 rounded to float64 once (correctly rounded integer division), then multiplied
 by pi in float64.
+
+Points (Sec. 2): Chebyshev-Gauss (GC) by default.  With ``gl=True`` the scalar product
+is the Chebyshev-Gauss-Lobatto point sum, which in coefficient space is the same sum
+with c_{N_x} = c_{N-1} = 2 (Table tab:matrices caption; GL quadrature with N points is
+exact to degree 2N-3, and only T_{N-1} T_{N-1} exceeds it): the mass-type matrices change
+in their highest-mode entries, the derivative couplings (stiffness, Q, C) do not.
 """
 import functools
 import math
@@ -20,11 +26,11 @@ import numpy as np
 from . import chebyshev as cb
 
 
-def _exact_matrix(N, trial, test, nderiv, n_trial, n_test):
+def _exact_matrix(N, trial, test, nderiv, n_trial, n_test, gl=False):
     """Exact matrix X[k, j] = (D^nderiv trial_j, test_k)_sigma / pi as (num, den) ints.
 
     trial(j, M) / test(k, M) return (integer coefficient list, integer scale):
-    the basis function equals coeffs / scale.
+    the basis function equals coeffs / scale.  gl: GL scalar product (c_{N-1} = 2).
     """
     M = N  # N Chebyshev modes: coefficient indices 0..N-1
     num = np.zeros((n_test, n_trial), dtype=object)
@@ -39,6 +45,9 @@ def _exact_matrix(N, trial, test, nderiv, n_trial, n_test):
         g = cb.cscale(cv)
         for _ in range(nderiv):
             g = cb.derivative_scaled(g)
+        if gl and len(g) >= M:
+            g = list(g)
+            g[M - 1] = 2 * g[M - 1]                  # c_{N-1} = 2 at GL points
         for k in range(n_test):
             nz, sk = tests[k]
             s = 0
@@ -84,10 +93,10 @@ def _check_N(N, minimum):
 # ---------------------------------------------------------------------------
 
 @functools.lru_cache(maxsize=None)
-def mass_dirichlet_exact(N):
+def mass_dirichlet_exact(N, gl=False):
     """B_D[k, j] = (phi_j, phi_k)_sigma / pi, exact (num, den) (Table tab:matrices)."""
     _check_N(N, 4)
-    return _exact_matrix(N, _dirichlet, _dirichlet, 0, N - 2, N - 2)
+    return _exact_matrix(N, _dirichlet, _dirichlet, 0, N - 2, N - 2, gl)
 
 
 @functools.lru_cache(maxsize=None)
@@ -98,8 +107,8 @@ def stiff_dirichlet_exact(N):
 
 
 @functools.lru_cache(maxsize=None)
-def mass_dirichlet(N):
-    return _to_f64(*mass_dirichlet_exact(N))
+def mass_dirichlet(N, gl=False):
+    return _to_f64(*mass_dirichlet_exact(N, gl))
 
 
 @functools.lru_cache(maxsize=None)
@@ -112,10 +121,10 @@ def stiff_dirichlet(N):
 # ---------------------------------------------------------------------------
 
 @functools.lru_cache(maxsize=None)
-def mass_biharmonic_exact(N):
+def mass_biharmonic_exact(N, gl=False):
     """B_B[k, j] = (psi_j, psi_k)_sigma / pi, exact (Table tab:matrices)."""
     _check_N(N, 6)
-    return _exact_matrix(N, _biharmonic, _biharmonic, 0, N - 4, N - 4)
+    return _exact_matrix(N, _biharmonic, _biharmonic, 0, N - 4, N - 4, gl)
 
 
 @functools.lru_cache(maxsize=None)
@@ -133,8 +142,8 @@ def bilaplace_biharmonic_exact(N):
 
 
 @functools.lru_cache(maxsize=None)
-def mass_biharmonic(N):
-    return _to_f64(*mass_biharmonic_exact(N))
+def mass_biharmonic(N, gl=False):
+    return _to_f64(*mass_biharmonic_exact(N, gl))
 
 
 @functools.lru_cache(maxsize=None)
@@ -153,7 +162,7 @@ def bilaplace_biharmonic(N):
 # ---------------------------------------------------------------------------
 
 @functools.lru_cache(maxsize=None)
-def coupling_exact(N, name):
+def coupling_exact(N, name, gl=False):
     """Exact (num, den) of a Table tab:matrices coupling matrix.
 
     'M_B'  (phi_j, psi_k)     k = 0..N-5, j = 0..N-3
@@ -163,18 +172,18 @@ def coupling_exact(N, name):
     """
     _check_N(N, 6)
     if name == "M_B":
-        return _exact_matrix(N, _dirichlet, _biharmonic, 0, N - 2, N - 4)
+        return _exact_matrix(N, _dirichlet, _biharmonic, 0, N - 2, N - 4, gl)
     if name == "C_B":
-        return _exact_matrix(N, _dirichlet, _biharmonic, 1, N - 2, N - 4)
+        return _exact_matrix(N, _dirichlet, _biharmonic, 1, N - 2, N - 4, gl)
     if name == "C_D":
-        return _exact_matrix(N, _biharmonic, _dirichlet, 1, N - 4, N - 2)
+        return _exact_matrix(N, _biharmonic, _dirichlet, 1, N - 4, N - 2, gl)
     if name == "C_T":
-        return _exact_matrix(N, _dirichlet, _chebyshev, 1, N - 2, N)
+        return _exact_matrix(N, _dirichlet, _chebyshev, 1, N - 2, N, gl)
     raise ValueError(name)
 
 
-def coupling(N, name):
-    return _to_f64(*coupling_exact(N, name))
+def coupling(N, name, gl=False):
+    return _to_f64(*coupling_exact(N, name, gl))
 
 
 # ---------------------------------------------------------------------------
@@ -189,25 +198,25 @@ def coupling(N, name):
 #   scaled: R_h = (c - z2) B_D + A_D ;  R_b = Q + (c - 2 z2) A_B + z2 (z2 - c) B_B
 # ---------------------------------------------------------------------------
 
-def helmholtz_system(N, alpha):
+def helmholtz_system(N, alpha, gl=False):
     """alpha B_D - A_D, the Helmholtz matrix in scaled form."""
-    return alpha * mass_dirichlet(N) - stiff_dirichlet(N)
+    return alpha * mass_dirichlet(N, gl) - stiff_dirichlet(N)
 
 
-def biharmonic_system(N, a, b):
+def biharmonic_system(N, a, b, gl=False):
     """Q + a A_B + b B_B, the biharmonic matrix in scaled form."""
-    return bilaplace_biharmonic(N) + a * stiff_biharmonic(N) + b * mass_biharmonic(N)
+    return bilaplace_biharmonic(N) + a * stiff_biharmonic(N) + b * mass_biharmonic(N, gl)
 
 
-def helmholtz_rhs_operator(N, z2, c):
+def helmholtz_rhs_operator(N, z2, c, gl=False):
     """R_h = (c - z2) B_D + A_D  (Eq. gfin, scaled by 2/(nu dt))."""
-    return (c - z2) * mass_dirichlet(N) + stiff_dirichlet(N)
+    return (c - z2) * mass_dirichlet(N, gl) + stiff_dirichlet(N)
 
 
-def biharmonic_rhs_operator(N, z2, c):
+def biharmonic_rhs_operator(N, z2, c, gl=False):
     """R_b = Q + (c - 2 z2) A_B + z2 (z2 - c) B_B  (Eq. ufin, scaled by 2/(nu dt))."""
     return (bilaplace_biharmonic(N) + (c - 2.0 * z2) * stiff_biharmonic(N)
-            + z2 * (z2 - c) * mass_biharmonic(N))
+            + z2 * (z2 - c) * mass_biharmonic(N, gl))
 
 
 def paper_helmholtz(N, z2, nu, dt):
@@ -253,9 +262,9 @@ PI_LD = np.longdouble("3.14159265358979323846264338327950288")
 
 
 @functools.lru_cache(maxsize=None)
-def ld_matrices(N, problem):
+def ld_matrices(N, problem, gl=False):
     """(mass, stiffness[, bi-Laplacian]) in longdouble for 'helmholtz' / 'biharmonic'."""
     if problem == "helmholtz":
-        return (_to_ld(*mass_dirichlet_exact(N)), _to_ld(*stiff_dirichlet_exact(N)))
-    return (_to_ld(*mass_biharmonic_exact(N)), _to_ld(*stiff_biharmonic_exact(N)),
+        return (_to_ld(*mass_dirichlet_exact(N, gl)), _to_ld(*stiff_dirichlet_exact(N)))
+    return (_to_ld(*mass_biharmonic_exact(N, gl)), _to_ld(*stiff_biharmonic_exact(N)),
             _to_ld(*bilaplace_biharmonic_exact(N)))

@@ -48,20 +48,20 @@ def n_unknowns(problem, N):
     return N - 2 if problem == "helmholtz" else N - 4
 
 
-def system_matrix(problem, N, z2, c):
+def system_matrix(problem, N, z2, c, gl=False):
     if problem == "helmholtz":
-        return mat.helmholtz_system(N, helmholtz_coeffs(z2, c))
+        return mat.helmholtz_system(N, helmholtz_coeffs(z2, c), gl)
     if problem == "biharmonic":
         a, b = biharmonic_coeffs(z2, c)
-        return mat.biharmonic_system(N, a, b)
+        return mat.biharmonic_system(N, a, b, gl)
     raise ValueError(problem)
 
 
-def rhs_operator(problem, N, z2, c):
+def rhs_operator(problem, N, z2, c, gl=False):
     if problem == "helmholtz":
-        return mat.helmholtz_rhs_operator(N, z2, c)
+        return mat.helmholtz_rhs_operator(N, z2, c, gl)
     if problem == "biharmonic":
-        return mat.biharmonic_rhs_operator(N, z2, c)
+        return mat.biharmonic_rhs_operator(N, z2, c, gl)
     raise ValueError(problem)
 
 
@@ -73,29 +73,29 @@ def solve_dense(H, f):
     return sol[:, 0] + 1j * sol[:, 1]
 
 
-def solve_mode(problem, N, z2, c, f):
+def solve_mode(problem, N, z2, c, f, gl=False):
     """Solution coefficients (length n_unknowns) of one mode's system for load f."""
     n = n_unknowns(problem, N)
-    return solve_dense(system_matrix(problem, N, z2, c), np.asarray(f)[:n])
+    return solve_dense(system_matrix(problem, N, z2, c, gl), np.asarray(f)[:n])
 
 
-def _system_ld(problem, N, z2, c):
+def _system_ld(problem, N, z2, c, gl=False):
     z2l, cl = np.longdouble(z2), np.longdouble(c)
     if problem == "helmholtz":
-        B, A = mat.ld_matrices(N, problem)
+        B, A = mat.ld_matrices(N, problem, gl)
         return (z2l + cl) * B - A
-    B, A, Q = mat.ld_matrices(N, problem)
+    B, A, Q = mat.ld_matrices(N, problem, gl)
     return Q - (2 * z2l + cl) * A + z2l * (z2l + cl) * B
 
 
-def solve_mode_ref(problem, N, z2, c, f, max_iter=6):
+def solve_mode_ref(problem, N, z2, c, f, max_iter=6, gl=False):
     """Reference solution for tight checks: dense LU, then iterative refinement whose
     residual f - H u uses the exactly assembled H in numpy longdouble, until the
     correction stops shrinking.  Removes the float64 assembly and LU roundoff of
     ``solve_mode`` (which is ~5e-13 relative at N = 1024, z = 1145)."""
     n = n_unknowns(problem, N)
-    H = system_matrix(problem, N, z2, c)
-    Hl = _system_ld(problem, N, z2, c)
+    H = system_matrix(problem, N, z2, c, gl)
+    Hl = _system_ld(problem, N, z2, c, gl)
     f = np.asarray(f)[:n]
     lu = __import__("scipy.linalg", fromlist=["lu_factor"])
     fac = lu.lu_factor(H)
@@ -116,10 +116,10 @@ def solve_mode_ref(problem, N, z2, c, f, max_iter=6):
     return out[0] + 1j * out[1]
 
 
-def matvec_mode(problem, N, z2, c, x, y=None, beta=0.0):
+def matvec_mode(problem, N, z2, c, x, y=None, beta=0.0, gl=False):
     """out = R x + beta y for one mode (R the right-hand-side operator of Eq. gfin / ufin)."""
     n = n_unknowns(problem, N)
-    out = rhs_operator(problem, N, z2, c) @ np.asarray(x)[:n]
+    out = rhs_operator(problem, N, z2, c, gl) @ np.asarray(x)[:n]
     if y is not None:
         out = out + beta * np.asarray(y)[:n]
     return out

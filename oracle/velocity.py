@@ -35,29 +35,29 @@ def mode_mn(Nx, Nz, Lx=2 * math.pi, Lz=math.pi):
     return m, n
 
 
-def f_from_u(N, U):
+def f_from_u(N, U, gl=False):
     """Dirichlet coefficients of f = -du/dx from biharmonic coefficients u_hat.
 
     U: complex (..., N) with entries 0..N-5 used; returns (..., N) with entries
     N-2.. zero.  Dense float64 solve of B_D f = -C u (Eq. ffin with the sign of Eq. f)."""
     U = np.asarray(U)
-    B = mat.mass_dirichlet(N)
-    C = mat.coupling(N, "C_D")                       # (N-2) x (N-4): (psi_j', phi_k)
+    B = mat.mass_dirichlet(N, gl)
+    C = mat.coupling(N, "C_D", gl)                   # (N-2) x (N-4): (psi_j', phi_k)
     rhs = -(U[..., : N - 4] @ C.T)
     F = np.zeros(U.shape, dtype=complex)
     F[..., : N - 2] = sla.solve(B, rhs.reshape(-1, N - 2).T).T.reshape(rhs.shape)
     return F
 
 
-def f_from_u_ref(N, U, steps=3):
+def f_from_u_ref(N, U, steps=3, gl=False):
     """``f_from_u`` with iterative refinement: the residual -C u - B_D f is evaluated
     with the exactly assembled B_D and C in numpy longdouble and the correction solved
     in float64, removing the float64 rounding that B_D's conditioning (about 0.4 (N/2)^2,
     1e5 at N = 1024) amplifies in the plain dense solve."""
     U = np.atleast_2d(np.asarray(U))
-    B = mat.mass_dirichlet(N)
-    Bl = mat._to_ld(*mat.mass_dirichlet_exact(N))
-    Cl = mat._to_ld(*mat.coupling_exact(N, "C_D"))
+    B = mat.mass_dirichlet(N, gl)
+    Bl = mat._to_ld(*mat.mass_dirichlet_exact(N, gl))
+    Cl = mat._to_ld(*mat.coupling_exact(N, "C_D", gl))
     lu = sla.lu_factor(B)
     out = np.zeros(U.shape, dtype=complex)
     for part in ("real", "imag"):
