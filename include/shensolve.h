@@ -68,7 +68,10 @@ typedef enum {
 typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
 
 /* Plan creation flags. */
-#define SHEN_PLAN_DF_ONLY 1u
+#define SHEN_PLAN_DF_ONLY 1u   /* keep only the float-float factor tables (shen_plan_create) */
+#define SHEN_PLAN_GL 2u        /* Chebyshev-Gauss-Lobatto scalar product (Sec. 2): the GL point sum,
+                                  i.e. c_{N_x} = 2 in the mass matrices' highest rows (Table
+                                  tab:matrices); default Chebyshev-Gauss.  Single and batched plans. */
 
 /* Arithmetic of a solve.  All variants read and write float64 (complex128) fields and
  * use the same float64 LU factors (built once per plan); they differ in how the
@@ -104,7 +107,8 @@ typedef enum {
  * (the paper's Re_tau = 2000 box is Lx = 2 pi, Lz = pi).  Builds the per-N tables,
  * groups modes by z2 (modes with equal z2 share one factorisation) and computes the
  * float64 LU factors of both systems for every distinct z2 on the device, on
- * `stream`.  Blocks until the plan is ready.  flags: 0, or SHEN_PLAN_DF_ONLY to keep
+ * `stream`.  Blocks until the plan is ready.  flags: SHEN_PLAN_GL (Gauss-Lobatto
+ * points instead of Gauss) and/or SHEN_PLAN_DF_ONLY to keep
  * only the float-float factor tables (about half the device memory: the float64 factors
  * are computed, converted and freed at creation); solves of such a plan accept
  * SHEN_DF and SHEN_AUTO only (others: SHEN_ERR_UNSUPPORTED); shen_rhs_matvec, which
@@ -257,8 +261,8 @@ typedef struct {
     double Lx, Lz;        /* box lengths, > 0 */
 } shen_instance_desc;
 
-/* Build a batched plan from n_inst HOST descriptors.  Blocks until ready.  flags must
- * be 0.  Errors as shen_plan_create. */
+/* Build a batched plan from n_inst HOST descriptors.  Blocks until ready.  flags: 0 or
+ * SHEN_PLAN_GL (every instance on Gauss-Lobatto points).  Errors as shen_plan_create. */
 shen_status shen_batch_plan_create(shen_batch_t *batch, int n_inst, const shen_instance_desc *descs,
                                    unsigned flags, void *stream);
 

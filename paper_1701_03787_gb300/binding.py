@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "shensolve.h")
 
 SHEN_OK, SHEN_ERR_ARG, SHEN_ERR_ALLOC, SHEN_ERR_CUDA, SHEN_ERR_SINGULAR, SHEN_ERR_UNSUPPORTED = range(6)
 SHEN_HELMHOLTZ, SHEN_BIHARMONIC = 0, 1
-SHEN_PLAN_DF_ONLY = 1
+SHEN_PLAN_DF_ONLY, SHEN_PLAN_GL = 1, 2
 PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5, "auto": 6}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
@@ -132,7 +132,7 @@ class Plan:
     shape (n_modes, N) in mode-major order."""
 
     def __init__(self, N, Nx=None, Nz=None, nu=None, dt=None, Lx=None, Lz=None, z2=None, stream=None,
-                 df_only=False):
+                 df_only=False, gl=False):
         import math
         self._h = ctypes.c_void_p()
         if z2 is not None:
@@ -140,12 +140,14 @@ class Plan:
             z = np.ascontiguousarray(np.asarray(z2, dtype=np.float64))
             st = lib().shen_plan_create_z2(ctypes.byref(self._h), int(N), int(z.size),
                                            z.ctypes.data_as(ctypes.c_void_p), float(nu), float(dt),
-                                           SHEN_PLAN_DF_ONLY if df_only else 0, _stream(stream))
+                                           (SHEN_PLAN_DF_ONLY if df_only else 0) | (SHEN_PLAN_GL if gl else 0),
+                                           _stream(stream))
         else:
             Lx = 2 * math.pi if Lx is None else Lx
             Lz = math.pi if Lz is None else Lz
             st = lib().shen_plan_create(ctypes.byref(self._h), int(N), int(Nx), int(Nz), float(nu), float(dt),
-                                        float(Lx), float(Lz), SHEN_PLAN_DF_ONLY if df_only else 0,
+                                        float(Lx), float(Lz),
+                                        (SHEN_PLAN_DF_ONLY if df_only else 0) | (SHEN_PLAN_GL if gl else 0),
                                         _stream(stream))
         check(st, "shen_plan_create")
         n_modes, n_classes, n = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
@@ -310,7 +312,7 @@ class BatchPlan:
     The batched field is a flat complex128 CUDA tensor of ``field_elems`` entries;
     ``offsets[i]`` is where instance i's (n_modes_i, N_i) block starts."""
 
-    def __init__(self, instances, stream=None):
+    def __init__(self, instances, stream=None, gl=False):
         import math
         descs = (InstanceDesc * len(instances))()
         for d, inst in zip(descs, instances):
@@ -320,7 +322,7 @@ class BatchPlan:
             d.Lz = float(inst.get("Lz", math.pi))
         self._h = ctypes.c_void_p()
         check(lib().shen_batch_plan_create(ctypes.byref(self._h), len(instances), ctypes.cast(descs, ctypes.c_void_p),
-                                           0, _stream(stream)), "shen_batch_plan_create")
+                                           SHEN_PLAN_GL if gl else 0, _stream(stream)), "shen_batch_plan_create")
         n_modes, elems, ncls = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
         nbytes = ctypes.c_longlong()
         check(lib().shen_batch_info(self._h, ctypes.byref(n_modes), ctypes.byref(elems), ctypes.byref(ncls),

@@ -172,7 +172,7 @@ BatchKernel batch_kernel(int prec, int problem, int v) {
 
 }  // namespace
 
-void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride);   // plan.cu
+void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride, bool gl);   // plan.cu
 
 }  // namespace shen
 
@@ -217,7 +217,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
                                    void *stream) {
     if (!out) return SHEN_ERR_ARG;
     *out = nullptr;
-    if (flags != 0 || n_inst < 1 || !descs) return SHEN_ERR_ARG;
+    if ((flags & ~SHEN_PLAN_GL) != 0 || n_inst < 1 || !descs) return SHEN_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // validate and lay out the instances
     std::vector<BatchInst> inst((size_t)n_inst);
@@ -324,7 +324,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
         std::vector<double> tab;
         std::vector<float> tab32;
         int stride = 0;
-        build_row_tables(b->tab_N[t], tab, tab32, stride);
+        build_row_tables(b->tab_N[t], tab, tab32, stride, (flags & SHEN_PLAN_GL) != 0);
         double *dt = nullptr;
         B_TRY(balloc(b, &dt, tab.size()));
         B_TRY(cudaMemcpyAsync(dt, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));

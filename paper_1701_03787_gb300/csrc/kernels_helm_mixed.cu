@@ -18,7 +18,7 @@
 //
 // Helmholtz system per parity (k = 2i + p, alpha = z2 + c, h = alpha pi / 2):
 //   H_{i,i-1} = -h,  H_ii = pi (alpha delta_k + 2 (k+1)(k+2)),
-//   H_{i,i+1} = -h + 4 pi (k+1),  H_{i,j>i+1} = 4 pi (k+1),  delta_k = (c_k + 1) / 2.
+//   H_{i,i+1} = -h + 4 pi (k+1),  H_{i,j>i+1} = 4 pi (k+1),  delta_k = (c_k + c_{k+2}) / 2.
 //   LU: y_i = f_i + g_i y_{i-1} (g_i = h / U_{i-1,i-1}),
 //   u_i = (y_i + h u_{i+1} - U2_i S_{i+1}) / U_ii,  S_{i+1} = sum_{j > i} u_j.
 #include "df.cuh"
@@ -130,7 +130,7 @@ __device__ __forceinline__ void backward_sweep(float2 (&w)[R], const float2 *fac
 // The row loop is kept rolled (its body is long) so the kernel stays small.
 template <int R, bool DF>
 __device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const double *fcol, int lane, int s,
-                                         int p, int n, double alpha) {
+                                         int p, int n, double alpha, int k_gl) {
     const df::F2 a_df = df::from_f64(alpha);
     const df::F2 pi_df = {kPiHi, kPiLo};
     // lane totals of u0, then the sum over the lanes above (rows with larger i)
@@ -192,7 +192,8 @@ __device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const do
         float2 r = f2(0.f, 0.f);
         if (k < n) {
             // row coefficients times pi (float-float): pi (alpha delta_k + 2(k+1)(k+2)), 4 pi (k+1)
-            const float delta = k == 0 ? 1.5f : 1.0f;
+            // delta_k = (c_k + c_{k+2}) / 2; c_{k+2} = c_{N-1} = 2 at Gauss-Lobatto points (k = k_gl)
+            const float delta = (k == 0 ? 1.5f : 1.0f) + (k == k_gl ? 0.5f : 0.0f);
             const float e = 2.0f * (float)((k + 1) * (k + 2));
             const float t = 4.0f * (float)(k + 1);
             float rv[2];
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order
 #pragma unroll
     for (int j = 0; j < R; j++) u0buf[j * 32 + lane] = w[j];
     __syncwarp();
-    residual<R, DF>(m0buf, u0buf, fcol, lane, s, par, n, alpha);
+    residual<R, DF>(m0buf, u0buf, fcol, lane, s, par, n, alpha, p.gl ? n - 1 : -1);
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < R; j++) w[j] = m0buf[j * 32 + lane];

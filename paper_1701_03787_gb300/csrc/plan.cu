@@ -34,7 +34,9 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 namespace shen {
 // Row tables of the Galerkin matrices for N Chebyshev modes (Chebyshev-Gauss scalar
 // product, so c_0 = 2 and c_k = 1 for k > 0 including k = N - 1).
-void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride) {
+// gl: Chebyshev-Gauss-Lobatto scalar product, c_{N-1} = 2 in the mass matrices' highest
+// rows (Table tab:matrices: the c_{k+2} term of B_D, the c_{k+4} term of B_B).
+void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, int &stride, bool gl) {
     const double pi = kPi;
     stride = N;
     h.assign((size_t)16 * N, 0.0);
@@ -45,13 +47,14 @@ void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, in
     double *pk = &h[10 * N], *rk = &h[11 * N], *qk = &h[12 * N], *sk = &h[13 * N];
     for (int k = 0; k < N; k++) {
         const double K = k, ck = (k == 0) ? 2.0 : 1.0;
+        const double ck2 = (gl && k + 2 == N - 1) ? 2.0 : 1.0, ck4 = (gl && k + 4 == N - 1) ? 2.0 : 1.0;
         // Dirichlet phi_k = T_k - T_{k+2}: B_kk = pi/2 (c_k + c_{k+2}); A = (phi_j'', phi_k)
-        bd0[k] = pi / 2 * (ck + 1.0);
+        bd0[k] = pi / 2 * (ck + ck2);
         ad0[k] = -2 * pi * (K + 1) * (K + 2);
         adt[k] = -4 * pi * (K + 1);
         // biharmonic psi_k: B (Table tab:matrices), A = (psi_j'', psi_k), Q (Eqs. N_Q, pk, rk)
         const double r2 = (K + 2) / (K + 3), r1 = (K + 1) / (K + 3);
-        bb0[k] = pi / 2 * (ck + 4 * r2 * r2 + r1 * r1);
+        bb0[k] = pi / 2 * (ck + 4 * r2 * r2 + ck4 * r1 * r1);
         bb2[k] = -pi * (r2 + (K + 4) * (K + 1) / ((K + 5) * (K + 3)));
         bb4[k] = pi / 2 * r1;
         ab0[k] = -4 * pi * (K + 1) * (K + 2) * (K + 2) / (K + 3);
@@ -100,7 +103,8 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
                            unsigned flags, void *stream) {
     if (!out) return SHEN_ERR_ARG;
     *out = nullptr;
-    if ((flags & ~SHEN_PLAN_DF_ONLY) != 0 || N < 8 || N > 4096 || n_modes < 1 || n_modes > (1L << 30) || !z2)
+    if ((flags & ~(SHEN_PLAN_DF_ONLY | SHEN_PLAN_GL)) != 0 || N < 8 || N > 4096 || n_modes < 1 ||
+        n_modes > (1L << 30) || !z2)
         return SHEN_ERR_ARG;
     if (!(nu > 0) || !(dt > 0) || !std::isfinite(nu) || !std::isfinite(dt)) return SHEN_ERR_ARG;
     const double c = 2.0 / (nu * dt);
@@ -159,7 +163,9 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     std::vector<double> tab;
     std::vector<float> tab32;
     int stride = 0;
-    build_row_tables(N, tab, tab32, stride);
+    const bool gl = (flags & SHEN_PLAN_GL) != 0;
+    p.gl = gl;
+    build_row_tables(N, tab, tab32, stride, gl);
 
     cudaStream_t s = as_stream(stream);
     auto fail = [&](shen_status st) {
@@ -213,7 +219,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(dalloc(&p.d_mv_df, matvec_df_floats(p), B));
     PLAN_TRY(pack_matvec_df(p, p.d_mv_df, s));
     std::vector<float4> vel;
-    build_velocity_table(N, vel);
+    build_velocity_table(N, vel, gl);
     PLAN_TRY(dalloc(&p.d_vel_df, vel.size() * 4, B));
     PLAN_TRY(cudaMemcpyAsync(p.d_vel_df, vel.data(), vel.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     // float32 factors in the lane layout of the warp-per-mode kernels

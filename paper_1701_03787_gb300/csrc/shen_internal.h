@@ -67,6 +67,7 @@ struct Plan {
     // autotuned choices per problem (SHEN_HELMHOLTZ, SHEN_BIHARMONIC): the path SHEN_AUTO
     // runs, and the row-block shape of the float-float kernels
     bool df_only = false;                 // SHEN_PLAN_DF_ONLY: float64 factors freed after conversion
+    bool gl = false;                      // SHEN_PLAN_GL: Gauss-Lobatto scalar product
     // float-float kernels: fixed grid of resident blocks per [problem][shape], and the
     // per-problem spill scratch of the forward result, [warp slot][chain row][lane]
     int df_grid[2][2] = {{0, 0}, {0, 0}};
@@ -99,7 +100,7 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
 cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of the float-float kernels
 
 // velocity.cu
-void build_velocity_table(int N, std::vector<float4> &T);
+void build_velocity_table(int N, std::vector<float4> &T, bool gl);
 cudaError_t launch_velocity_df(const Plan &p, const double *u, const double *g, double *v, double *w, double *f,
                                cudaStream_t s);
 

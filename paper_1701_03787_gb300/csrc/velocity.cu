@@ -6,8 +6,8 @@
 //
 // C has three diagonals (Table tab:matrices): C_{k,k-3} = pi (k-2)(k+1)/k,
 // C_{k,k-1} = -2 pi (k+1)^2/(k+2), C_{k,k+1} = pi (k+1), coupling opposite parities;
-// B_D is tridiagonal per parity (B_kk = pi/2 (c_k + 1), B_{k,k+-2} = -pi/2) and the same
-// for every mode, so its LU factors are one per-N table.
+// B_D is tridiagonal per parity (B_kk = pi/2 (c_k + c_{k+2}), B_{k,k+-2} = -pi/2) and the
+// same for every mode, so its LU factors are one per-N table.
 //
 // One thread per (mode, parity of f): the forward sweep forms the right-hand side
 // -C u from a rolling window of u rows of the other parity and eliminates with the
@@ -115,8 +115,8 @@ inline float4 pair4(double a, double b) {
 }  // namespace
 
 // Per-N table of velocity_df_kernel, built on the host in float64 and split into
-// float-float pairs: 3 N float4.
-void build_velocity_table(int N, std::vector<float4> &T) {
+// float-float pairs: 3 N float4 (gl: Chebyshev-Gauss-Lobatto B_D, c_{N-1} = 2).
+void build_velocity_table(int N, std::vector<float4> &T, bool gl) {
     const double pi = kPi;
     T.assign((size_t)3 * N, make_float4(0.f, 0.f, 0.f, 0.f));
     const int n = N - 2, nu = N - 4;
@@ -124,7 +124,7 @@ void build_velocity_table(int N, std::vector<float4> &T) {
     const double off = -pi / 2;
     for (int k = 0; k < n; k++) {
         const int par = k & 1;
-        const double d = pi / 2 * ((k == 0 ? 2.0 : 1.0) + 1.0);
+        const double d = pi / 2 * ((k == 0 ? 2.0 : 1.0) + ((gl && k + 2 == N - 1) ? 2.0 : 1.0));
         double l = 0.0, U0 = d;
         if (k >= 2) {
             l = off / U0prev[par];
