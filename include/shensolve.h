@@ -159,6 +159,16 @@ shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, lon
 shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
                             void *stream);
 
+/* Mass matrix of the problem's space (B_D for SHEN_HELMHOLTZ, B_B for SHEN_BIHARMONIC;
+ * Table tab:matrices): out = B x + beta y for every mode, float-float arithmetic.
+ * Arguments and errors as shen_rhs_matvec.  With it, the mean-flow equations of the
+ * m = n = 0 mode (Eqs. v00, w00), scaled like the Helmholtz solve, read
+ *     H_h v_new = R_h v_old + (2 / nu) (B_D H_y - S(beta)),  S(beta)_k = pi beta [k = 0],
+ * which a one-mode plan (shen_plan_create_z2 with z2 = {0}) evaluates with
+ * shen_mass_matvec, shen_rhs_matvec and shen_helmholtz_solve. */
+shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
+                             double *out, void *stream);
+
 /* Velocity recovery of the linear step (Sec. 3).  From the wall-normal velocity u
  * (biharmonic coefficients, the solution of shen_biharmonic_solve) and g (Dirichlet
  * coefficients, the solution of shen_helmholtz_solve) of every mode:

@@ -48,6 +48,7 @@ def lib():
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_residual": ([P, I, P, P, P, P], I),
         "shen_velocity": ([P, P, P, P, P, P, I, P], I),
+        "shen_mass_matvec": ([P, I, P, P, D, P, P], I),
         "shen_last_error_detail": ([P, P, P], I),
         "shen_solve_host": ([P, I, P, P, I, P], I),
         "shen_plan_info": ([P, P, P, P, P], I),
@@ -256,6 +257,19 @@ class Plan:
         check(lib().shen_plan_autotune(self._h, _problem(problem), _ptr(f), _ptr(u), ctypes.byref(chosen),
                                        ctypes.byref(ms), _stream(stream)), "shen_plan_autotune")
         return PRECISION_NAMES[chosen.value], ms.value
+
+    def mass_matvec(self, problem, x, y=None, beta=0.0, out=None, stream=None):
+        """out = B x + beta y with the problem space's mass matrix (float-float)."""
+        import torch
+        _field_ok(x, self.n_modes, self.N, "x")
+        if y is not None:
+            _field_ok(y, self.n_modes, self.N, "y")
+        if out is None:
+            out = torch.empty_like(x)
+        _field_ok(out, self.n_modes, self.N, "out")
+        check(lib().shen_mass_matvec(self._h, _problem(problem), _ptr(x), _ptr(y), float(beta), _ptr(out),
+                                     _stream(stream)), "shen_mass_matvec")
+        return out
 
     def velocity(self, u, g, v=None, w=None, f=None, precision="df", stream=None):
         """(v, w) from the wall-normal velocity u and g (Sec. 3, Eqs. ffin, f3, g3); f is

@@ -390,6 +390,20 @@ shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, do
     return SHEN_OK;
 }
 
+shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
+                             double *out, void *stream) {
+    if (!plan || !x || !out) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
+    const long nd = 2 * p.n_modes * (long)p.N;
+    if (x == out || (y && y == out)) return SHEN_ERR_ARG;
+    if (!overlap_ok(x, out, nd) || !overlap_ok(y, out, nd)) return SHEN_ERR_ARG;
+    if (y && !std::isfinite(beta)) return SHEN_ERR_ARG;
+    SHEN_CUDA_TRY(launch_mass_df(p, problem, x, y, beta, out, as_stream(stream)));
+    return SHEN_OK;
+}
+
 shen_status shen_residual(shen_plan_t plan, int problem, const double *f, const double *u, double *rel,
                           void *stream) {
     if (!plan || !f || !u) return SHEN_ERR_ARG;

@@ -109,6 +109,8 @@ size_t matvec_df_floats(const Plan &p);
 cudaError_t pack_matvec_df(const Plan &p, float *T, cudaStream_t s);
 cudaError_t launch_matvec_df(const Plan &p, int problem, const double *x, const double *y, double beta,
                              double *out, cudaStream_t s);
+cudaError_t launch_mass_df(const Plan &p, int problem, const double *x, const double *y, double beta, double *out,
+                           cudaStream_t s);
 cudaError_t launch_residual_df(const Plan &p, int problem, const double *f, const double *u, double *rel,
                                cudaStream_t s);
 
