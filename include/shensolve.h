@@ -159,6 +159,26 @@ shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, lon
 shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
                             void *stream);
 
+/* One linear step of the channel-flow solver (Sec. 3, Algorithm NS, its linear part),
+ * in the scaled forms of the solves:
+ *   u_new = -H_b^-1 (R_b u_old + (2/nu) load_u)       (Eq. ufin; load_u = S(h_v^{k+1/2}))
+ *   g_new =  H_h^-1 (R_h g_old + (2/nu) load_g)       (Eq. gfin; load_g = S(h_g^{k+1/2}))
+ * The minus sign of the biharmonic step: the solve's H_b is -2/(nu dt) times the
+ * paper's Hchk, while R_b is +2/(nu dt) times its right-hand-side matrix.
+ *   (v, w) from u_new, g_new as shen_velocity          (Eqs. ffin, f3, g3)
+ * load_u / load_g may be NULL (no nonlinear term).  The right-hand sides use the
+ * float-float operators (float64 ones when precision is SHEN_FP64); the solves use
+ * `precision` (SHEN_AUTO: each problem's autotuned path).  The m = n = 0 mode's v and w
+ * are left untouched (mean flow: see shen_mass_matvec).  Composed of the library's
+ * kernels on `stream` (two operators, two solves in place in u_new and g_new, the
+ * velocity recovery); no scratch memory.  All fields DEVICE, n_modes * N complex; the
+ * outputs must not overlap the inputs or each other (SHEN_ERR_ARG).  Plans from an
+ * explicit z2 list: SHEN_ERR_UNSUPPORTED.  Float-float solves of a plan must not run
+ * concurrently with this call. */
+shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double *g_old, const double *load_u,
+                             const double *load_g, double *u_new, double *g_new, double *v, double *w,
+                             int precision, void *stream);
+
 /* Mass matrix of the problem's space (B_D for SHEN_HELMHOLTZ, B_B for SHEN_BIHARMONIC;
  * Table tab:matrices): out = B x + beta y for every mode, float-float arithmetic.
  * Arguments and errors as shen_rhs_matvec.  With it, the mean-flow equations of the
@@ -226,7 +246,13 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
 
 /* Right-hand-side operator: out = R x + beta * y for every mode (R = R_h or R_b by
  * `problem`).  y may be NULL (then beta is ignored).  x, y, out: DEVICE fields;
- * out must not overlap x or y.  float64 arithmetic. */
+ * out must not overlap x or y.  float64 arithmetic.
+ * R_h = (c - z2) B_D + A_D = (2/(nu dt)) (2 Bbar - Hbar) and R_b = Q + (c - 2 z2) A_B +
+ * z2 (z2 - c) B_B = (2/(nu dt)) (2 Achk - 2 z2 Bchk - Hchk) (Eqs. gfin, ufin).  The
+ * Helmholtz system carries the same factor, so the Crank-Nicolson step reads
+ * H_h g_new = R_h g_old + (2/nu) S(h_g); the biharmonic system carries the opposite one
+ * (H_b = -(2/(nu dt)) Hchk), so that step reads H_b u_new = -R_b u_old - (2/nu) S(h_v)
+ * (shen_linear_step applies both). */
 shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y,
                             double beta, double *out, void *stream);
 

@@ -49,6 +49,7 @@ def lib():
         "shen_residual": ([P, I, P, P, P, P], I),
         "shen_velocity": ([P, P, P, P, P, P, I, P], I),
         "shen_mass_matvec": ([P, I, P, P, D, P, P], I),
+        "shen_linear_step": ([P, P, P, P, P, P, P, P, P, I, P], I),
         "shen_last_error_detail": ([P, P, P], I),
         "shen_solve_host": ([P, I, P, P, I, P], I),
         "shen_plan_info": ([P, P, P, P, P], I),
@@ -257,6 +258,24 @@ class Plan:
         check(lib().shen_plan_autotune(self._h, _problem(problem), _ptr(f), _ptr(u), ctypes.byref(chosen),
                                        ctypes.byref(ms), _stream(stream)), "shen_plan_autotune")
         return PRECISION_NAMES[chosen.value], ms.value
+
+    def linear_step(self, u_old, g_old, load_u=None, load_g=None, out=None, precision="auto", stream=None):
+        """One linear step: returns (u_new, g_new, v, w) (see shen_linear_step)."""
+        import torch
+        for t, nm in ((u_old, "u_old"), (g_old, "g_old")):
+            _field_ok(t, self.n_modes, self.N, nm)
+        for t, nm in ((load_u, "load_u"), (load_g, "load_g")):
+            if t is not None:
+                _field_ok(t, self.n_modes, self.N, nm)
+        if out is None:
+            out = tuple(torch.zeros_like(u_old) for _ in range(4))
+        for t in out:
+            _field_ok(t, self.n_modes, self.N, "out")
+        u_new, g_new, v, w = out
+        check(lib().shen_linear_step(self._h, _ptr(u_old), _ptr(g_old), _ptr(load_u), _ptr(load_g), _ptr(u_new),
+                                     _ptr(g_new), _ptr(v), _ptr(w), _prec(precision), _stream(stream)),
+              "shen_linear_step")
+        return u_new, g_new, v, w
 
     def mass_matvec(self, problem, x, y=None, beta=0.0, out=None, stream=None):
         """out = B x + beta y with the problem space's mass matrix (float-float)."""

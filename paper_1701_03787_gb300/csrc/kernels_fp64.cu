@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128) solve_biharmonic_fp64_kernel(Plan p, cons
 //   (R x)_k = g (B_{k,k-2} x_{k-2} + B_kk x_k + B_{k,k+2} x_{k+2}) + A_kk x_k
 //             + A_tail(k) sum_{j = k+2, k+4, ...} x_j,   g = c - z2, B_{k,k+-2} = -pi/2.
 __global__ void __launch_bounds__(128) matvec_helmholtz_fp64_kernel(Plan p, const double *x, const double *y,
-                                                                    double beta, double *out) {
+                                                                    double beta, double *out, double sign) {
     WorkItem w;
     if (!work_item(p, nullptr, 0, p.n_modes, w)) return;
     const int N = p.N, n = N - 2, par = w.par;
@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_fp64_kernel(Plan p, cons
         double2 r;
         r.x = g * (off * (xp.x + xn.x) + b0 * xc.x) + a0 * xc.x + at * S.x;
         r.y = g * (off * (xp.y + xn.y) + b0 * xc.y) + a0 * xc.y + at * S.y;
+        r.x *= sign;
+        r.y *= sign;
         if (y) {
             const double2 yi = ld2(y, base + k);
             r.x = fma(beta, yi.x, r.x);
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_fp64_kernel(Plan p, cons
 //   (A x)_k = A_{k,k-2} x_{k-2} + A_kk x_k + A_{k,k+2} x_{k+2}
 //   (B x)_k = B_{k-4,k} x_{k-4} + B_{k-2,k} x_{k-2} + B_kk x_k + B_{k,k+2} x_{k+2} + B_{k,k+4} x_{k+4}
 __global__ void __launch_bounds__(128) matvec_biharmonic_fp64_kernel(Plan p, const double *x, const double *y,
-                                                                     double beta, double *out) {
+                                                                     double beta, double *out, double sign) {
     WorkItem w;
     if (!work_item(p, nullptr, 0, p.n_modes, w)) return;
     const int N = p.N, n = N - 4, par = w.par;
@@ -149,6 +151,8 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_fp64_kernel(Plan p, con
         r.y = T.qb0[k] * xc.y + T.pk[k] * Sq.y + T.rk[k] * Ss.y
             + ga * (am * xm1.y + T.ab0[k] * xc.y + ap * xp1.y)
             + gb * (bm4 * xm2.y + bm2 * xm1.y + T.bb0[k] * xc.y + bp2 * xp1.y + bp4 * xp2.y);
+        r.x *= sign;
+        r.y *= sign;
         if (y) {
             const double2 yi = ld2(y, base + k);
             r.x = fma(beta, yi.x, r.x);
@@ -187,12 +191,12 @@ cudaError_t launch_solve_fp64(const Plan &p, int problem, long m0, long count, c
 }
 
 cudaError_t launch_matvec_fp64(const Plan &p, int problem, const double *x, const double *y, double beta,
-                               double *out, cudaStream_t s) {
+                               double *out, cudaStream_t s, double sign) {
     if (p.n_modes <= 0) return cudaSuccess;
     if (problem == SHEN_HELMHOLTZ)
-        matvec_helmholtz_fp64_kernel<<<blocks_for(2 * p.n_modes, 128), 128, 0, s>>>(p, x, y, beta, out);
+        matvec_helmholtz_fp64_kernel<<<blocks_for(2 * p.n_modes, 128), 128, 0, s>>>(p, x, y, beta, out, sign);
     else
-        matvec_biharmonic_fp64_kernel<<<blocks_for(2 * p.n_modes, 128), 128, 0, s>>>(p, x, y, beta, out);
+        matvec_biharmonic_fp64_kernel<<<blocks_for(2 * p.n_modes, 128), 128, 0, s>>>(p, x, y, beta, out, sign);
     return cudaGetLastError();
 }
 

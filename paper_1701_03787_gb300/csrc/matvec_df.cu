@@ -9,7 +9,9 @@
 //                           ga = c - 2 z2, gb = z2 (z2 - c)
 // (sums over the same parity; entries beyond the unknowns are zero), then out = R x + beta y.
 //
-// MODE 2 evaluates the mass matrix alone (B_D or B_B): out = B x + beta y.
+// MODE 2 evaluates the mass matrix alone (B_D or B_B): out = B x + beta y; MODE 3 the
+// negated operator, out = -R x + beta y (the biharmonic Crank-Nicolson step in the
+// scaled form of the solve, see shen_linear_step).
 // The same kernels also evaluate the system operators of the solves (MODE 1):
 //   H_h = (z2 + c) B - A      and      H_b = Q - (2 z2 + c) A + z2 (z2 + c) B,
 // i.e. the RHS structure with other scalars, for the a posteriori residual
@@ -119,8 +121,9 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
     const int rows = (n - par + 1) / 2;
     const double *xc_ = x + c.col;
     const double *yc_ = y ? y + c.col : nullptr;
+    constexpr int OP = MODE == 3 ? 0 : MODE;                    // operator: R_h, H_h or B
     double *oc = MODE != 1 ? out + c.col : nullptr;
-    const double gd = MODE == 0 ? p.c - c.z2 : (MODE == 1 ? p.c + c.z2 : 1.0);   // coefficient of B
+    const double gd = OP == 0 ? p.c - c.z2 : (OP == 1 ? p.c + c.z2 : 1.0);   // coefficient of B
     const F2 g = df::from_f64(gd);
     const F2 gm = df::from_f64(-gd * (kPi / 2));                 // g B_{k,k+-2}
     Res res;
@@ -136,10 +139,10 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
         const float4 t0 = T[2 * k], t1 = T[2 * k + 1];
         // coefficient of x_k: g B_kk +- A_kk (+ for R_h, - for H_h, none for B)
         const F2 zero2{0.f, 0.f};
-        Acc a0 = acc_of(MODE == 0 ? ff(t0, 1) : (MODE == 1 ? chains::neg(ff(t0, 1)) : zero2));
+        Acc a0 = acc_of(OP == 0 ? ff(t0, 1) : (OP == 1 ? chains::neg(ff(t0, 1)) : zero2));
         acc_mad(a0, g, ff(t0, 0));
         const F2 c0 = acc_done(a0);
-        const F2 at = MODE == 0 ? ff(t1, 0) : (MODE == 1 ? chains::neg(ff(t1, 0)) : zero2);
+        const F2 at = OP == 0 ? ff(t1, 0) : (OP == 1 ? chains::neg(ff(t1, 0)) : zero2);
         CF2 r;
         Acc ar{0.f, 0.f}, ai{0.f, 0.f};
         acc_mad(ar, at, S.re);
@@ -152,6 +155,7 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
         acc_mad(ai, c0, xc.im);
         r.re = acc_done(ar);
         r.im = acc_done(ai);
+        if (MODE == 3) r = CF2{chains::neg(r.re), chains::neg(r.im)};
         if (MODE != 1) st_out(oc, yc_, beta, k, r);
         else res.add(yc_, k, r);
         xn = xc;
@@ -177,11 +181,12 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
     const int rows = (n - par + 1) / 2;
     const double *xc_ = x + c.col;
     const double *yc_ = y ? y + c.col : nullptr;
+    constexpr int OP = MODE == 3 ? 0 : MODE;                    // operator: R_b, H_b or B
     double *oc = MODE != 1 ? out + c.col : nullptr;
     // coefficients of A and B: R_b (c - 2 z2, z2 (z2 - c)), H_b (-(2 z2 + c), z2 (z2 + c)),
     // or the mass matrix alone (0, 1, and no Q)
-    const F2 ga = df::from_f64(MODE == 0 ? p.c - 2.0 * c.z2 : (MODE == 1 ? -(2.0 * c.z2 + p.c) : 0.0));
-    const F2 gb = df::from_f64(MODE == 0 ? c.z2 * (c.z2 - p.c) : (MODE == 1 ? c.z2 * (c.z2 + p.c) : 1.0));
+    const F2 ga = df::from_f64(OP == 0 ? p.c - 2.0 * c.z2 : (OP == 1 ? -(2.0 * c.z2 + p.c) : 0.0));
+    const F2 gb = df::from_f64(OP == 0 ? c.z2 * (c.z2 - p.c) : (OP == 1 ? c.z2 * (c.z2 + p.c) : 1.0));
     Res res;
     const F2 zero{0.f, 0.f};
     const CF2 z{zero, zero};
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
         const F2 bm4 = i >= 2 ? ff(T[6 * (k - 4) + 4], 0) : zero;      // B_{k-4,k}
         const F2 bm2 = i >= 1 ? ff(T[6 * (k - 2) + 3], 1) : zero;      // B_{k-2,k}
         const F2 am = i >= 1 ? ff(t2, 1) : zero;
-        Acc a = acc_of(MODE == 2 ? zero : ff(t0, 0));                    // Q_kk + ga A_kk + gb B_kk
+        Acc a = acc_of(OP == 2 ? zero : ff(t0, 0));                      // Q_kk + ga A_kk + gb B_kk
         acc_mad(a, ga, ff(t1, 1));
         acc_mad(a, gb, ff(t3, 0));
         const F2 c0 = acc_done(a);
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
         a = Acc{0.f, 0.f};
         acc_mad(a, gb, ff(t4, 0));
         const F2 cp4 = acc_done(a);
-        const F2 pk = MODE == 2 ? zero : ff(t0, 1), rk = MODE == 2 ? zero : ff(t1, 0);
+        const F2 pk = OP == 2 ? zero : ff(t0, 1), rk = OP == 2 ? zero : ff(t1, 0);
         CF2 r;
         Acc ar{0.f, 0.f}, ai{0.f, 0.f};
         acc_mad(ar, pk, Sq.re);
@@ -248,6 +253,7 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
         acc_mad(ai, c0, xc.im);
         r.re = acc_done(ar);
         r.im = acc_done(ai);
+        if (MODE == 3) r = CF2{chains::neg(r.re), chains::neg(r.im)};
         if (MODE != 1) st_out(oc, yc_, beta, k, r);
         else res.add(yc_, k, r);
         xp2 = xp1;
@@ -307,6 +313,18 @@ cudaError_t launch_matvec_df(const Plan &p, int problem, const double *x, const 
         matvec_helmholtz_df_kernel<0><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T, x, y, beta, out, nullptr);
     else
         matvec_biharmonic_df_kernel<0><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T + 2 * p.N, x, y, beta, out,
+                                                                                nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_neg_df(const Plan &p, int problem, const double *x, const double *y, double beta,
+                                 double *out, cudaStream_t s) {
+    if (p.n_modes <= 0) return cudaSuccess;
+    const float4 *T = reinterpret_cast<const float4 *>(p.d_mv_df);
+    if (problem == SHEN_HELMHOLTZ)
+        matvec_helmholtz_df_kernel<3><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T, x, y, beta, out, nullptr);
+    else
+        matvec_biharmonic_df_kernel<3><<<nblk(2 * p.n_modes, 128), 128, 0, s>>>(p, T + 2 * p.N, x, y, beta, out,
                                                                                 nullptr);
     return cudaGetLastError();
 }

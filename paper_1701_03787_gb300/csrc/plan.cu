@@ -390,6 +390,49 @@ shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, do
     return SHEN_OK;
 }
 
+shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double *g_old, const double *load_u,
+                             const double *load_g, double *u_new, double *g_new, double *v, double *w,
+                             int precision, void *stream) {
+    if (!plan || !u_old || !g_old || !u_new || !g_new || !v || !w) return SHEN_ERR_ARG;
+    Plan &p = plan->p;
+    if (p.grid_Nz <= 0) return SHEN_ERR_UNSUPPORTED;            // the velocity step needs (m, n)
+    const long nd = 2 * p.n_modes * (long)p.N;
+    // every output disjoint from every input and from the other outputs
+    const double *ins[4] = {u_old, g_old, load_u, load_g};
+    double *outs[4] = {u_new, g_new, v, w};
+    for (int a = 0; a < 4; a++) {
+        if (!aligned16(outs[a])) return SHEN_ERR_ARG;
+        for (int b = 0; b < 4; b++)
+            if (ins[b] && (!aligned16(ins[b]) || outs[a] == ins[b] || !overlap_ok(outs[a], ins[b], nd)))
+                return SHEN_ERR_ARG;
+        for (int b = a + 1; b < 4; b++)
+            if (outs[a] == outs[b] || !overlap_ok(outs[a], outs[b], nd)) return SHEN_ERR_ARG;
+    }
+    int ph = precision == SHEN_AUTO ? p.auto_prec[SHEN_HELMHOLTZ] : precision;
+    int pb = precision == SHEN_AUTO ? p.auto_prec[SHEN_BIHARMONIC] : precision;
+    shen_status st = check_precision(p, SHEN_HELMHOLTZ, ph);
+    if (st == SHEN_OK) st = check_precision(p, SHEN_BIHARMONIC, pb);
+    if (st != SHEN_OK) return st;
+    // Scaled Crank-Nicolson steps (Eqs. gfin, ufin; the solves' H_h = (2/(nu dt)) Hbar,
+    // H_b = -(2/(nu dt)) Hchk, the operators' R = (2/(nu dt)) x paper right-hand side):
+    //   H_h g_new = R_h g_old + (2/nu) load_g,   H_b u_new = -R_b u_old - (2/nu) load_u
+    const double load_scale = 2.0 / p.nu;
+    cudaStream_t s = as_stream(stream);
+    // right-hand sides into the new fields (float-float operators unless float64 was asked)
+    auto rhs = [&](int problem, const double *x, const double *load, double *out) {
+        const double sg = problem == SHEN_BIHARMONIC ? -1.0 : 1.0;
+        if (precision == SHEN_FP64) return launch_matvec_fp64(p, problem, x, load, sg * load_scale, out, s, sg);
+        return sg > 0 ? launch_matvec_df(p, problem, x, load, load_scale, out, s)
+                      : launch_matvec_neg_df(p, problem, x, load, -load_scale, out, s);
+    };
+    SHEN_CUDA_TRY(rhs(SHEN_BIHARMONIC, u_old, load_u, u_new));
+    SHEN_CUDA_TRY(launch_solve_range(p, SHEN_BIHARMONIC, pb, 0, p.n_modes, u_new, u_new, s));
+    SHEN_CUDA_TRY(rhs(SHEN_HELMHOLTZ, g_old, load_g, g_new));
+    SHEN_CUDA_TRY(launch_solve_range(p, SHEN_HELMHOLTZ, ph, 0, p.n_modes, g_new, g_new, s));
+    SHEN_CUDA_TRY(launch_velocity_df(p, u_new, g_new, v, w, nullptr, s));
+    return SHEN_OK;
+}
+
 shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
                              double *out, void *stream) {
     if (!plan || !x || !out) return SHEN_ERR_ARG;

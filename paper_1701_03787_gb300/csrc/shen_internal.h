@@ -84,7 +84,7 @@ cudaError_t launch_factor_biharmonic(const Plan &p, cudaStream_t s);
 cudaError_t launch_solve_fp64(const Plan &p, int problem, long m0, long count, const double *f,
                               double *u, cudaStream_t s);
 cudaError_t launch_matvec_fp64(const Plan &p, int problem, const double *x, const double *y,
-                               double beta, double *out, cudaStream_t s);
+                               double beta, double *out, cudaStream_t s, double sign = 1.0);   // sign R x + beta y
 
 // kernels_helm_mixed.cu
 int helm_mixed_R(int N);                       // rows per lane for N (0: unsupported)
@@ -109,6 +109,8 @@ size_t matvec_df_floats(const Plan &p);
 cudaError_t pack_matvec_df(const Plan &p, float *T, cudaStream_t s);
 cudaError_t launch_matvec_df(const Plan &p, int problem, const double *x, const double *y, double beta,
                              double *out, cudaStream_t s);
+cudaError_t launch_matvec_neg_df(const Plan &p, int problem, const double *x, const double *y, double beta,
+                                 double *out, cudaStream_t s);   // out = -R x + beta y
 cudaError_t launch_mass_df(const Plan &p, int problem, const double *x, const double *y, double beta, double *out,
                            cudaStream_t s);
 cudaError_t launch_residual_df(const Plan &p, int problem, const double *f, const double *u, double *rel,

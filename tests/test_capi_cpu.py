@@ -63,6 +63,7 @@ def test_null_plan_and_pointers_rejected(L):
     assert L.shen_residual(None, 0, None, None, None, None) == 1
     assert L.shen_velocity(None, None, None, None, None, None, 5, None) == 1
     assert L.shen_mass_matvec(None, 0, None, None, 0.0, None, None) == 1
+    assert L.shen_linear_step(None, None, None, None, None, None, None, None, None, 5, None) == 1
     assert L.shen_last_error_detail(None, None, None) == 1
     assert L.shen_rhs_matvec_ex(None, 0, None, None, 0.0, None, 3, None) == 5     # no such path
     assert L.shen_rhs_matvec_ex(None, 0, None, None, 0.0, None, 99, None) == 1
