@@ -525,8 +525,24 @@ def main():
         torch.cuda.synchronize()
         mvel = float(np.mean([ev_v[s].elapsed_time(ev_v[s + 1]) for s in range(nrep)]))
         mv["velocity"] = {"ms": mvel, "bytes_per_row": 64, "frac_hbm": rows * 64 / (mvel * 1e-3) / 1e9 / pk,
-                          "precision": "df"}
+                          "precision": "df", "traffic": measured_traffic("velocity:df", rows)}
         del out, vv, ww
+        # the whole linear step (two operators, two solves, the velocity recovery): reads
+        # u_old, g_old and both loads, writes u_new, g_new, v, w
+        if not lean:
+            outs = tuple(torch.empty_like(f_h) for _ in range(4))
+            for _ in range(2):
+                plan.linear_step(f_b, f_h, u_b, u_h, out=outs, precision="auto", stream=stream)
+            ev_l = [torch.cuda.Event(enable_timing=True) for _ in range(nrep + 1)]
+            for s in range(nrep):
+                ev_l[s].record(stream)
+                plan.linear_step(f_b, f_h, u_b, u_h, out=outs, precision="auto", stream=stream)
+            ev_l[nrep].record(stream)
+            torch.cuda.synchronize()
+            mls = float(np.mean([ev_l[s].elapsed_time(ev_l[s + 1]) for s in range(nrep)]))
+            mv["linear_step"] = {"ms": mls, "value": rows * 2 / (mls * 1e-3), "unit": "solves*N/s",
+                                 "bytes_per_row": 128, "frac_hbm": rows * 128 / (mls * 1e-3) / 1e9 / pk}
+            del outs
     ms, = max_over_ranks([ms], pg, "cuda")
     step_rows = 2 * rows + (2 * N if lean else 0)            # complex rows solved per step
     value = world * step_rows / (ms * 1e-3)
@@ -661,6 +677,7 @@ def main():
         stream.synchronize()
 
     velocity = mv.pop("velocity", None) if mv else None
+    linear_step = mv.pop("linear_step", None) if mv else None
     peak, peak_kind = peaks()
     dom = "biharmonic" if t_b >= t_h else "helmholtz"
     t_dom = max(t_b, t_h)
@@ -680,7 +697,7 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": (4 if lean else 2) * args.steps, "clocks": clk, "e2e": e2e,
-            "rhs_matvec": mv, "velocity": velocity}
+            "rhs_matvec": mv, "velocity": velocity, "linear_step": linear_step}
     if sample is not None:
         modes, refined, F_h, U_h, F_b, U_b = sample
         line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
