@@ -88,6 +88,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_fac_df);
     cudaFree(p.d_mv_df);
     cudaFree(p.d_vel_df);
+    cudaFree(p.d_vel_ys);
     cudaFree(p.d_ys[0]);
     cudaFree(p.d_ys[1]);
     p = Plan{};
@@ -222,6 +223,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     build_velocity_table(N, vel, gl);
     PLAN_TRY(dalloc(&p.d_vel_df, vel.size() * 4, B));
     PLAN_TRY(cudaMemcpyAsync(p.d_vel_df, vel.data(), vel.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+    PLAN_TRY(velocity_setup(p, B));
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);

@@ -61,6 +61,8 @@ struct Plan {
     const float4 *df_qs = nullptr;        // per-N (q_k, s_k), N + 8 entries
     float *d_mv_df = nullptr;             // float-float row tables of the rhs_matvec operators
     float *d_vel_df = nullptr;            // float-float per-N table of the velocity recovery
+    float4 *d_vel_ys = nullptr;           // its spill scratch, [warp slot][row][lane]
+    int vel_grid = 0;                     // its fixed grid of resident blocks
     // grid of the modes (plans from shen_plan_create; zero for explicit z2 lists)
     int grid_Nx = 0, grid_Nz = 0;
     double grid_Lx = 0, grid_Lz = 0;
@@ -103,6 +105,7 @@ cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of
 void build_velocity_table(int N, std::vector<float4> &T, bool gl);
 cudaError_t launch_velocity_df(const Plan &p, const double *u, const double *g, double *v, double *w, double *f,
                                cudaStream_t s);
+cudaError_t velocity_setup(Plan &p, long long &bytes);   // grid and spill scratch of the velocity kernel
 
 // matvec_df.cu
 size_t matvec_df_floats(const Plan &p);

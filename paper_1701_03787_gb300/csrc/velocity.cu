@@ -9,11 +9,13 @@
 // B_D is tridiagonal per parity (B_kk = pi/2 (c_k + c_{k+2}), B_{k,k+-2} = -pi/2) and the
 // same for every mode, so its LU factors are one per-N table.
 //
-// One thread per (mode, parity of f): the forward sweep forms the right-hand side
-// -C u from a rolling window of u rows of the other parity and eliminates with the
-// table's l; it spills y (float-float) through the chain's rows of the v column.  The
-// back substitution finishes f row by row and turns (f, g) into (v, w) at once, so f is
-// never stored unless the caller asks for it.  Float-float arithmetic; float64 in and out.
+// One thread per (mode, parity of f), on a fixed grid of resident blocks whose warp slots
+// stride over the chains: the forward sweep forms the right-hand side -C u from a
+// rolling window of u rows of the other parity and eliminates with the table's l; it
+// spills y (float-float) to the plan's [warp slot][row][lane] scratch (512 contiguous
+// bytes per warp and row).  The back substitution finishes f row by row and turns
+// (f, g) into (v, w) at once, so f is never stored unless the caller asks for it.
+// Float-float arithmetic; float64 in and out.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -40,10 +42,8 @@ __device__ __forceinline__ CF2 lin2(F2 a, CF2 x, F2 b, CF2 y) {
 
 // Table row k (3 float4): (l_k, 1/U0_k) of B_D's LU on k's parity chain,
 // (-C_{k,k-3}, -C_{k,k-1}), (-C_{k,k+1}, 0); entries outside the matrices are zero.
-__global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *T, const double *u,
-                                                          const double *g, double *v, double *w, double *fo) {
-    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (tid >= 2 * p.n_modes) return;
+__device__ void velocity_chain(const Plan &p, const float4 *T, const double *u, const double *g, double *v,
+                               double *w, double *fo, long tid, float4 *ys) {
     const long mode = tid >> 1;
     const int par = (int)(tid & 1);
     const int N = p.N, n = N - 2, nu_ = N - 4;
@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *
     const F2 zero{0.f, 0.f};
     const CF2 z{zero, zero};
     auto U = [&](int j) { return (j >= 0 && j < nu_) ? ld_cf2(uc, j) : z; };
-    float4 *ys = chains::column_spill(vc, par);
-    // forward: y_i = r_i - l_i y_{i-1}, r_i = -(C u)_k, k = 2 i + par
+    // forward: y_i = r_i - l_i y_{i-1}, r_i = -(C u)_k, k = 2 i + par.  (Register prefetch of
+    // the rows, as in the solves, made this kernel slower: its long float-float body runs
+    // best in these plain rolled loops.)
     CF2 um3 = U(par - 3), um1 = U(par - 1), up1 = U(par + 1);
     CF2 y{zero, zero};
     for (int i = 0; i < rows; i++) {
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *
         r.im = nrm(df::add(df::add(df::mul(c3, um3.im), df::mul(c1, um1.im)), df::mul(cp, up1.im)));
         y.re = chains::fnma(l, y.re, r.re);
         y.im = chains::fnma(l, y.im, r.im);
-        ys[(long)i * 2] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
+        ys[(long)i * 32] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
         um3 = um1;
         um1 = up1;
         up1 = U(k + 3);
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *
     CF2 fn = z;
     for (int i = rows - 1; i >= 0; i--) {
         const int k = 2 * i + par;
-        const float4 yv = ys[(long)i * 2];
+        const float4 yv = ys[(long)i * 32];
         const F2 inv{T[3 * k].z, T[3 * k].w};
         CF2 f;
         f.re = nrm(df::mul(inv, df::add(F2{yv.x, yv.y}, df::mul(half_pi, fn.re))));
@@ -93,9 +94,9 @@ __global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *
         const CF2 gk = ld_cf2(gc, k);
         // v = i (a g - b f), w = -i (a f + b g);  i (x + i y) = -y + i x
         const CF2 t = lin2(a, gk, chains::neg(b), f);
-        const CF2 s = lin2(a, f, b, gk);
+        const CF2 sm = lin2(a, f, b, gk);
         reinterpret_cast<double2 *>(vc)[k] = make_double2(-df::to_f64(t.im), df::to_f64(t.re));
-        reinterpret_cast<double2 *>(wc)[k] = make_double2(df::to_f64(s.im), -df::to_f64(s.re));
+        reinterpret_cast<double2 *>(wc)[k] = make_double2(df::to_f64(sm.im), -df::to_f64(sm.re));
         if (fc) reinterpret_cast<double2 *>(fc)[k] = make_double2(df::to_f64(f.re), df::to_f64(f.im));
         fn = f;
     }
@@ -105,6 +106,17 @@ __global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *
             reinterpret_cast<double2 *>(wc)[k] = make_double2(0.0, 0.0);
             if (fc) reinterpret_cast<double2 *>(fc)[k] = make_double2(0.0, 0.0);
         }
+}
+
+__global__ void __launch_bounds__(128) velocity_df_kernel(Plan p, const float4 *T, const double *u,
+                                                          const double *g, double *v, double *w, double *fo,
+                                                          float4 *scr) {
+    const int lane = threadIdx.x & 31;
+    const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
+    float4 *ys = scr + slot * (long)((p.N - 2 + 1) / 2) * 32 + lane;
+    for (long t0 = slot * 32; t0 < 2 * p.n_modes; t0 += nslots * 32)
+        if (t0 + lane < 2 * p.n_modes) velocity_chain(p, T, u, g, v, w, fo, t0 + lane, ys);
 }
 
 inline float4 pair4(double a, double b) {
@@ -144,9 +156,22 @@ void build_velocity_table(int N, std::vector<float4> &T, bool gl) {
 cudaError_t launch_velocity_df(const Plan &p, const double *u, const double *g, double *v, double *w, double *f,
                                cudaStream_t s) {
     if (p.n_modes <= 0) return cudaSuccess;
-    velocity_df_kernel<<<(unsigned)((2 * p.n_modes + 127) / 128), 128, 0, s>>>(
-        p, reinterpret_cast<const float4 *>(p.d_vel_df), u, g, v, w, f);
+    velocity_df_kernel<<<(unsigned)p.vel_grid, 128, 0, s>>>(p, reinterpret_cast<const float4 *>(p.d_vel_df), u, g,
+                                                            v, w, f, p.d_vel_ys);
     return cudaGetLastError();
+}
+
+cudaError_t velocity_setup(Plan &p, long long &bytes) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_df_kernel, 128, 0);
+    if (e != cudaSuccess) return e;
+    const long needed = (2 * p.n_modes + 127) / 128;
+    p.vel_grid = (int)std::max<long>(1, std::min<long>((long)std::max(1, per_sm) * sms, needed));
+    const size_t n = (size_t)p.vel_grid * 4 * ((p.N - 2 + 1) / 2) * 32;        // float4
+    bytes += (long long)(n * sizeof(float4));
+    return cudaMalloc((void **)&p.d_vel_ys, n * sizeof(float4));
 }
 
 }  // namespace shen
