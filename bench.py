@@ -673,6 +673,18 @@ def main():
         c2.record(stream)
         stream.synchronize()
         fp64_ms = {"helmholtz": a.elapsed_time(b), "biharmonic": b.elapsed_time(c2)}
+        # the float32-sweep + one-refinement-step paths of the Helmholtz problem (the
+        # biharmonic has none: one step misses the 1e-10 bar there)
+        for name in ("df_r1", "fp32_r1"):
+            try:
+                plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)
+            except Exception:                    # not built for this N (warp-per-mode limit)
+                continue
+            a.record(stream)
+            plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)
+            b.record(stream)
+            stream.synchronize()
+            fp64_ms[f"helmholtz_{name}"] = a.elapsed_time(b)
         step()                                   # leave the headline results in u_h, u_b
         stream.synchronize()
 
@@ -695,7 +707,7 @@ def main():
                        "streams": args.streams, "cuda_graph": use_graph, "plan_device_bytes": plan.info()[3]
                        if not batched else plan.device_bytes,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
-            "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "fp64_kernel_ms": fp64_ms, "plan_s": t_plan,
+            "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "compare_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": (4 if lean else 2) * args.steps, "clocks": clk, "e2e": e2e,
             "rhs_matvec": mv, "velocity": velocity, "linear_step": linear_step}
     if sample is not None:
