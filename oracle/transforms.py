@@ -99,8 +99,15 @@ def combination(space, N, dtype=float):
 
 
 def basis_at_points(space, N, gl=False, dtype=float):
-    """phi_l(x_i) as an (N, dim) matrix."""
-    return cheb_at_points(N, gl, dtype) @ combination(space, N, dtype)
+    """phi_l(x_i) as an (N, dim) matrix, from the T_k(x_i) columns by Eqs. phiD / phiN."""
+    T = cheb_at_points(N, gl, dtype)
+    n = dim(space, N)
+    if space == "chebyshev":
+        return T
+    if space == "dirichlet":
+        return T[:, :n] - T[:, 2: n + 2]
+    l = np.arange(n).astype(dtype)
+    return T[:, :n] - (2 * (l + 2) / (l + 3)) * T[:, 2: n + 2] + ((l + 1) / (l + 3)) * T[:, 4: n + 4]
 
 
 def mass(space, N, gl=False):
