@@ -207,6 +207,52 @@ shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, con
 shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, double *v, double *w, double *f,
                           int precision, void *stream);
 
+/* ---- Wall-normal transforms (Sec. 2, Eqs. ifft, sst1, sst2, fstB; Algorithms fst, ifst) ----
+ *
+ * For every mode column of the plan, between the values at the N Chebyshev-Gauss points
+ * x_i = cos((2i+1) pi / (2N)), i = 0 .. N-1 (weights pi / N), and the coefficients of one
+ * of three spaces:
+ *   SHEN_SPACE_CHEBYSHEV   T_k, k = 0 .. N-1                              (Eq. Tk)
+ *   SHEN_SPACE_DIRICHLET   phi_k = T_k - T_{k+2}, k = 0 .. N-3            (Eq. phiD)
+ *   SHEN_SPACE_BIHARMONIC  psi_k = T_k - 2(k+2)/(k+3) T_{k+2} + (k+1)/(k+3) T_{k+4},
+ *                          k = 0 .. N-5                                     (Eq. phiN)
+ * kind:
+ *   SHEN_TRANSFORM_INVERSE  out_i = sum_k in_k phi_k(x_i)     (Eq. ifft; inputs beyond
+ *                           the space's dimension are ignored)
+ *   SHEN_TRANSFORM_SCALAR   out_k = (u, phi_k)_sigma = (pi/N) sum_i in_i phi_k(x_i)
+ *                           (Eq. sst1; entries beyond the dimension written 0)
+ *   SHEN_TRANSFORM_FORWARD  out = B^{-1} (u, phi)_sigma with the space's mass matrix B
+ *                           (Eqs. sst2, fstB; Table tab:matrices), the sigma-orthogonal
+ *                           projection of u on the space (entries beyond written 0)
+ * Each cosine sum is one complex FFT of length N per column (Makhoul's reordering), run
+ * in float-float arithmetic (about 48 significant bits) in shared memory; the mass
+ * solves use the float64 LU of B (the same for every mode) as per-N tables.  Relative
+ * errors are of order 1e-14 for the inverse and scalar transforms; the forward transform
+ * adds the conditioning of B (about 1e9 for the biharmonic B at N = 1024, so inputs far
+ * from the space lose digits there, as a float64 solve of the same system does).
+ *
+ * in, out: DEVICE fields of n_modes * N complex values, mode-major like the solves'
+ * (in == out allowed; other overlap SHEN_ERR_ARG).  Plans with N a power of two on
+ * Gauss points only: other plans (Gauss-Lobatto, N not a power of two) return
+ * SHEN_ERR_UNSUPPORTED, and so does a (kind, space) whose shared-memory buffers do not fit
+ * one block (on GB300: the forward transform in phi or psi at N = 4096).  Asynchronous
+ * on `stream`; no scratch memory: calls on one plan may overlap.  Each column is staged
+ * in shared memory by a bulk asynchronous copy; a copy that does not complete within a
+ * bounded wait stops the kernel and is reported by shen_plan_check as SHEN_ERR_CUDA. */
+typedef enum {
+    SHEN_SPACE_CHEBYSHEV = 0,
+    SHEN_SPACE_DIRICHLET = 1,
+    SHEN_SPACE_BIHARMONIC = 2
+} shen_space;
+
+typedef enum {
+    SHEN_TRANSFORM_INVERSE = 0,
+    SHEN_TRANSFORM_SCALAR = 1,
+    SHEN_TRANSFORM_FORWARD = 2
+} shen_transform_kind;
+
+shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *in, double *out, void *stream);
+
 /* A posteriori check of a solve: for every mode, the relative residual
  * ||f - H u||_2 / ||f||_2 over the unknowns, H the Helmholtz or biharmonic system
  * matrix of the plan (Eqs. Helmholtz_matrix, Biharmonic_matrix in the scaled form of
@@ -271,7 +317,8 @@ shen_status shen_plan_info(shen_plan_t plan, long *n_modes, long *n_classes, lon
                            long long *device_bytes);
 
 /* Device-side error state of the plan after the stream is synchronised: SHEN_OK, or
- * SHEN_ERR_SINGULAR (with the first offending class index in *where if non-NULL). */
+ * SHEN_ERR_SINGULAR (with the first offending class index in *where if non-NULL), or
+ * SHEN_ERR_CUDA if a transform's column copy did not complete (shen_transform). */
 shen_status shen_plan_check(shen_plan_t plan, long *where);
 
 /* Free the plan (after any work using it has completed).  NULL is ignored. */

@@ -19,6 +19,8 @@ SHEN_PLAN_DF_ONLY, SHEN_PLAN_GL = 1, 2
 PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5, "auto": 6}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
+SPACES = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2}
+TRANSFORMS = {"inverse": 0, "scalar": 1, "forward": 2}
 
 _lib = None
 
@@ -47,6 +49,7 @@ def lib():
         "shen_rhs_matvec": ([P, I, P, P, D, P, P], I),
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_residual": ([P, I, P, P, P, P], I),
+        "shen_transform": ([P, I, I, P, P, P], I),
         "shen_velocity": ([P, P, P, P, P, P, I, P], I),
         "shen_mass_matvec": ([P, I, P, P, D, P, P], I),
         "shen_linear_step": ([P, P, P, P, P, P, P, P, P, I, P], I),
@@ -307,6 +310,21 @@ class Plan:
         check(lib().shen_velocity(self._h, _ptr(u), _ptr(g), _ptr(v), _ptr(w), _ptr(f), _prec(precision),
                                   _stream(stream)), "shen_velocity")
         return v, w
+
+    def transform(self, kind, space, x, out=None, stream=None):
+        """Wall-normal transform of every mode column (see shen_transform): kind "inverse"
+        (coefficients -> values at the Gauss points), "scalar" (values -> scalar products
+        with the basis) or "forward" (values -> coefficients); space "chebyshev",
+        "dirichlet" or "biharmonic".  out may be x (in place)."""
+        import torch
+        _field_ok(x, self.n_modes, self.N, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        _field_ok(out, self.n_modes, self.N, "out")
+        k = TRANSFORMS[kind] if isinstance(kind, str) else int(kind)
+        sp = SPACES[space] if isinstance(space, str) else int(space)
+        check(lib().shen_transform(self._h, k, sp, _ptr(x), _ptr(out), _stream(stream)), "shen_transform")
+        return out
 
     def residual(self, problem, f, u, rel=None, stream=None):
         """Per-mode relative residual ||f - H u|| / ||f|| (float64 CUDA tensor of n_modes)."""

@@ -89,6 +89,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_mv_df);
     cudaFree(p.d_vel_df);
     cudaFree(p.d_vel_ys);
+    cudaFree(p.d_tr);
     cudaFree(p.d_ys[0]);
     cudaFree(p.d_ys[1]);
     p = Plan{};
@@ -224,6 +225,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(dalloc(&p.d_vel_df, vel.size() * 4, B));
     PLAN_TRY(cudaMemcpyAsync(p.d_vel_df, vel.data(), vel.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     PLAN_TRY(velocity_setup(p, B));
+    PLAN_TRY(transform_setup(p, B, s));
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);
@@ -449,6 +451,18 @@ shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, con
     return SHEN_OK;
 }
 
+shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *in, double *out, void *stream) {
+    if (!plan || !in || !out) return SHEN_ERR_ARG;
+    if (kind < SHEN_TRANSFORM_INVERSE || kind > SHEN_TRANSFORM_FORWARD) return SHEN_ERR_ARG;
+    if (space < SHEN_SPACE_CHEBYSHEV || space > SHEN_SPACE_BIHARMONIC) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (!aligned16(in) || !aligned16(out)) return SHEN_ERR_ARG;
+    if (!overlap_ok(in, out, 2 * p.n_modes * (long)p.N)) return SHEN_ERR_ARG;
+    if (!transform_supported(p) || !transform_shape_ok(p, kind, space)) return SHEN_ERR_UNSUPPORTED;
+    SHEN_CUDA_TRY(launch_transform(p, kind, space, in, out, as_stream(stream)));
+    return SHEN_OK;
+}
+
 shen_status shen_residual(shen_plan_t plan, int problem, const double *f, const double *u, double *rel,
                           void *stream) {
     if (!plan || !f || !u) return SHEN_ERR_ARG;
@@ -498,10 +512,11 @@ shen_status shen_plan_info(shen_plan_t plan, long *n_modes, long *n_classes, lon
 
 shen_status shen_plan_check(shen_plan_t plan, long *where) {
     if (!plan) return SHEN_ERR_ARG;
-    int err_host[2];
+    int err_host[4];
     SHEN_CUDA_TRY(cudaMemcpy(err_host, plan->p.d_err, sizeof(err_host), cudaMemcpyDeviceToHost));
     if (where) *where = err_host[0] ? err_host[1] : -1;
-    return err_host[0] ? SHEN_ERR_SINGULAR : SHEN_OK;
+    if (err_host[0]) return SHEN_ERR_SINGULAR;
+    return err_host[3] ? SHEN_ERR_CUDA : SHEN_OK;
 }
 
 void shen_plan_destroy(shen_plan_t plan) {

@@ -51,7 +51,8 @@ struct Plan {
     double *d_fac_h = nullptr;            // Helmholtz factors
     double *d_fac_b = nullptr;            // biharmonic factors
     float *d_fac_h32 = nullptr, *d_fac_b32 = nullptr;
-    int *d_err = nullptr;                 // [4]: flag, first bad class, chains with a bad pivot, 0
+    int *d_err = nullptr;                 // [4]: flag, first bad class, chains with a bad pivot,
+                                          //      a transform column copy that did not complete
     unsigned long long *d_resmax = nullptr;   // largest relative residual of the last shen_residual (bits)
     int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
     float *d_fac_df = nullptr;            // backing store of the float-float factor streams below
@@ -63,6 +64,10 @@ struct Plan {
     float *d_vel_df = nullptr;            // float-float per-N table of the velocity recovery
     float4 *d_vel_ys = nullptr;           // its spill scratch, [warp slot][row][lane]
     int vel_grid = 0;                     // its fixed grid of resident blocks
+    // wall-normal transforms (power-of-two N, Gauss points): per-N tables, launch shape
+    float4 *d_tr = nullptr;
+    int tr_stride = 0, tr_psh = 0, tr_ntw = 0, tr_off_mass = 0, tr_G = 1;
+    int tr_groups[3][3] = {}, tr_smem[3][3] = {}, tr_grid[3][3] = {};   // per (kind, space)
     // grid of the modes (plans from shen_plan_create; zero for explicit z2 lists)
     int grid_Nx = 0, grid_Nz = 0;
     double grid_Lx = 0, grid_Lz = 0;
@@ -106,6 +111,12 @@ void build_velocity_table(int N, std::vector<float4> &T, bool gl);
 cudaError_t launch_velocity_df(const Plan &p, const double *u, const double *g, double *v, double *w, double *f,
                                cudaStream_t s);
 cudaError_t velocity_setup(Plan &p, long long &bytes);   // grid and spill scratch of the velocity kernel
+
+// transform.cu
+bool transform_supported(const Plan &p);
+bool transform_shape_ok(const Plan &p, int kind, int space);   // the launch fits on this GPU
+cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s);   // tables and launch shape
+cudaError_t launch_transform(const Plan &p, int kind, int space, const double *in, double *out, cudaStream_t s);
 
 // matvec_df.cu
 size_t matvec_df_floats(const Plan &p);

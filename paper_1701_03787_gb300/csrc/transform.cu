@@ -1,0 +1,765 @@
+// Wall-normal Shen transforms (Sec. 2, Eqs. ifft, sst1, sst2, fstB; Algorithms fst and
+// ifst of the appendix) for every Fourier mode of a plan, Chebyshev-Gauss points
+// x_i = cos((2i+1) pi / (2N)), i = 0 .. N-1, weights pi / N:
+//
+//   inverse   u(x_i) = sum_l uhat_l phi_l(x_i)                   (Eq. ifft, S^{-1})
+//   scalar    S_l = (u, phi_l)_sigma = (pi/N) sum_i u(x_i) phi_l(x_i)     (Eq. sst1)
+//   forward   uhat = B^{-1} S, B = (phi_q, phi_l)_sigma           (Eqs. sst2, fstB)
+//
+// for the spaces T_k (Eq. Tk), phi_k = T_k - T_{k+2} (Eq. phiD) and
+// psi_k = T_k - 2(k+2)/(k+3) T_{k+2} + (k+1)/(k+3) T_{k+4} (Eq. phiN).
+//
+// Both cosine sums go through one complex FFT of length N per column (Makhoul's
+// reordering, IEEE Trans. ASSP 28, 1980), which handles the real and imaginary parts of
+// a complex column together:
+//   DCT-II   C_k = sum_n x_n cos(pi k (2n+1) / (2N)):  v = (x_0, x_2, ..., x_3, x_1),
+//            V = FFT(v),  C_k = (w_k V_k + conj(w_k) V_{N-k}) / 2,  w_k = e^{-i pi k/(2N)};
+//            for 0 < k < N/2 the pair (k, N-k) comes from P = w_k V_k, Q = conj(w_k) V_{N-k}
+//            as C_k = (P + Q)/2, C_{N-k} = i (P - Q)/2.
+//   DCT-III  u_n = sum_k t_k cos(pi k (2n+1) / (2N)):  V_0 = t_0,
+//            V_k = e^{i pi k/(2N)} (t_k - i t_{N-k}) / 2,  v = sum_k V_k e^{2 pi i k n/N},
+//            u_{2n} = v_n, u_{2n+1} = v_{N-1-n}.
+// The FFT is an in-place decimation-in-frequency radix-4 (and one radix-2) pass sequence
+// in shared memory; its output sits in digit-reversed positions, which the post-processing
+// reads through dpos().  The mass solve B uhat = S (tridiagonal per parity for phi,
+// pentadiagonal per parity for psi, the same for every mode) runs as chunked scans: 16
+// lanes per parity chain each solve a contiguous chunk with zero carries, a shuffle scan
+// composes the chunks' affine carry maps, and a fix-up adds the carried part through the
+// precomputed homogeneous solutions of each chunk (per-N tables from the float64 LU of B).
+//
+// One warp per mode column, persistent blocks; float-float arithmetic (pairs of float32,
+// df.cuh), float64 (complex128) in and out.  Power-of-two N only.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "df.cuh"
+#include "shen_internal.h"
+
+namespace shen {
+namespace {
+
+using df::F2;
+
+struct Z {   // complex float-float
+    F2 re, im;
+};
+
+__device__ __forceinline__ Z ldz(const float4 *A, int i) {
+    const float4 v = A[i];
+    return Z{F2{v.x, v.y}, F2{v.z, v.w}};
+}
+__device__ __forceinline__ void stz(float4 *A, int i, Z v) { A[i] = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
+__device__ __forceinline__ F2 dneg(F2 a) { return F2{-a.hi, -a.lo}; }
+__device__ __forceinline__ F2 nrm(F2 a) { return df::fast_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ Z zadd(Z a, Z b) { return Z{df::add(a.re, b.re), df::add(a.im, b.im)}; }
+__device__ __forceinline__ Z zsub(Z a, Z b) { return Z{df::add(a.re, dneg(b.re)), df::add(a.im, dneg(b.im))}; }
+__device__ __forceinline__ Z zmul(Z a, Z w) {        // a w
+    return Z{df::add(df::mul(a.re, w.re), dneg(df::mul(a.im, w.im))),
+             df::add(df::mul(a.re, w.im), df::mul(a.im, w.re))};
+}
+__device__ __forceinline__ Z zmulc(Z a, Z w) {       // a conj(w)
+    return Z{df::add(df::mul(a.re, w.re), df::mul(a.im, w.im)),
+             df::add(df::mul(a.im, w.re), dneg(df::mul(a.re, w.im)))};
+}
+__device__ __forceinline__ Z zi(Z a) { return Z{dneg(a.im), a.re}; }      // i a
+__device__ __forceinline__ Z zmi(Z a) { return Z{a.im, dneg(a.re)}; }     // -i a
+__device__ __forceinline__ Z zhalf(Z a) {
+    return Z{F2{0.5f * a.re.hi, 0.5f * a.re.lo}, F2{0.5f * a.im.hi, 0.5f * a.im.lo}};
+}
+__device__ __forceinline__ Z zpow2(Z a, float s) {   // a s, s a power of two (exact)
+    return Z{F2{s * a.re.hi, s * a.re.lo}, F2{s * a.im.hi, s * a.im.lo}};
+}
+__device__ __forceinline__ Z zscale(Z a, F2 s) { return Z{nrm(df::mul(a.re, s)), nrm(df::mul(a.im, s))}; }
+__device__ __forceinline__ Z zfma(F2 s, Z a, Z b) {  // b + s a
+    return Z{df::add(b.re, df::mul(a.re, s)), df::add(b.im, df::mul(a.im, s))};
+}
+__device__ __forceinline__ Z zld(const float4 *p) {
+    const float4 v = __ldg(p);
+    return Z{F2{v.x, v.y}, F2{v.z, v.w}};
+}
+__device__ __forceinline__ Z zfromf64(double2 v) { return Z{df::from_f64(v.x), df::from_f64(v.y)}; }
+__device__ __forceinline__ double2 ztof64(Z v) { return make_double2(df::to_f64(v.re), df::to_f64(v.im)); }
+
+constexpr Z kZero{F2{0.f, 0.f}, F2{0.f, 0.f}};
+constexpr F2 kOne{1.f, 0.f};
+constexpr F2 kNil{0.f, 0.f};
+
+// Position of frequency k after the in-place DIF passes (radix 4 first, then one radix 2
+// when log2 N is odd): the first pass puts k mod 4 in quarter (k mod 4), and so on.
+__device__ __forceinline__ int dpos(int k, int lg) {
+    int p = 0, kk = k, ls = lg;
+    while (ls >= 2) {
+        ls -= 2;
+        p += (kk & 3) << ls;
+        kk >>= 2;
+    }
+    if (ls == 1) p += kk & 1;
+    return p;
+}
+
+// Thread group of one mode column: G warps (32 G threads) synchronised by the named
+// barrier `id` (ids 1 .. 15; 0 is __syncthreads).
+struct Group {
+    int t, nt, id;   // thread index in the group, group size, barrier id
+    __device__ __forceinline__ void sync() const {
+        if (nt == 32)
+            __syncwarp();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nt) : "memory");
+    }
+    // AND of v over the group (also a barrier)
+    __device__ __forceinline__ bool all(bool v) const {
+        uint32_t r;
+        asm volatile(
+            "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, %2, %3, pi;\n"
+            " selp.u32 %0, 1, 0, po;\n}\n"
+            : "=r"(r)
+            : "r"((uint32_t)v), "r"(id), "r"(nt)
+            : "memory");
+        return r != 0;
+    }
+};
+
+// In-place FFT of the group's column A[0 .. N): forward e^{-2 pi i jk/N}, or (INV) e^{+...},
+// unnormalised, output in dpos() order.  tw: per radix-4 pass p (span L = N / 4^p,
+// Q = L/4), entries [3 j + m - 1] = e^{-2 pi i m j 4^p / N}, j < Q, m = 1, 2, 3, passes
+// stored one after the other, so a pass reads its twiddles contiguously.
+template <bool INV>
+__device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
+    const int N = 1 << lg, half = N >> 1;
+    int lgL = lg;
+    const float4 *twp = tw;
+    for (; lgL >= 2; lgL -= 2) {
+        const int lgQ = lgL - 2, Q = 1 << lgQ;
+#pragma unroll 2
+        for (int b = g.t; b < (N >> 2); b += g.nt) {
+            const int j = b & (Q - 1);
+            const int base = ((b >> lgQ) << lgL) + j;
+            const Z a = ldz(A, base), bb = ldz(A, base + Q), c = ldz(A, base + 2 * Q), d = ldz(A, base + 3 * Q);
+            const Z s0 = zadd(a, c), s1 = zsub(a, c), s2 = zadd(bb, d), s3 = zsub(bb, d);
+            Z y0 = zadd(s0, s2), y2 = zsub(s0, s2);
+            Z y1 = INV ? zadd(s1, zi(s3)) : zadd(s1, zmi(s3));
+            Z y3 = INV ? zadd(s1, zmi(s3)) : zadd(s1, zi(s3));
+            if (j != 0) {
+                Z w1 = ldz(twp, 3 * j), w2 = ldz(twp, 3 * j + 1), w3 = ldz(twp, 3 * j + 2);
+                if (INV) {
+                    y1 = zmulc(y1, w1);
+                    y2 = zmulc(y2, w2);
+                    y3 = zmulc(y3, w3);
+                } else {
+                    y1 = zmul(y1, w1);
+                    y2 = zmul(y2, w2);
+                    y3 = zmul(y3, w3);
+                }
+            }
+            stz(A, base, y0);
+            stz(A, base + Q, y1);
+            stz(A, base + 2 * Q, y2);
+            stz(A, base + 3 * Q, y3);
+        }
+        twp += 3 * Q;
+        g.sync();
+    }
+    if (lgL == 1) {
+        for (int b = g.t; b < half; b += g.nt) {
+            const Z a = ldz(A, 2 * b), c = ldz(A, 2 * b + 1);
+            stz(A, 2 * b, zadd(a, c));
+            stz(A, 2 * b + 1, zsub(a, c));
+        }
+        g.sync();
+    }
+}
+
+// ------------------------------------------------------------------ mass solve
+
+// Shuffle of a float-float value / complex value between lanes of a 16-lane group.
+__device__ __forceinline__ F2 shup(F2 v, int d) {
+    return F2{__shfl_up_sync(0xffffffffu, v.hi, d, 16), __shfl_up_sync(0xffffffffu, v.lo, d, 16)};
+}
+__device__ __forceinline__ F2 shdn(F2 v, int d) {
+    return F2{__shfl_down_sync(0xffffffffu, v.hi, d, 16), __shfl_down_sync(0xffffffffu, v.lo, d, 16)};
+}
+__device__ __forceinline__ Z shup(Z v, int d) { return Z{shup(v.re, d), shup(v.im, d)}; }
+__device__ __forceinline__ Z shdn(Z v, int d) { return Z{shdn(v.re, d), shdn(v.im, d)}; }
+__device__ __forceinline__ F2 dmul(F2 a, F2 b) { return nrm(df::mul(a, b)); }
+__device__ __forceinline__ F2 dfma2(F2 a, F2 b, F2 c, F2 d) {   // a b + c d
+    return df::add(df::mul(a, b), df::mul(c, d));
+}
+
+// Affine carry map of a chunk on the state (s0, s1) (BW = 2) or s0 (BW = 1):
+//   state -> M state + c.
+struct CarryMap {
+    F2 m00, m01, m10, m11;
+    Z c0, c1;
+};
+
+// (M, c) o (M', c'):  x -> M (M' x + c') + c
+template <int BW>
+__device__ __forceinline__ CarryMap compose(const CarryMap &a, const CarryMap &b) {
+    CarryMap r;
+    if (BW == 1) {
+        r.m00 = dmul(a.m00, b.m00);
+        r.c0 = zfma(a.m00, b.c0, a.c0);
+        r.m01 = r.m10 = r.m11 = kNil;
+        r.c1 = kZero;
+    } else {
+        r.m00 = dfma2(a.m00, b.m00, a.m01, b.m10);
+        r.m01 = dfma2(a.m00, b.m01, a.m01, b.m11);
+        r.m10 = dfma2(a.m10, b.m00, a.m11, b.m10);
+        r.m11 = dfma2(a.m10, b.m01, a.m11, b.m11);
+        r.c0 = zfma(a.m01, b.c1, zfma(a.m00, b.c0, a.c0));
+        r.c1 = zfma(a.m11, b.c1, zfma(a.m10, b.c0, a.c1));
+    }
+    return r;
+}
+
+template <int BW, bool UP>
+__device__ __forceinline__ CarryMap shuffle_map(const CarryMap &m, int d) {
+    CarryMap r;
+    if (UP) {
+        r.m00 = shup(m.m00, d);
+        r.c0 = shup(m.c0, d);
+        if (BW == 2) {
+            r.m01 = shup(m.m01, d); r.m10 = shup(m.m10, d); r.m11 = shup(m.m11, d); r.c1 = shup(m.c1, d);
+        }
+    } else {
+        r.m00 = shdn(m.m00, d);
+        r.c0 = shdn(m.c0, d);
+        if (BW == 2) {
+            r.m01 = shdn(m.m01, d); r.m10 = shdn(m.m10, d); r.m11 = shdn(m.m11, d); r.c1 = shdn(m.c1, d);
+        }
+    }
+    if (BW == 1) { r.m01 = r.m10 = r.m11 = kNil; r.c1 = kZero; }
+    return r;
+}
+
+// Per-row mass-solve table (5 float4 per row of a parity chain, float-float pairs):
+//   [0] (l1, l2)   L_{i,i-1}, L_{i,i-2} of B's LU (unit lower)
+//   [1] (G1, G2)   chunk-local homogeneous forward solutions for carries (y_{s-1}, y_{s-2}) = (1,0), (0,1)
+//   [2] (1/d, f1)  1/U_ii and U_{i,i+1}/U_ii
+//   [3] (f2, 0)    U_{i,i+2}/U_ii
+//   [4] (H1, H2)   chunk-local homogeneous backward solutions for (x_{e+1}, x_{e+2}) = (1,0), (0,1)
+// Solve B x = S for the warp's column: S in A (padded positions), x written back to A;
+// B is scratch.  n unknowns, chunk length K, padding shift psh.
+template <int BW>
+__device__ void mass_solve(float4 *A, float4 *Bf, int n, int K, int psh, const float4 *T, int RM, int lane) {
+    const int h = lane >> 4, j = lane & 15;
+    const int R = (n - h + 1) / 2;
+    const int s = j * K, e = min(R, s + K) - 1;
+    const bool act = s < R;
+    auto P = [&](int i) {
+        const int k = 2 * i + h;
+        return k + (k >> psh);
+    };
+    const float4 *Th = T + (long)h * RM * 5;
+    auto pr = [](float4 v, int w) { return w == 0 ? F2{v.x, v.y} : F2{v.z, v.w}; };
+
+    // forward elimination, chunk-local with zero carries: p_i = S_i - l1 p_{i-1} - l2 p_{i-2}
+    Z p1 = kZero, p2 = kZero;
+    CarryMap mp{kOne, kNil, kNil, kOne, kZero, kZero};
+    if (act) {
+        for (int i = s; i <= e; i++) {
+            const float4 lv = __ldg(Th + 5 * i);
+            Z y = ldz(A, P(i));
+            y = zfma(dneg(pr(lv, 0)), p1, y);
+            if (BW == 2) y = zfma(dneg(pr(lv, 1)), p2, y);
+            y = Z{nrm(y.re), nrm(y.im)};
+            stz(Bf, P(i), y);
+            p2 = p1;
+            p1 = y;
+        }
+        const float4 ge = __ldg(Th + 5 * e + 1);
+        mp.m00 = pr(ge, 0);
+        mp.c0 = p1;
+        if (BW == 2) {
+            mp.m01 = pr(ge, 1);
+            if (e - 1 >= s) {
+                const float4 g1 = __ldg(Th + 5 * (e - 1) + 1);
+                mp.m10 = pr(g1, 0);
+                mp.m11 = pr(g1, 1);
+                mp.c1 = p2;
+            } else {
+                mp.m10 = kOne;
+                mp.m11 = kNil;
+                mp.c1 = kZero;
+            }
+        } else {
+            mp.m01 = mp.m10 = mp.m11 = kNil;
+        }
+    } else if (BW == 1) {
+        mp.m11 = kNil;
+    }
+    // inclusive scan of the chunk maps, chunk 0 first
+    for (int d = 1; d < 16; d <<= 1) {
+        const CarryMap o = shuffle_map<BW, true>(mp, d);
+        if (j >= d) mp = compose<BW>(mp, o);
+    }
+    Z Y1 = shup(mp.c0, 1), Y2 = BW == 2 ? shup(mp.c1, 1) : kZero;
+    if (j == 0) Y1 = Y2 = kZero;
+    if (act) {
+        for (int i = s; i <= e; i++) {
+            const float4 gv = __ldg(Th + 5 * i + 1);
+            Z y = zfma(pr(gv, 0), Y1, ldz(Bf, P(i)));
+            if (BW == 2) y = zfma(pr(gv, 1), Y2, y);
+            stz(Bf, P(i), Z{nrm(y.re), nrm(y.im)});
+        }
+    }
+    // back substitution, chunk-local: q_i = y_i / d_i - f1 q_{i+1} - f2 q_{i+2}
+    Z q1 = kZero, q2 = kZero;
+    CarryMap mq{kOne, kNil, kNil, kOne, kZero, kZero};
+    if (BW == 1) mq.m11 = kNil;
+    if (act) {
+        for (int i = e; i >= s; i--) {
+            const float4 b0 = __ldg(Th + 5 * i + 2);
+            Z x = zscale(ldz(Bf, P(i)), pr(b0, 0));
+            x = zfma(dneg(pr(b0, 1)), q1, x);
+            if (BW == 2) x = zfma(dneg(pr(__ldg(Th + 5 * i + 3), 0)), q2, x);
+            x = Z{nrm(x.re), nrm(x.im)};
+            stz(Bf, P(i), x);
+            q2 = q1;
+            q1 = x;
+        }
+        const float4 hs = __ldg(Th + 5 * s + 4);
+        mq.m00 = pr(hs, 0);
+        mq.c0 = q1;
+        if (BW == 2) {
+            mq.m01 = pr(hs, 1);
+            if (s + 1 <= e) {
+                const float4 h1 = __ldg(Th + 5 * (s + 1) + 4);
+                mq.m10 = pr(h1, 0);
+                mq.m11 = pr(h1, 1);
+                mq.c1 = q2;
+            } else {
+                mq.m10 = kOne;
+                mq.m11 = kNil;
+                mq.c1 = kZero;
+            }
+        } else {
+            mq.m01 = mq.m10 = mq.m11 = kNil;
+        }
+    }
+    // inclusive scan from the last chunk down
+    for (int d = 1; d < 16; d <<= 1) {
+        const CarryMap o = shuffle_map<BW, false>(mq, d);
+        if (j + d < 16) mq = compose<BW>(mq, o);
+    }
+    Z X1 = shdn(mq.c0, 1), X2 = BW == 2 ? shdn(mq.c1, 1) : kZero;
+    if (j == 15) X1 = X2 = kZero;
+    if (act) {
+        for (int i = s; i <= e; i++) {
+            const float4 hv = __ldg(Th + 5 * i + 4);
+            Z x = zfma(pr(hv, 0), X1, ldz(Bf, P(i)));
+            if (BW == 2) x = zfma(pr(hv, 1), X2, x);
+            stz(A, P(i), Z{nrm(x.re), nrm(x.im)});
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ kernel
+
+// One-dimensional bulk copies (TMA, cp.async.bulk) of a whole column from global to
+// shared memory, completed on a per-warp mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase `parity` of the warp's barrier (each try_wait suspends for a
+// bounded time): false after the limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+struct TrArgs {
+    int N, lg;
+    int G, n_groups;         // warps per mode group, groups per block
+    long n_modes;
+    int stride;              // float4 per buffer
+    int n_tw;                // float4 of the per-pass twiddle table (copied to shared memory)
+    int K, psh, RM;          // mass solve: chunk length, padding shift, rows per parity stride
+    const float4 *tw;        // per-pass twiddles
+    const float4 *mk;        // e^{-i pi k/(2N)}, k = 0 .. N/2
+    const float4 *coef;      // per k: (g1i_k, g2i_k), (g1_k, g2_k)
+    const float4 *mass;      // mass-solve rows of the space
+    int *err;                // set to 1 if a column copy did not complete
+    F2 pi_over_N;
+};
+
+// Buffers of a mode group: 2 (inverse, scalar products, forward in T_k) or 3 (forward in
+// phi, psi) of `stride` float4.  The column copy lands in R; the next mode's copy is
+// issued as soon as R is free, so it overlaps the current mode's FFT.
+constexpr int nbuf_of(int kind, int space) { return (kind == 2 && space != 0) ? 3 : 2; }
+
+// KIND: 0 inverse, 1 scalar product, 2 forward.  SPACE: 0 T_k, 1 phi_k, 2 psi_k.
+template <int KIND, int SPACE>
+__global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *in, double *out) {
+    extern __shared__ float4 sm[];
+    const int N = a.N, lg = a.lg, half = N >> 1;
+    const float4 *tw = sm;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + a.n_tw);
+    for (int t = threadIdx.x; t < a.n_tw; t += blockDim.x) sm[t] = __ldg(a.tw + t);
+    const int gsize = 32 * a.G, gi = threadIdx.x / gsize;
+    const Group g{(int)threadIdx.x - gi * gsize, gsize, 1 + gi};
+    constexpr int NB = nbuf_of(KIND, SPACE);
+    float4 *A = sm + a.n_tw + 8 + (long)gi * NB * a.stride;
+    float4 *Bf = A + a.stride;
+    float4 *R = NB == 3 ? Bf + a.stride : Bf;
+    uint64_t *bar = bars + gi;
+    const int n = SPACE == 0 ? N : (SPACE == 1 ? N - 2 : N - 4);
+    const long groups_total = (long)gridDim.x * a.n_groups;
+    const uint32_t col_bytes = (uint32_t)N * 16u;
+    long mode = (long)blockIdx.x * a.n_groups + gi;
+    if (g.t == 0) {
+        mbar_init(bar);
+        fence_mbar_init();
+        fence_async_smem();
+        if (mode < a.n_modes) bulk_load(R, in + 2 * mode * (long)N, col_bytes, bar);
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    auto prefetch_next = [&](long next) {   // R is free: every thread's last access to it is done
+        fence_async_smem();
+        g.sync();
+        if (g.t == 0 && next < a.n_modes) bulk_load(R, in + 2 * next * (long)N, col_bytes, bar);
+    };
+    auto mkz = [&](int k) { return zld(a.mk + k); };
+    for (; mode < a.n_modes; mode += groups_total) {
+        const long next = mode + groups_total;
+        if (!g.all(mbar_wait(bar, parity))) {
+            // the copy did not land: flag it, give it time to finish, stop (group-uniform)
+            if (g.t == 0) atomicExch(a.err, 1);
+            mbar_wait(bar, parity);
+            return;
+        }
+        parity ^= 1u;
+        double2 *y = reinterpret_cast<double2 *>(out) + mode * N;
+        const double2 *xs = reinterpret_cast<const double2 *>(R);
+        if (KIND == 0) {
+            // coefficients (zero beyond the space) converted in place in R (= B), natural order
+            for (int k = g.t; k < N; k += g.nt) {
+                const double2 v = xs[k];
+                stz(Bf, k, k < n ? zfromf64(v) : kZero);
+            }
+            g.sync();
+            auto tk = [&](int k) -> Z {
+                if (k >= N) return kZero;
+                Z t = ldz(Bf, k);
+                if (SPACE == 1 && k >= 2) t = zsub(t, ldz(Bf, k - 2));
+                if (SPACE == 2 && k >= 2) {
+                    const float4 c = __ldg(a.coef + 2 * k);
+                    t = zfma(dneg(F2{c.x, c.y}), ldz(Bf, k - 2), t);
+                    if (k >= 4) t = zfma(F2{c.z, c.w}, ldz(Bf, k - 4), t);
+                }
+                return t;
+            };
+            for (int k = g.t; k < N; k += g.nt) {
+                Z v;
+                if (k == 0) {
+                    v = tk(0);
+                } else {
+                    const Z d = zadd(tk(k), zmi(tk(N - k)));          // t_k - i t_{N-k}
+                    // e^{i pi k/(2N)} = conj(mk[k]) for k <= N/2, i mk[N-k] above
+                    v = k <= half ? zmulc(d, mkz(k)) : zi(zmul(d, mkz(N - k)));
+                    v = zhalf(v);
+                }
+                stz(A, k, v);
+            }
+            prefetch_next(next);
+            fft_dif<true>(A, lg, tw, g);
+            for (int m = g.t; m < N; m += g.nt) {
+                const int src = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
+                y[m] = ztof64(ldz(A, dpos(src, lg)));
+            }
+        } else {
+            // values -> Makhoul order in A; R free for the next column
+            for (int m = g.t; m < N; m += g.nt) {
+                const int dst = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
+                stz(A, dst, zfromf64(xs[m]));
+            }
+            prefetch_next(next);
+            fft_dif<false>(A, lg, tw, g);
+            // C_k (DCT-II) in place: the pair (k, N-k) is read and written by one thread at
+            // positions dpos(k), dpos(N-k)
+            for (int k = g.t; k <= half; k += g.nt) {
+                if (k == 0) continue;                                  // C_0 = V_0
+                const int pk = dpos(k, lg), pn = dpos(N - k, lg);
+                const Z w = mkz(k);
+                const Z P = zmul(ldz(A, pk), w);
+                const Z Q = zmulc(ldz(A, pn), w);
+                stz(A, pk, zhalf(zadd(P, Q)));
+                if (k != half) stz(A, pn, zhalf(zi(zsub(P, Q))));
+            }
+            g.sync();
+            auto C = [&](int k) { return ldz(A, dpos(k, lg)); };
+            if (KIND == 2 && SPACE == 0) {
+                // uhat_k = C_k 2 / (N c_k): B is diagonal, pi c_k / 2
+                const float sc = 2.0f / (float)N;
+                for (int k = g.t; k < N; k += g.nt) y[k] = ztof64(zpow2(C(k), k == 0 ? 0.5f * sc : sc));
+            } else {
+                // scalar products S_l (Algorithm fst, forwardScalar)
+                auto S = [&](int l) -> Z {
+                    if (l >= n) return kZero;
+                    Z v = C(l);
+                    if (SPACE == 1) v = zsub(v, C(l + 2));
+                    if (SPACE == 2) {
+                        const float4 c = __ldg(a.coef + 2 * l + 1);
+                        v = zfma(dneg(F2{c.x, c.y}), C(l + 2), v);
+                        v = zfma(F2{c.z, c.w}, C(l + 4), v);
+                    }
+                    return zscale(v, a.pi_over_N);
+                };
+                if (KIND == 1) {
+                    for (int l = g.t; l < N; l += g.nt) y[l] = ztof64(S(l));
+                } else {
+                    for (int l = g.t; l < N; l += g.nt) stz(Bf, l + (l >> a.psh), S(l));
+                    g.sync();
+                    if (g.t < 32) mass_solve<SPACE == 1 ? 1 : 2>(Bf, A, n, a.K, a.psh, a.mass, a.RM, g.t);
+                    g.sync();
+                    for (int k = g.t; k < N; k += g.nt)
+                        y[k] = k < n ? ztof64(ldz(Bf, k + (k >> a.psh))) : make_double2(0.0, 0.0);
+                }
+            }
+        }
+        g.sync();
+    }
+}
+
+template <int KIND, int SPACE>
+const void *kernel_ptr() {
+    return reinterpret_cast<const void *>(&transform_kernel<KIND, SPACE>);
+}
+
+const void *kernel_of(int kind, int space) {
+    static const void *const k[3][3] = {
+        {kernel_ptr<0, 0>(), kernel_ptr<0, 1>(), kernel_ptr<0, 2>()},
+        {kernel_ptr<1, 0>(), kernel_ptr<1, 1>(), kernel_ptr<1, 2>()},
+        {kernel_ptr<2, 0>(), kernel_ptr<2, 1>(), kernel_ptr<2, 2>()},
+    };
+    return k[kind][space];
+}
+
+inline float4 pair4(long double a, long double b) {
+    const float ah = (float)a, bh = (float)b;
+    return make_float4(ah, (float)(a - (long double)ah), bh, (float)(b - (long double)bh));
+}
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return l;
+}
+
+// Chunk length of the mass solve for n unknowns: a power of two >= 2 with 16 chunks
+// covering the longer parity chain.
+int chunk_len(int n) {
+    const int R0 = (n + 1) / 2;
+    int K = 2;
+    while (16 * K < R0) K <<= 1;
+    return K;
+}
+
+// Per-row mass-solve table of one space (B rows: diag, +1, +2 per parity chain), from the
+// float64 LU (long double arithmetic) of each parity chain of B.
+void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const int n = space == 1 ? N - 2 : N - 4;
+    T.assign((size_t)2 * RM * 5, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int h = 0; h < 2; h++) {
+        const int R = (n - h + 1) / 2;
+        std::vector<long double> dg(R), s1(R, 0.0L), s2(R, 0.0L);
+        for (int i = 0; i < R; i++) {
+            const long double k = 2 * i + h, ck = (2 * i + h == 0) ? 2.0L : 1.0L;
+            if (space == 1) {
+                dg[i] = pi / 2 * (ck + 1);
+                if (i + 1 < R) s1[i] = -pi / 2;
+            } else {
+                const long double r2 = (k + 2) / (k + 3), r1 = (k + 1) / (k + 3);
+                dg[i] = pi / 2 * (ck + 4 * r2 * r2 + r1 * r1);
+                if (i + 1 < R) s1[i] = -pi * (r2 + (k + 4) * (k + 1) / ((k + 5) * (k + 3)));
+                if (i + 2 < R) s2[i] = pi / 2 * r1;
+            }
+        }
+        // unpivoted banded LU: B = L U, L unit lower (l1, l2), U (d, e1, e2); B symmetric
+        std::vector<long double> l1(R, 0.0L), l2(R, 0.0L), d(R), e1(R), e2(R);
+        for (int i = 0; i < R; i++) {
+            if (i >= 2) l2[i] = s2[i - 2] / d[i - 2];
+            if (i >= 1) l1[i] = (s1[i - 1] - (i >= 2 ? l2[i] * e1[i - 2] : 0.0L)) / d[i - 1];
+            d[i] = dg[i] - (i >= 1 ? l1[i] * e1[i - 1] : 0.0L) - (i >= 2 ? l2[i] * e2[i - 2] : 0.0L);
+            e1[i] = s1[i] - (i >= 1 ? l1[i] * e2[i - 1] : 0.0L);
+            e2[i] = s2[i];
+        }
+        float4 *Th = T.data() + (size_t)h * RM * 5;
+        for (int s = 0; s < R; s += K) {
+            const int e = std::min(R, s + K) - 1;
+            long double a1 = 1, a2 = 0, b1 = 0, b2 = 1;       // (G1, G2) at rows i-1, i-2
+            for (int i = s; i <= e; i++) {
+                const long double g1 = -l1[i] * a1 - l2[i] * b1, g2 = -l1[i] * a2 - l2[i] * b2;
+                Th[5 * i + 1] = pair4(g1, g2);
+                b1 = a1; b2 = a2; a1 = g1; a2 = g2;
+            }
+            a1 = 1; a2 = 0; b1 = 0; b2 = 1;                    // (H1, H2) at rows i+1, i+2
+            for (int i = e; i >= s; i--) {
+                const long double f1 = e1[i] / d[i], f2 = e2[i] / d[i];
+                const long double x1 = -f1 * a1 - f2 * b1, x2 = -f1 * a2 - f2 * b2;
+                Th[5 * i + 4] = pair4(x1, x2);
+                b1 = a1; b2 = a2; a1 = x1; a2 = x2;
+            }
+        }
+        for (int i = 0; i < R; i++) {
+            Th[5 * i + 0] = pair4(l1[i], l2[i]);
+            Th[5 * i + 2] = pair4(1.0L / d[i], e1[i] / d[i]);
+            Th[5 * i + 3] = pair4(e2[i] / d[i], 0.0L);
+        }
+    }
+}
+
+}  // namespace
+
+bool transform_supported(const Plan &p) { return !p.gl && p.N >= 8 && (p.N & (p.N - 1)) == 0; }
+
+// Number of float4 of the per-pass twiddle table: 3 Q per radix-4 pass.
+int twiddle_count(int N) {
+    int c = 0;
+    for (int lgL = ilog2(N); lgL >= 2; lgL -= 2) c += 3 * (1 << (lgL - 2));
+    return c;
+}
+
+// Tables of the transforms of an N-mode plan (float4 units, float-float pairs):
+//   [0, ntw)                per-pass twiddles of fft_dif
+//   [ntw, ntw + N/2 + 1)    mk[k] = e^{-i pi k/(2N)}, k = 0 .. N/2
+//   then 2 N: per k, (2k/(k+1), (k-3)/(k-1)) (psi -> T coefficients, k >= 2 / 4) and
+//                    (2(k+2)/(k+3), (k+1)/(k+3)) (Eq. phiN weights, k < N-4)
+//   then the mass-solve rows of phi (2 RMd 5) and of psi (2 RMb 5).
+cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
+    if (!transform_supported(p)) return cudaSuccess;
+    const int N = p.N, lg = ilog2(N);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const int Kd = chunk_len(N - 2), Kb = chunk_len(N - 4);
+    const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
+    const int ntw = twiddle_count(N), nmk = N / 2 + 1;
+    std::vector<float4> tab;
+    tab.reserve((size_t)ntw + nmk + 2 * N);
+    for (int lgL = lg, sh = 0; lgL >= 2; lgL -= 2, sh += 2) {
+        const int Q = 1 << (lgL - 2);
+        for (int j = 0; j < Q; j++)
+            for (int m = 1; m <= 3; m++) {
+                const long t = ((long)m * j) << sh;                    // < 3N/4
+                const long double ang = -2 * pi * (long double)t / N;
+                tab.push_back(pair4(cosl(ang), sinl(ang)));
+            }
+    }
+    for (int k = 0; k < nmk; k++) {
+        const long double ang = -pi * k / (2 * (long double)N);
+        tab.push_back(pair4(cosl(ang), sinl(ang)));
+    }
+    for (int k = 0; k < N; k++) {
+        const long double K = k;
+        const long double gi1 = k >= 2 ? 2 * K / (K + 1) : 0.0L, gi2 = k >= 4 ? (K - 3) / (K - 1) : 0.0L;
+        const long double g1 = k < N - 4 ? 2 * (K + 2) / (K + 3) : 0.0L, g2 = k < N - 4 ? (K + 1) / (K + 3) : 0.0L;
+        tab.push_back(pair4(gi1, gi2));
+        tab.push_back(pair4(g1, g2));
+    }
+    std::vector<float4> md, mb;
+    mass_rows(N, 1, Kd, RMd, md);
+    mass_rows(N, 2, Kb, RMb, mb);
+    p.tr_off_mass = (int)tab.size();
+    tab.insert(tab.end(), md.begin(), md.end());
+    tab.insert(tab.end(), mb.begin(), mb.end());
+    p.tr_ntw = ntw;
+    bytes += (long long)(tab.size() * sizeof(float4));
+    cudaError_t e = cudaMalloc((void **)&p.d_tr, tab.size() * sizeof(float4));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(p.d_tr, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    // launch shape per (kind, space): G warps per mode group (more threads per column for
+    // larger N), groups per block from the shared memory budget (twiddles, barriers,
+    // nbuf buffers per group) and the kernel's 768-thread bound; persistent grid from the
+    // occupancy.  A (kind, space) whose buffers do not fit gets no shape (unsupported).
+    int dev = 0, smem_max = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int psh = std::min(ilog2(2 * Kd), ilog2(2 * Kb));
+    const int stride = N + (N >> psh) + 4;
+    p.tr_stride = stride;
+    p.tr_psh = psh;
+    const int G = std::max(1, std::min(4, N / 256));
+    const long fixed = (long)(ntw + 8) * sizeof(float4);
+    for (int kind = 0; kind < 3; kind++)
+        for (int space = 0; space < 3; space++) {
+            const long per_group = (long)nbuf_of(kind, space) * stride * sizeof(float4);
+            const int groups = (int)std::min<long>(std::min(8, 24 / G), (smem_max - fixed) / per_group);
+            p.tr_groups[kind][space] = 0;
+            if (groups < 1) continue;
+            const int smem = (int)(fixed + groups * per_group);
+            const void *k = kernel_of(kind, space);
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                return e;
+            int per_sm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * G * groups, smem)) != cudaSuccess)
+                return e;
+            if (per_sm < 1) continue;
+            const long need = (p.n_modes + groups - 1) / groups;
+            p.tr_groups[kind][space] = groups;
+            p.tr_G = G;
+            p.tr_smem[kind][space] = smem;
+            p.tr_grid[kind][space] = (int)std::max<long>(1, std::min<long>((long)per_sm * sms, need));
+        }
+    return cudaSuccess;
+}
+
+bool transform_shape_ok(const Plan &p, int kind, int space) { return p.d_tr && p.tr_groups[kind][space] > 0; }
+
+cudaError_t launch_transform(const Plan &p, int kind, int space, const double *in, double *out, cudaStream_t s) {
+    if (p.n_modes <= 0) return cudaSuccess;
+    const int N = p.N;
+    TrArgs a;
+    a.N = N;
+    a.lg = ilog2(N);
+    a.G = p.tr_G;
+    a.n_groups = p.tr_groups[kind][space];
+    a.n_modes = p.n_modes;
+    a.stride = p.tr_stride;
+    a.n_tw = p.tr_ntw;
+    a.psh = p.tr_psh;
+    const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
+    a.K = space == 1 ? chunk_len(N - 2) : chunk_len(N - 4);
+    a.RM = space == 1 ? RMd : RMb;
+    a.tw = p.d_tr;
+    a.mk = p.d_tr + p.tr_ntw;
+    a.coef = a.mk + (N / 2 + 1);
+    const float4 *mass = p.d_tr + p.tr_off_mass;
+    a.mass = space == 1 ? mass : mass + (size_t)2 * RMd * 5;
+    const double pn = kPi / N;
+    const float ph = (float)pn;
+    a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
+    a.err = p.d_err + 3;
+    const dim3 grid((unsigned)p.tr_grid[kind][space]), block((unsigned)(32 * a.G * a.n_groups));
+    void *args[] = {&a, &in, &out};
+    return cudaLaunchKernel(kernel_of(kind, space), grid, block, args, (size_t)p.tr_smem[kind][space], s);
+}
+
+}  // namespace shen
