@@ -53,6 +53,16 @@ __device__ __forceinline__ void stz(float4 *A, int i, Z v) { A[i] = make_float4(
 __device__ __forceinline__ F2 dneg(F2 a) { return F2{-a.hi, -a.lo}; }
 __device__ __forceinline__ F2 nrm(F2 a) { return df::fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ Z zadd(Z a, Z b) { return Z{df::add(a.re, b.re), df::add(a.im, b.im)}; }
+// Sum without the final renormalisation: hi carries the float32 sum, lo the exact error of
+// it plus the low parts.  Only fed into a normalising add (never into a product).
+__device__ __forceinline__ F2 add_raw(F2 x, F2 y) {
+    const F2 s = df::two_sum(x.hi, y.hi);
+    return F2{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+__device__ __forceinline__ Z zadd_raw(Z a, Z b) { return Z{add_raw(a.re, b.re), add_raw(a.im, b.im)}; }
+__device__ __forceinline__ Z zsub_raw(Z a, Z b) {
+    return Z{add_raw(a.re, F2{-b.re.hi, -b.re.lo}), add_raw(a.im, F2{-b.im.hi, -b.im.lo})};
+}
 __device__ __forceinline__ Z zsub(Z a, Z b) { return Z{df::add(a.re, dneg(b.re)), df::add(a.im, dneg(b.im))}; }
 __device__ __forceinline__ Z zmul(Z a, Z w) {        // a w
     return Z{df::add(df::mul(a.re, w.re), dneg(df::mul(a.im, w.im))),
@@ -86,16 +96,18 @@ constexpr F2 kOne{1.f, 0.f};
 constexpr F2 kNil{0.f, 0.f};
 
 // Position of frequency k after the in-place DIF passes (radix 4 first, then one radix 2
-// when log2 N is odd): the first pass puts k mod 4 in quarter (k mod 4), and so on.
+// when log2 N is odd): the first pass puts k mod 4 in quarter (k mod 4), and so on, so
+// the base-4 digits of k come out reversed (times 2, plus the radix-2 digit, for odd lg).
+__device__ __forceinline__ uint32_t rev4(uint32_t x, int nd) {   // reverse nd base-4 digits
+    if (nd == 0) return 0u;
+    uint32_t r = __brev(x) >> (32 - 2 * nd);
+    return ((r & 0x55555555u) << 1) | ((r >> 1) & 0x55555555u);
+}
 __device__ __forceinline__ int dpos(int k, int lg) {
-    int p = 0, kk = k, ls = lg;
-    while (ls >= 2) {
-        ls -= 2;
-        p += (kk & 3) << ls;
-        kk >>= 2;
-    }
-    if (ls == 1) p += kk & 1;
-    return p;
+    const int nd = lg >> 1;
+    if ((lg & 1) == 0) return (int)rev4((uint32_t)k, nd);
+    const uint32_t low = (uint32_t)k & ((1u << (lg - 1)) - 1u);
+    return (int)(2u * rev4(low, nd) + ((uint32_t)k >> (lg - 1)));
 }
 
 // Thread group of one mode column: G warps (32 G threads) synchronised by the named
@@ -137,7 +149,7 @@ __device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
             const int j = b & (Q - 1);
             const int base = ((b >> lgQ) << lgL) + j;
             const Z a = ldz(A, base), bb = ldz(A, base + Q), c = ldz(A, base + 2 * Q), d = ldz(A, base + 3 * Q);
-            const Z s0 = zadd(a, c), s1 = zsub(a, c), s2 = zadd(bb, d), s3 = zsub(bb, d);
+            const Z s0 = zadd_raw(a, c), s1 = zsub_raw(a, c), s2 = zadd_raw(bb, d), s3 = zsub_raw(bb, d);
             Z y0 = zadd(s0, s2), y2 = zsub(s0, s2);
             Z y1 = INV ? zadd(s1, zi(s3)) : zadd(s1, zmi(s3));
             Z y3 = INV ? zadd(s1, zmi(s3)) : zadd(s1, zi(s3));
@@ -173,19 +185,22 @@ __device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
 
 // ------------------------------------------------------------------ mass solve
 
-// Shuffle of a float-float value / complex value between lanes of a 16-lane group.
-__device__ __forceinline__ F2 shup(F2 v, int d) {
-    return F2{__shfl_up_sync(0xffffffffu, v.hi, d, 16), __shfl_up_sync(0xffffffffu, v.lo, d, 16)};
+// Shuffles of float-float / complex values within segments of `w` lanes (16 or 32).
+__device__ __forceinline__ F2 shup(F2 v, int d, int w) {
+    return F2{__shfl_up_sync(0xffffffffu, v.hi, d, w), __shfl_up_sync(0xffffffffu, v.lo, d, w)};
 }
-__device__ __forceinline__ F2 shdn(F2 v, int d) {
-    return F2{__shfl_down_sync(0xffffffffu, v.hi, d, 16), __shfl_down_sync(0xffffffffu, v.lo, d, 16)};
+__device__ __forceinline__ F2 shdn(F2 v, int d, int w) {
+    return F2{__shfl_down_sync(0xffffffffu, v.hi, d, w), __shfl_down_sync(0xffffffffu, v.lo, d, w)};
 }
-__device__ __forceinline__ Z shup(Z v, int d) { return Z{shup(v.re, d), shup(v.im, d)}; }
-__device__ __forceinline__ Z shdn(Z v, int d) { return Z{shdn(v.re, d), shdn(v.im, d)}; }
+__device__ __forceinline__ Z shup(Z v, int d, int w) { return Z{shup(v.re, d, w), shup(v.im, d, w)}; }
+__device__ __forceinline__ Z shdn(Z v, int d, int w) { return Z{shdn(v.re, d, w), shdn(v.im, d, w)}; }
 __device__ __forceinline__ F2 dmul(F2 a, F2 b) { return nrm(df::mul(a, b)); }
 __device__ __forceinline__ F2 dfma2(F2 a, F2 b, F2 c, F2 d) {   // a b + c d
     return df::add(df::mul(a, b), df::mul(c, d));
 }
+__device__ __forceinline__ F2 lo2(float4 v) { return F2{v.x, v.y}; }
+__device__ __forceinline__ F2 hi2(float4 v) { return F2{v.z, v.w}; }
+__device__ __forceinline__ Z znrm(Z v) { return Z{nrm(v.re), nrm(v.im)}; }
 
 // Affine carry map of a chunk on the state (s0, s1) (BW = 2) or s0 (BW = 1):
 //   state -> M state + c.
@@ -215,36 +230,36 @@ __device__ __forceinline__ CarryMap compose(const CarryMap &a, const CarryMap &b
 }
 
 template <int BW, bool UP>
-__device__ __forceinline__ CarryMap shuffle_map(const CarryMap &m, int d) {
+__device__ __forceinline__ CarryMap shuffle_map(const CarryMap &m, int d, int w) {
     CarryMap r;
-    if (UP) {
-        r.m00 = shup(m.m00, d);
-        r.c0 = shup(m.c0, d);
-        if (BW == 2) {
-            r.m01 = shup(m.m01, d); r.m10 = shup(m.m10, d); r.m11 = shup(m.m11, d); r.c1 = shup(m.c1, d);
-        }
+    auto sh = [&](F2 v) { return UP ? shup(v, d, w) : shdn(v, d, w); };
+    auto shz = [&](Z v) { return UP ? shup(v, d, w) : shdn(v, d, w); };
+    r.m00 = sh(m.m00);
+    r.c0 = shz(m.c0);
+    if (BW == 2) {
+        r.m01 = sh(m.m01); r.m10 = sh(m.m10); r.m11 = sh(m.m11); r.c1 = shz(m.c1);
     } else {
-        r.m00 = shdn(m.m00, d);
-        r.c0 = shdn(m.c0, d);
-        if (BW == 2) {
-            r.m01 = shdn(m.m01, d); r.m10 = shdn(m.m10, d); r.m11 = shdn(m.m11, d); r.c1 = shdn(m.c1, d);
-        }
+        r.m01 = r.m10 = r.m11 = kNil; r.c1 = kZero;
     }
-    if (BW == 1) { r.m01 = r.m10 = r.m11 = kNil; r.c1 = kZero; }
     return r;
 }
 
-// Per-row mass-solve table (5 float4 per row of a parity chain, float-float pairs):
-//   [0] (l1, l2)   L_{i,i-1}, L_{i,i-2} of B's LU (unit lower)
-//   [1] (G1, G2)   chunk-local homogeneous forward solutions for carries (y_{s-1}, y_{s-2}) = (1,0), (0,1)
-//   [2] (1/d, f1)  1/U_ii and U_{i,i+1}/U_ii
-//   [3] (f2, 0)    U_{i,i+2}/U_ii
-//   [4] (H1, H2)   chunk-local homogeneous backward solutions for (x_{e+1}, x_{e+2}) = (1,0), (0,1)
-// Solve B x = S for the warp's column: S in A (padded positions), x written back to A;
-// B is scratch.  n unknowns, chunk length K, padding shift psh.
+// Per-N mass-solve tables, five planes of float4 (float-float pairs), plane f, parity h,
+// row i at [(2 f + h) RM + i]:
+//   f = 0 (l1, l2)   L_{i,i-1}, L_{i,i-2} of B's LU (unit lower)
+//   f = 1 (G1, G2)   chunk-local homogeneous forward solutions for the carries
+//                    (y_{s-1}, y_{s-2}) = (1, 0), (0, 1)
+//   f = 2 (1/d, f1)  1/U_ii and U_{i,i+1} / U_ii
+//   f = 3 (f2, 0)    U_{i,i+2} / U_ii
+//   f = 4 (H1, H2)   chunk-local homogeneous backward solutions for (x_{e+1}, x_{e+2})
+// Solve B x = S for the column: S in X (padded positions), x written back to X; W is
+// scratch.  LP lanes per parity chain (16: lanes 0-15 / 16-31 of one warp; 32: warp 0 of
+// the caller for parity 0, warp 1 for parity 1); chunk length K, padding shift psh.
+// Table rows of the serial passes are fetched in blocks of PB ahead of their use.
 template <int BW>
-__device__ void mass_solve(float4 *A, float4 *Bf, int n, int K, int psh, const float4 *T, int RM, int lane) {
-    const int h = lane >> 4, j = lane & 15;
+__device__ void mass_solve(float4 *X, float4 *W, int n, int K, int psh, const float4 *T, int RM, int h, int j,
+                           int LP) {
+    constexpr int PB = 4;
     const int R = (n - h + 1) / 2;
     const int s = j * K, e = min(R, s + K) - 1;
     const bool act = s < R;
@@ -252,109 +267,140 @@ __device__ void mass_solve(float4 *A, float4 *Bf, int n, int K, int psh, const f
         const int k = 2 * i + h;
         return k + (k >> psh);
     };
-    const float4 *Th = T + (long)h * RM * 5;
-    auto pr = [](float4 v, int w) { return w == 0 ? F2{v.x, v.y} : F2{v.z, v.w}; };
+    const float4 *TL = T + (long)(0 + h) * RM, *TG = T + (long)(2 + h) * RM, *TB = T + (long)(4 + h) * RM;
+    const float4 *TF = T + (long)(6 + h) * RM, *TH = T + (long)(8 + h) * RM;
 
     // forward elimination, chunk-local with zero carries: p_i = S_i - l1 p_{i-1} - l2 p_{i-2}
     Z p1 = kZero, p2 = kZero;
     CarryMap mp{kOne, kNil, kNil, kOne, kZero, kZero};
     if (act) {
-        for (int i = s; i <= e; i++) {
-            const float4 lv = __ldg(Th + 5 * i);
-            Z y = ldz(A, P(i));
-            y = zfma(dneg(pr(lv, 0)), p1, y);
-            if (BW == 2) y = zfma(dneg(pr(lv, 1)), p2, y);
-            y = Z{nrm(y.re), nrm(y.im)};
-            stz(Bf, P(i), y);
-            p2 = p1;
-            p1 = y;
+        float4 la[PB], lb[PB];
+        auto load = [&](float4 (&l)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) l[q] = __ldg(TL + min(i0 + q, e));
+        };
+        auto run = [&](const float4 (&l)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                const int i = i0 + q;
+                if (i <= e) {
+                    Z y = zfma(dneg(lo2(l[q])), p1, ldz(X, P(i)));
+                    if (BW == 2) y = zfma(dneg(hi2(l[q])), p2, y);
+                    y = znrm(y);
+                    stz(W, P(i), y);
+                    p2 = p1;
+                    p1 = y;
+                }
+            }
+        };
+        load(la, s);
+        for (int i0 = s; i0 <= e; i0 += 2 * PB) {
+            load(lb, i0 + PB);
+            run(la, i0);
+            load(la, i0 + 2 * PB);
+            run(lb, i0 + PB);
         }
-        const float4 ge = __ldg(Th + 5 * e + 1);
-        mp.m00 = pr(ge, 0);
+        const float4 ge = __ldg(TG + e);
+        mp.m00 = lo2(ge);
         mp.c0 = p1;
         if (BW == 2) {
-            mp.m01 = pr(ge, 1);
+            mp.m01 = hi2(ge);
             if (e - 1 >= s) {
-                const float4 g1 = __ldg(Th + 5 * (e - 1) + 1);
-                mp.m10 = pr(g1, 0);
-                mp.m11 = pr(g1, 1);
+                const float4 g1 = __ldg(TG + e - 1);
+                mp.m10 = lo2(g1);
+                mp.m11 = hi2(g1);
                 mp.c1 = p2;
-            } else {
+            } else {                       // one-row chunk: y_{e-1} = y_{s-1} is the carry itself
                 mp.m10 = kOne;
                 mp.m11 = kNil;
-                mp.c1 = kZero;
             }
-        } else {
-            mp.m01 = mp.m10 = mp.m11 = kNil;
         }
-    } else if (BW == 1) {
-        mp.m11 = kNil;
     }
+    if (BW == 1) mp.m01 = mp.m10 = mp.m11 = kNil;
     // inclusive scan of the chunk maps, chunk 0 first
-    for (int d = 1; d < 16; d <<= 1) {
-        const CarryMap o = shuffle_map<BW, true>(mp, d);
+    for (int d = 1; d < LP; d <<= 1) {
+        const CarryMap o = shuffle_map<BW, true>(mp, d, LP);
         if (j >= d) mp = compose<BW>(mp, o);
     }
-    Z Y1 = shup(mp.c0, 1), Y2 = BW == 2 ? shup(mp.c1, 1) : kZero;
+    Z Y1 = shup(mp.c0, 1, LP), Y2 = BW == 2 ? shup(mp.c1, 1, LP) : kZero;
     if (j == 0) Y1 = Y2 = kZero;
     if (act) {
+#pragma unroll 4
         for (int i = s; i <= e; i++) {
-            const float4 gv = __ldg(Th + 5 * i + 1);
-            Z y = zfma(pr(gv, 0), Y1, ldz(Bf, P(i)));
-            if (BW == 2) y = zfma(pr(gv, 1), Y2, y);
-            stz(Bf, P(i), Z{nrm(y.re), nrm(y.im)});
+            const float4 gv = __ldg(TG + i);
+            Z y = zfma(lo2(gv), Y1, ldz(W, P(i)));
+            if (BW == 2) y = zfma(hi2(gv), Y2, y);
+            stz(W, P(i), znrm(y));
         }
     }
     // back substitution, chunk-local: q_i = y_i / d_i - f1 q_{i+1} - f2 q_{i+2}
     Z q1 = kZero, q2 = kZero;
     CarryMap mq{kOne, kNil, kNil, kOne, kZero, kZero};
-    if (BW == 1) mq.m11 = kNil;
     if (act) {
-        for (int i = e; i >= s; i--) {
-            const float4 b0 = __ldg(Th + 5 * i + 2);
-            Z x = zscale(ldz(Bf, P(i)), pr(b0, 0));
-            x = zfma(dneg(pr(b0, 1)), q1, x);
-            if (BW == 2) x = zfma(dneg(pr(__ldg(Th + 5 * i + 3), 0)), q2, x);
-            x = Z{nrm(x.re), nrm(x.im)};
-            stz(Bf, P(i), x);
-            q2 = q1;
-            q1 = x;
+        float4 ba[PB], bb[PB], fa[PB], fb[PB];
+        auto load = [&](float4 (&b)[PB], float4 (&f)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                const int i = max(i0 - q, s);
+                b[q] = __ldg(TB + i);
+                if (BW == 2) f[q] = __ldg(TF + i);
+            }
+        };
+        auto run = [&](const float4 (&b)[PB], const float4 (&f)[PB], int i0) {
+#pragma unroll
+            for (int q = 0; q < PB; q++) {
+                const int i = i0 - q;
+                if (i >= s) {
+                    Z x = zscale(ldz(W, P(i)), lo2(b[q]));
+                    x = zfma(dneg(hi2(b[q])), q1, x);
+                    if (BW == 2) x = zfma(dneg(lo2(f[q])), q2, x);
+                    x = znrm(x);
+                    stz(W, P(i), x);
+                    q2 = q1;
+                    q1 = x;
+                }
+            }
+        };
+        load(ba, fa, e);
+        for (int i0 = e; i0 >= s; i0 -= 2 * PB) {
+            load(bb, fb, i0 - PB);
+            run(ba, fa, i0);
+            load(ba, fa, i0 - 2 * PB);
+            run(bb, fb, i0 - PB);
         }
-        const float4 hs = __ldg(Th + 5 * s + 4);
-        mq.m00 = pr(hs, 0);
+        const float4 hs = __ldg(TH + s);
+        mq.m00 = lo2(hs);
         mq.c0 = q1;
         if (BW == 2) {
-            mq.m01 = pr(hs, 1);
+            mq.m01 = hi2(hs);
             if (s + 1 <= e) {
-                const float4 h1 = __ldg(Th + 5 * (s + 1) + 4);
-                mq.m10 = pr(h1, 0);
-                mq.m11 = pr(h1, 1);
+                const float4 h1 = __ldg(TH + s + 1);
+                mq.m10 = lo2(h1);
+                mq.m11 = hi2(h1);
                 mq.c1 = q2;
-            } else {
+            } else {                       // one-row chunk: x_{s+1} = x_{e+1} is the carry itself
                 mq.m10 = kOne;
                 mq.m11 = kNil;
-                mq.c1 = kZero;
             }
-        } else {
-            mq.m01 = mq.m10 = mq.m11 = kNil;
         }
     }
+    if (BW == 1) mq.m01 = mq.m10 = mq.m11 = kNil;
     // inclusive scan from the last chunk down
-    for (int d = 1; d < 16; d <<= 1) {
-        const CarryMap o = shuffle_map<BW, false>(mq, d);
-        if (j + d < 16) mq = compose<BW>(mq, o);
+    for (int d = 1; d < LP; d <<= 1) {
+        const CarryMap o = shuffle_map<BW, false>(mq, d, LP);
+        if (j + d < LP) mq = compose<BW>(mq, o);
     }
-    Z X1 = shdn(mq.c0, 1), X2 = BW == 2 ? shdn(mq.c1, 1) : kZero;
-    if (j == 15) X1 = X2 = kZero;
+    Z X1 = shdn(mq.c0, 1, LP), X2 = BW == 2 ? shdn(mq.c1, 1, LP) : kZero;
+    if (j == LP - 1) X1 = X2 = kZero;
     if (act) {
+#pragma unroll 4
         for (int i = s; i <= e; i++) {
-            const float4 hv = __ldg(Th + 5 * i + 4);
-            Z x = zfma(pr(hv, 0), X1, ldz(Bf, P(i)));
-            if (BW == 2) x = zfma(pr(hv, 1), X2, x);
-            stz(A, P(i), Z{nrm(x.re), nrm(x.im)});
+            const float4 hv = __ldg(TH + i);
+            Z x = zfma(lo2(hv), X1, ldz(W, P(i)));
+            if (BW == 2) x = zfma(hi2(hv), X2, x);
+            stz(X, P(i), znrm(x));
         }
     }
-    __syncwarp();
 }
 
 // ------------------------------------------------------------------ kernel
@@ -474,17 +520,17 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 }
                 return t;
             };
-            for (int k = g.t; k < N; k += g.nt) {
-                Z v;
+            // pairs (k, N-k), 0 < k <= N/2, with w = e^{-i pi k/(2N)} = mk[k]:
+            //   V_k     = conj(w) (t_k - i t_{N-k}) / 2
+            //   V_{N-k} = i w (t_{N-k} - i t_k) / 2      (e^{i pi (N-k)/(2N)} = i w)
+            for (int k = g.t; k <= half; k += g.nt) {
                 if (k == 0) {
-                    v = tk(0);
-                } else {
-                    const Z d = zadd(tk(k), zmi(tk(N - k)));          // t_k - i t_{N-k}
-                    // e^{i pi k/(2N)} = conj(mk[k]) for k <= N/2, i mk[N-k] above
-                    v = k <= half ? zmulc(d, mkz(k)) : zi(zmul(d, mkz(N - k)));
-                    v = zhalf(v);
+                    stz(A, 0, tk(0));
+                    continue;
                 }
-                stz(A, k, v);
+                const Z t1 = tk(k), t2 = tk(N - k), w = mkz(k);
+                stz(A, k, zhalf(zmulc(zadd(t1, zmi(t2)), w)));
+                if (k != half) stz(A, N - k, zhalf(zi(zmul(zadd(t2, zmi(t1)), w))));
             }
             prefetch_next(next);
             fft_dif<true>(A, lg, tw, g);
@@ -535,7 +581,10 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 } else {
                     for (int l = g.t; l < N; l += g.nt) stz(Bf, l + (l >> a.psh), S(l));
                     g.sync();
-                    if (g.t < 32) mass_solve<SPACE == 1 ? 1 : 2>(Bf, A, n, a.K, a.psh, a.mass, a.RM, g.t);
+                    // lanes per parity: a warp each when the group has two or more, else half a warp
+                    const int LP = g.nt >= 64 ? 32 : 16;
+                    if (g.t < 2 * LP)
+                        mass_solve<SPACE == 1 ? 1 : 2>(Bf, A, n, a.K, a.psh, a.mass, a.RM, g.t / LP, g.t % LP, LP);
                     g.sync();
                     for (int k = g.t; k < N; k += g.nt)
                         y[k] = k < n ? ztof64(ldz(Bf, k + (k >> a.psh))) : make_double2(0.0, 0.0);
@@ -571,17 +620,23 @@ int ilog2(int v) {
     return l;
 }
 
-// Chunk length of the mass solve for n unknowns: a power of two >= 2 with 16 chunks
-// covering the longer parity chain.
-int chunk_len(int n) {
+// Chunk length of the mass solve for n unknowns and LP lanes per parity chain: a power of
+// two >= 2 with LP chunks covering the longer parity chain.
+int chunk_len(int n, int LP) {
     const int R0 = (n + 1) / 2;
     int K = 2;
-    while (16 * K < R0) K <<= 1;
+    while (LP * K < R0) K <<= 1;
     return K;
 }
 
-// Per-row mass-solve table of one space (B rows: diag, +1, +2 per parity chain), from the
-// float64 LU (long double arithmetic) of each parity chain of B.
+// Warps per mode group of an N-mode plan (more threads per column for larger N), and the
+// mass solve's lanes per parity chain that go with it.
+int group_warps(int N) { return std::max(1, std::min(4, N / 256)); }
+int lanes_per_parity(int N) { return group_warps(N) >= 2 ? 32 : 16; }
+
+// Mass-solve tables of one space in the five planes mass_solve reads (B rows: diagonal,
+// +1, +2 per parity chain), from the unpivoted LU of each parity chain of B in long double
+// arithmetic, rounded to float-float pairs.
 void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T) {
     const long double pi = 3.141592653589793238462643383279502884L;
     const int n = space == 1 ? N - 2 : N - 4;
@@ -610,27 +665,27 @@ void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T) {
             e1[i] = s1[i] - (i >= 1 ? l1[i] * e2[i - 1] : 0.0L);
             e2[i] = s2[i];
         }
-        float4 *Th = T.data() + (size_t)h * RM * 5;
+        auto at = [&](int f, int i) -> float4 & { return T[(size_t)(2 * f + h) * RM + i]; };
         for (int s = 0; s < R; s += K) {
             const int e = std::min(R, s + K) - 1;
             long double a1 = 1, a2 = 0, b1 = 0, b2 = 1;       // (G1, G2) at rows i-1, i-2
             for (int i = s; i <= e; i++) {
                 const long double g1 = -l1[i] * a1 - l2[i] * b1, g2 = -l1[i] * a2 - l2[i] * b2;
-                Th[5 * i + 1] = pair4(g1, g2);
+                at(1, i) = pair4(g1, g2);
                 b1 = a1; b2 = a2; a1 = g1; a2 = g2;
             }
             a1 = 1; a2 = 0; b1 = 0; b2 = 1;                    // (H1, H2) at rows i+1, i+2
             for (int i = e; i >= s; i--) {
                 const long double f1 = e1[i] / d[i], f2 = e2[i] / d[i];
                 const long double x1 = -f1 * a1 - f2 * b1, x2 = -f1 * a2 - f2 * b2;
-                Th[5 * i + 4] = pair4(x1, x2);
+                at(4, i) = pair4(x1, x2);
                 b1 = a1; b2 = a2; a1 = x1; a2 = x2;
             }
         }
         for (int i = 0; i < R; i++) {
-            Th[5 * i + 0] = pair4(l1[i], l2[i]);
-            Th[5 * i + 2] = pair4(1.0L / d[i], e1[i] / d[i]);
-            Th[5 * i + 3] = pair4(e2[i] / d[i], 0.0L);
+            at(0, i) = pair4(l1[i], l2[i]);
+            at(2, i) = pair4(1.0L / d[i], e1[i] / d[i]);
+            at(3, i) = pair4(e2[i] / d[i], 0.0L);
         }
     }
 }
@@ -656,7 +711,8 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
     const int N = p.N, lg = ilog2(N);
     const long double pi = 3.141592653589793238462643383279502884L;
-    const int Kd = chunk_len(N - 2), Kb = chunk_len(N - 4);
+    const int LP = lanes_per_parity(N);
+    const int Kd = chunk_len(N - 2, LP), Kb = chunk_len(N - 4, LP);
     const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
     const int ntw = twiddle_count(N), nmk = N / 2 + 1;
     std::vector<float4> tab;
@@ -706,7 +762,7 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     const int stride = N + (N >> psh) + 4;
     p.tr_stride = stride;
     p.tr_psh = psh;
-    const int G = std::max(1, std::min(4, N / 256));
+    const int G = group_warps(N);
     const long fixed = (long)(ntw + 8) * sizeof(float4);
     for (int kind = 0; kind < 3; kind++)
         for (int space = 0; space < 3; space++) {
@@ -717,6 +773,9 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
             const int smem = (int)(fixed + groups * per_group);
             const void *k = kernel_of(kind, space);
             if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                return e;
+            const int carve = (int)std::min<long>(100, (smem * 100L + smem_max - 1) / smem_max + 1);
+            if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carve)) != cudaSuccess)
                 return e;
             int per_sm = 0;
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * G * groups, smem)) != cudaSuccess)
@@ -746,7 +805,7 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, const double *i
     a.n_tw = p.tr_ntw;
     a.psh = p.tr_psh;
     const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
-    a.K = space == 1 ? chunk_len(N - 2) : chunk_len(N - 4);
+    a.K = space == 1 ? chunk_len(N - 2, lanes_per_parity(N)) : chunk_len(N - 4, lanes_per_parity(N));
     a.RM = space == 1 ? RMd : RMb;
     a.tw = p.d_tr;
     a.mk = p.d_tr + p.tr_ntw;
