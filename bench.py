@@ -42,6 +42,19 @@ LEAN_WORKLOADS = {"large"}
 BYTES_PER_ROW = 32          # algorithmic bytes per complex row of one solve: read f + write u
 
 
+# arithmetic of each solve path (all read and write complex128 fields)
+DTYPES = {"fp64": "f64", "df": "f32x2 (float-float)", "df_r1": "f32 sweeps + f32x2 refinement",
+          "df_r2": "f32 sweeps + f32x2 refinement", "fp32_r1": "f32 sweeps + f64 refinement",
+          "fp32_r2": "f32 sweeps + f64 refinement"}
+
+
+def dtype_of(prec):
+    names = {DTYPES.get(p, p) for p in prec.values()}
+    if len(names) == 1:
+        return names.pop()
+    return ", ".join(f"{k}: {DTYPES.get(v, v)}" for k, v in sorted(prec.items()))
+
+
 def n_modes_of(w):
     return (w["Nx"] // 2 + 1) * w["Nz"]
 
@@ -544,6 +557,30 @@ def main():
         mv["linear_step"] = {"ms": mls, "value": rows * 2 / (mls * 1e-3), "unit": "solves*N/s",
                              "bytes_per_row": 128, "frac_hbm": rows * 128 / (mls * 1e-3) / 1e9 / pk}
         del outs
+        if N & (N - 1) == 0:
+            # wall-normal transforms of every mode column (Algorithms fst / ifst): read one
+            # complex128 field, write one (32 algorithmic bytes per complex point)
+            tr_out = torch.empty_like(f_h)
+            trs = {"bytes_per_point": 32, "input": "the Helmholtz solution field"}
+            for kind in ("inverse", "scalar", "forward"):
+                for space in ("chebyshev", "dirichlet", "biharmonic"):
+                    try:
+                        for _ in range(2):
+                            plan.transform(kind, space, u_h, out=tr_out, stream=stream)
+                    except Exception as exc:             # a shape that does not fit this GPU
+                        trs[f"{kind}_{space}"] = {"unsupported": str(exc)}
+                        continue
+                    ev_t = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                    for s in range(5):
+                        ev_t[s].record(stream)
+                        plan.transform(kind, space, u_h, out=tr_out, stream=stream)
+                    ev_t[5].record(stream)
+                    torch.cuda.synchronize()
+                    mt = float(np.mean([ev_t[s].elapsed_time(ev_t[s + 1]) for s in range(5)]))
+                    trs[f"{kind}_{space}"] = {"ms": mt, "points_per_s": rows / (mt * 1e-3),
+                                              "frac_hbm": rows * 32 / (mt * 1e-3) / 1e9 / pk}
+            mv["transforms"] = trs
+            del tr_out
     ms, = max_over_ranks([ms], pg, "cuda")
     step_rows = 2 * rows + (2 * N if lean else 0)            # complex rows solved per step
     value = world * step_rows / (ms * 1e-3)
@@ -701,6 +738,7 @@ def main():
 
     velocity = mv.pop("velocity", None) if mv else None
     linear_step = mv.pop("linear_step", None) if mv else None
+    transforms = mv.pop("transforms", None) if mv else None
     peak, peak_kind = peaks()
     dom = "biharmonic" if t_b >= t_h else "helmholtz"
     t_dom = max(t_b, t_h)
@@ -712,7 +750,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "solves*N/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if set(prec.values()) == {"fp64"} else "f32 sweeps + refinement (io f64)",
+            "dtype": dtype_of(prec),
             "data": "synthetic", "precision": prec,
             "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes, "rows": rows,
                        "streams": args.streams, "cuda_graph": use_graph, "plan_device_bytes": plan.info()[3]
@@ -720,7 +758,7 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "compare_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": (4 if lean else 2) * args.steps, "clocks": clk, "e2e": e2e,
-            "rhs_matvec": mv, "velocity": velocity, "linear_step": linear_step}
+            "rhs_matvec": mv, "velocity": velocity, "linear_step": linear_step, "transforms": transforms}
     if sample is not None:
         modes, refined, F_h, U_h, F_b, U_b = sample
         line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
