@@ -60,6 +60,34 @@ def test_on_roundoff_relative_to_pivoted_lu():
                 assert e_on <= 10 * e_lu + 1e-13, (problem, N, zl, e_on, e_lu)
 
 
+def test_roundoff_matches_paper_table_order():
+    """Table tab:roundoff (Sec. 5; stored in tests/golden/roundoff_table.json): the same
+    procedure -- u ~ U(0, 1), f = H u, v from the O(N) algorithms, max|u - v| / max|u|,
+    averaged -- lands within a factor 5 of the printed values at N_x = 64 and 128 for every
+    wavenumber and both problems, including the biharmonic's growth with z.  (At larger N_x
+    this oracle's errors keep growing roughly like N_x while the printed ones level off.)"""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "roundoff_table.json")) as fh:
+        tab = json.load(fh)
+    c = so.c_of(tab["nu"], tab["dt"])
+    rng = np.random.default_rng(2017)
+    for problem in ("biharmonic", "helmholtz"):
+        for zi, zl in enumerate(tab["z"]):
+            for ni, N in enumerate(tab["N_x"][:2]):
+                n = so.n_unknowns(problem, N)
+                H = so.system_matrix(problem, N, float(zl) ** 2, c)
+                errs = []
+                for _ in range(30):
+                    u = rng.uniform(0, 1, n)
+                    f = np.zeros(N, complex)
+                    f[:n] = H @ u
+                    v = on.solve_modes(problem, N, np.array([float(zl) ** 2]), c, f[None, :])[0, :n].real
+                    errs.append(np.max(np.abs(u - v)) / np.max(np.abs(u)))
+                paper = tab[problem][zi][ni]
+                assert paper / 5 <= np.mean(errs) <= 5 * paper, (problem, zl, N, np.mean(errs), paper)
+
+
 def test_on_rejects_too_small():
     with pytest.raises(ValueError):
         on.solve_modes("biharmonic", 7, np.array([0.0]), 1.0, np.zeros((1, 7), complex))
