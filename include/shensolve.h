@@ -290,6 +290,16 @@ shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, l
 shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, double *u, int *chosen,
                                float *ms, void *stream);
 
+/* Row-block shape of the plan's float-float sweeps for `problem` (the choice
+ * shen_plan_autotune makes; every shape gives the same bits):
+ *   0  rows prefetched in registers, 4 (biharmonic) / 8 (Helmholtz) per block, two blocks in
+ *      flight;
+ *   1  the same with 4 + 4 rows (biharmonic) / 4 rows (Helmholtz) per block.
+ * shen_plan_set_shape returns SHEN_ERR_ARG for another shape; the setting lasts until the
+ * next call or shen_plan_autotune.  A property of the library, not of the method. */
+shen_status shen_plan_set_shape(shen_plan_t plan, int problem, int shape);
+shen_status shen_plan_get_shape(shen_plan_t plan, int problem, int *shape);
+
 /* Right-hand-side operator: out = R x + beta * y for every mode (R = R_h or R_b by
  * `problem`).  y may be NULL (then beta is ignored).  x, y, out: DEVICE fields;
  * out must not overlap x or y.  float64 arithmetic.

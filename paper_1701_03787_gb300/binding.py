@@ -50,6 +50,8 @@ def lib():
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_residual": ([P, I, P, P, P, P], I),
         "shen_transform": ([P, I, I, P, P, P], I),
+        "shen_plan_set_shape": ([P, I, I], I),
+        "shen_plan_get_shape": ([P, I, P], I),
         "shen_velocity": ([P, P, P, P, P, P, I, P], I),
         "shen_mass_matvec": ([P, I, P, P, D, P, P], I),
         "shen_linear_step": ([P, P, P, P, P, P, P, P, P, I, P], I),
@@ -310,6 +312,15 @@ class Plan:
         check(lib().shen_velocity(self._h, _ptr(u), _ptr(g), _ptr(v), _ptr(w), _ptr(f), _prec(precision),
                                   _stream(stream)), "shen_velocity")
         return v, w
+
+    def set_shape(self, problem, shape):
+        """Row-block shape (0, 1, 2) of the float-float sweeps of `problem` (same bits)."""
+        check(lib().shen_plan_set_shape(self._h, _problem(problem), int(shape)), "shen_plan_set_shape")
+
+    def shape(self, problem):
+        v = ctypes.c_int()
+        check(lib().shen_plan_get_shape(self._h, _problem(problem), ctypes.byref(v)), "shen_plan_get_shape")
+        return v.value
 
     def transform(self, kind, space, x, out=None, stream=None):
         """Wall-normal transform of every mode column (see shen_transform): kind "inverse"

@@ -174,13 +174,13 @@ cudaError_t df_setup(Plan &p, long long &bytes) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const void *kern[2][2] = {{(const void *)helm_df_kernel<0>, (const void *)helm_df_kernel<1>},
-                              {(const void *)bih_df_kernel<0>, (const void *)bih_df_kernel<1>}};
+    const void *kern[2][kDfShapes] = {{(const void *)helm_df_kernel<0>, (const void *)helm_df_kernel<1>},
+                                      {(const void *)bih_df_kernel<0>, (const void *)bih_df_kernel<1>}};
     // a launch covers at most all the plan's chains: no more blocks than that
     const int needed = (int)std::min<long>(nblocks(2 * p.n_modes, 128), 1L << 30);
     for (int pb = 0; pb < 2; pb++) {
         int most = 1;
-        for (int v = 0; v < 2; v++) {
+        for (int v = 0; v < kDfShapes; v++) {
             int per_sm = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[pb][v], 128, 0);
             if (e != cudaSuccess) return e;

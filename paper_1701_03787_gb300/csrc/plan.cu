@@ -603,6 +603,21 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
     return SHEN_OK;
 }
 
+shen_status shen_plan_set_shape(shen_plan_t plan, int problem, int shape) {
+    if (!plan) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (shape < 0 || shape >= kDfShapes) return SHEN_ERR_ARG;
+    plan->p.df_variant[problem] = shape;
+    return SHEN_OK;
+}
+
+shen_status shen_plan_get_shape(shen_plan_t plan, int problem, int *shape) {
+    if (!plan || !shape) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    *shape = plan->p.df_variant[problem];
+    return SHEN_OK;
+}
+
 const char *shen_status_string(int status) {
     switch (status) {
     case SHEN_OK: return "ok";

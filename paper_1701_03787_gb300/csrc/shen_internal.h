@@ -34,6 +34,7 @@ struct RowTables {
 //       U1 = U_{i,i+1}, U2 = U_{i,i+2}, ta, tb (tail U_ij = ta_i q_j + tb_i s_j,
 //       j >= i+3; Eq. ab), 0
 constexpr int kHelmF64 = 4;
+constexpr int kDfShapes = 2;   // row-block shapes of the single-plan float-float sweeps
 constexpr int kBiF64 = 8;
 
 struct Plan {

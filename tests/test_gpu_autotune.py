@@ -61,6 +61,39 @@ def test_batch_autotune_and_auto_precision(problem):
         assert torch.equal(after, before)
 
 
+@pytest.mark.parametrize("N", [8, 33, 130, 1024])
+@pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
+def test_every_shape_gives_the_same_bits(problem, N):
+    """Shapes 0 and 1 (rows prefetched in registers, blocks of different depth) run the same
+    arithmetic: identical bits, out of place, in place and on a mode range, and the oracle's
+    bar."""
+    import torch
+    Nx, Nz = (16, 12) if N < 1024 else (64, 64)
+    with Plan(N, Nx, Nz, 1 / 2000, 1e-4) as plan:
+        f = inputs.rhs_torch(plan.n_modes, N, seed=N)
+        outs = []
+        for shape in (0, 1):
+            plan.set_shape(problem, shape)
+            assert plan.shape(problem) == shape
+            a = plan.solve(problem, f, precision="df")
+            g = f.clone()
+            plan.solve(problem, g, u=g, precision="df")
+            h = plan.solve_modes(problem, 3, f[3:plan.n_modes - 2].contiguous(), precision="df")
+            torch.cuda.synchronize()
+            assert torch.equal(a, g)
+            assert torch.equal(a[3:plan.n_modes - 2], h)
+            outs.append(a)
+        assert torch.equal(outs[0], outs[1])
+        z2 = so.mode_z2(Nx, Nz)
+        modes = [0, 1, plan.n_modes // 2, int(z2.argmax()), plan.n_modes - 1]
+        R = on.solve_modes(problem, N, z2[modes], so.c_of(1 / 2000, 1e-4), f[modes].cpu().numpy())
+        U = outs[1][modes].cpu().numpy()
+        n = so.n_unknowns(problem, N)
+        assert max(so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))) < 1e-10
+        with pytest.raises(ShenError):
+            plan.set_shape(problem, 2)
+
+
 def test_autotune_rejects_in_place_and_bad_problem():
     with Plan(64, 8, 8, 1 / 180, 1e-3) as plan:
         f = inputs.rhs_torch(plan.n_modes, plan.N, seed=43)
