@@ -72,6 +72,13 @@ typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
 #define SHEN_PLAN_GL 2u        /* Chebyshev-Gauss-Lobatto scalar product (Sec. 2): the GL point sum,
                                   i.e. c_{N_x} = 2 in the mass matrices' highest rows (Table
                                   tab:matrices); default Chebyshev-Gauss.  Single and batched plans. */
+#define SHEN_PLAN_WALL_FIRST 4u /* fields stored wall-index-first, the paper's uhat(l, m, n) order (Sec. 2):
+                                  element (m, k) at complex index k * n_modes + m, so each Chebyshev
+                                  index k holds all modes contiguously.  Solves (SHEN_FP64, SHEN_DF,
+                                  SHEN_AUTO resolving to them, shen_solve_modes with f, u pointing at
+                                  element (mode_begin, 0) of the full field) support it; the other
+                                  entry points return SHEN_ERR_UNSUPPORTED on such a plan.  Single
+                                  plans (shen_plan_create / _z2) only. */
 
 /* Arithmetic of a solve.  All variants read and write float64 (complex128) fields and
  * use the same float64 LU factors (built once per plan); they differ in how the

@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "shensolve.h")
 
 SHEN_OK, SHEN_ERR_ARG, SHEN_ERR_ALLOC, SHEN_ERR_CUDA, SHEN_ERR_SINGULAR, SHEN_ERR_UNSUPPORTED = range(6)
 SHEN_HELMHOLTZ, SHEN_BIHARMONIC = 0, 1
-SHEN_PLAN_DF_ONLY, SHEN_PLAN_GL = 1, 2
+SHEN_PLAN_DF_ONLY, SHEN_PLAN_GL, SHEN_PLAN_WALL_FIRST = 1, 2, 4
 PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5, "auto": 6}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
@@ -139,7 +139,7 @@ class Plan:
     shape (n_modes, N) in mode-major order."""
 
     def __init__(self, N, Nx=None, Nz=None, nu=None, dt=None, Lx=None, Lz=None, z2=None, stream=None,
-                 df_only=False, gl=False):
+                 df_only=False, gl=False, wall_first=False):
         import math
         self._h = ctypes.c_void_p()
         if z2 is not None:
@@ -147,14 +147,16 @@ class Plan:
             z = np.ascontiguousarray(np.asarray(z2, dtype=np.float64))
             st = lib().shen_plan_create_z2(ctypes.byref(self._h), int(N), int(z.size),
                                            z.ctypes.data_as(ctypes.c_void_p), float(nu), float(dt),
-                                           (SHEN_PLAN_DF_ONLY if df_only else 0) | (SHEN_PLAN_GL if gl else 0),
+                                           (SHEN_PLAN_DF_ONLY if df_only else 0) | (SHEN_PLAN_GL if gl else 0)
+                                           | (SHEN_PLAN_WALL_FIRST if wall_first else 0),
                                            _stream(stream))
         else:
             Lx = 2 * math.pi if Lx is None else Lx
             Lz = math.pi if Lz is None else Lz
             st = lib().shen_plan_create(ctypes.byref(self._h), int(N), int(Nx), int(Nz), float(nu), float(dt),
                                         float(Lx), float(Lz),
-                                        (SHEN_PLAN_DF_ONLY if df_only else 0) | (SHEN_PLAN_GL if gl else 0),
+                                        (SHEN_PLAN_DF_ONLY if df_only else 0) | (SHEN_PLAN_GL if gl else 0)
+                                           | (SHEN_PLAN_WALL_FIRST if wall_first else 0),
                                         _stream(stream))
         check(st, "shen_plan_create")
         n_modes, n_classes, n = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()

@@ -133,8 +133,10 @@ __device__ inline void factor_bih_chain(const RowTables &T, int N, double z2, do
 // ------------------------------------------------------------- float64 sweeps
 
 // f, u: the column's first complex element (u may equal f).  F: the chain's factors.
+// rs: complex elements between consecutive Chebyshev indices of the column (1 for the
+// mode-major layout, the plan's mode count for the wall-index-first one).
 __device__ inline void solve_helm_fp64_chain(int N, int par, const double *f, double *u, const double *F,
-                                             double h) {
+                                             double h, long rs = 1) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
     const long base = 0;
@@ -148,7 +150,7 @@ __device__ inline void solve_helm_fp64_chain(int N, int par, const double *f, do
 #pragma unroll
         for (int q = 0; q < PB; q++) {
             const int i = min(i0 + q, rows - 1);
-            fb[q] = ld2(f, base + 2 * i + par);
+            fb[q] = ld2(f, base + (2 * i + par) * rs);
             lb[q] = F[i * kHelmF64 + 2];
         }
 #pragma unroll
@@ -156,7 +158,7 @@ __device__ inline void solve_helm_fp64_chain(int N, int par, const double *f, do
             if (i0 + q < rows) {
                 y.x = fma(-lb[q], y.x, fb[q].x);
                 y.y = fma(-lb[q], y.y, fb[q].y);
-                st2(u, base + 2 * (i0 + q) + par, y);
+                st2(u, base + (2 * (i0 + q) + par) * rs, y);
             }
         }
     }
@@ -167,7 +169,7 @@ __device__ inline void solve_helm_fp64_chain(int N, int par, const double *f, do
 #pragma unroll
         for (int q = 0; q < PB; q++) {
             const int i = max(i0 - q, 0);
-            yb[q] = ld2(u, base + 2 * i + par);
+            yb[q] = ld2(u, base + (2 * i + par) * rs);
             ab[q] = *reinterpret_cast<const double2 *>(F + i * kHelmF64);   // (1/U0, U2), 32-byte rows
         }
 #pragma unroll
@@ -180,18 +182,18 @@ __device__ inline void solve_helm_fp64_chain(int N, int par, const double *f, do
                 un.y = ab[q].x * t.y;
                 S.x += un.x;
                 S.y += un.y;
-                st2(u, base + 2 * (i0 - q) + par, un);
+                st2(u, base + (2 * (i0 - q) + par) * rs, un);
             }
         }
     }
     if (par == 0) {
-        st2(u, n, make_double2(0.0, 0.0));
-        st2(u, n + 1, make_double2(0.0, 0.0));
+        st2(u, n * rs, make_double2(0.0, 0.0));
+        st2(u, (n + 1) * rs, make_double2(0.0, 0.0));
     }
 }
 
 __device__ inline void solve_bih_fp64_chain(int N, int par, const double *f, double *u, const double *F,
-                                            const double *qk, const double *sk) {
+                                            const double *qk, const double *sk, long rs = 1) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
     const long base = 0;
@@ -203,7 +205,7 @@ __device__ inline void solve_bih_fp64_chain(int N, int par, const double *f, dou
 #pragma unroll
         for (int q = 0; q < PB; q++) {
             const int i = min(i0 + q, rows - 1);
-            fb[q] = ld2(f, base + 2 * i + par);
+            fb[q] = ld2(f, base + (2 * i + par) * rs);
             lb[q] = *reinterpret_cast<const double2 *>(F + i * kBiF64);
         }
 #pragma unroll
@@ -212,7 +214,7 @@ __device__ inline void solve_bih_fp64_chain(int N, int par, const double *f, dou
                 double2 y;
                 y.x = fma(-lb[q].y, y2.x, fma(-lb[q].x, y1.x, fb[q].x));
                 y.y = fma(-lb[q].y, y2.y, fma(-lb[q].x, y1.y, fb[q].y));
-                st2(u, base + 2 * (i0 + q) + par, y);
+                st2(u, base + (2 * (i0 + q) + par) * rs, y);
                 y2 = y1;
                 y1 = y;
             }
@@ -228,7 +230,7 @@ __device__ inline void solve_bih_fp64_chain(int N, int par, const double *f, dou
 #pragma unroll
         for (int q = 0; q < PB; q++) {
             const int i = max(i0 - q, 0);
-            yb[q] = ld2(u, base + 2 * i + par);
+            yb[q] = ld2(u, base + (2 * i + par) * rs);
             b1[q] = *reinterpret_cast<const double2 *>(F + i * kBiF64 + 2);   // 1/U0, U1
             b2[q] = *reinterpret_cast<const double2 *>(F + i * kBiF64 + 4);   // U2, ta
             tbb[q] = F[i * kBiF64 + 6];
@@ -248,7 +250,7 @@ __device__ inline void solve_bih_fp64_chain(int N, int par, const double *f, dou
                 t.x = yb[q].x - b1[q].y * u1.x - b2[q].x * u2.x - b2[q].y * Sq.x - tbb[q] * Ss.x;
                 t.y = yb[q].y - b1[q].y * u1.y - b2[q].x * u2.y - b2[q].y * Sq.y - tbb[q] * Ss.y;
                 const double2 ui = make_double2(b1[q].x * t.x, b1[q].x * t.y);
-                st2(u, base + 2 * i + par, ui);
+                st2(u, base + (2 * i + par) * rs, ui);
                 u3 = u2;
                 u2 = u1;
                 u1 = ui;
@@ -256,7 +258,7 @@ __device__ inline void solve_bih_fp64_chain(int N, int par, const double *f, dou
         }
     }
     if (par == 0)
-        for (int k = n; k < N; k++) st2(u, k, make_double2(0.0, 0.0));
+        for (int k = n; k < N; k++) st2(u, k * rs, make_double2(0.0, 0.0));
 }
 
 // --------------------------------------------------------- float-float sweeps
@@ -293,7 +295,7 @@ struct BihDF {
 
 template <int PB>
 __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
-                                             float4 *ys, int ystride) {
+                                             float4 *ys, int ystride, long rs) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
     // Forward elimination y_i = f_i - l_i y_{i-1}.  Rows are fetched PB at a time into two
@@ -308,7 +310,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = min(i0 + q, rows - 1);
-                fx[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
+                fx[q] = reinterpret_cast<const double2 *>(fcol)[(2 * i + par) * rs];
                 lx[q] = F.f[(long)i * F.s];
             }
         };
@@ -358,7 +360,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
                     un.im = df::fast_two_sum(un.im.hi, un.im.lo);
                     S.re = df::add(S.re, un.re);
                     S.im = df::add(S.im, un.im);
-                    store_f64(ucol, 2 * (i0 - q) + par, un);
+                    store_f64(ucol, (2 * (i0 - q) + par) * rs, un);
                 }
             }
         };
@@ -371,8 +373,8 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
         }
     }
     if (par == 0) {
-        reinterpret_cast<double2 *>(ucol)[n] = make_double2(0.0, 0.0);
-        reinterpret_cast<double2 *>(ucol)[n + 1] = make_double2(0.0, 0.0);
+        reinterpret_cast<double2 *>(ucol)[n * rs] = make_double2(0.0, 0.0);
+        reinterpret_cast<double2 *>(ucol)[(n + 1) * rs] = make_double2(0.0, 0.0);
     }
 }
 
@@ -397,7 +399,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 // when u == f).
 template <int PBF, int PBB, bool QSD>
 __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, double *ucol, BihDF F,
-                                            const float4 *qs, float4 *ys, int ystride) {
+                                            const float4 *qs, float4 *ys, int ystride, long rs) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
     const F2 zero{0.f, 0.f};
@@ -411,7 +413,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = min(i0 + q, rows - 1);
-                fx[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
+                fx[q] = reinterpret_cast<const double2 *>(fcol)[(2 * i + par) * rs];
                 lx[q] = F.f[(long)i * F.s];
             }
         };
@@ -485,7 +487,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
                     ui.im = df::mul(inv0, t.im);
                     ui.re = df::fast_two_sum(ui.re.hi, ui.re.lo);
                     ui.im = df::fast_two_sum(ui.im.hi, ui.im.lo);
-                    store_f64(ucol, 2 * i + par, ui);
+                    store_f64(ucol, (2 * i + par) * rs, ui);
                     u3 = u2;
                     u2 = u1;
                     u1 = ui;
@@ -501,7 +503,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
         }
     }
     if (par == 0)
-        for (int k = n; k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
+        for (int k = n; k < N; k++) reinterpret_cast<double2 *>(ucol)[k * rs] = make_double2(0.0, 0.0);
 }
 
 // Row-block shapes of the float-float chains, chosen per plan by the autotuner.  They
@@ -517,18 +519,18 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
 // 32), where each warp's spill of a row is 512 contiguous bytes.
 template <int V>
 __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
-                                           float4 *ys, int ystride) {
-    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride);
+                                           float4 *ys, int ystride, long rs = 1) {
+    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride, rs);
 }
 
 template <int V>
 __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, BihDF F,
-                                          const float4 *qs, float4 *ys, int ystride) {
+                                          const float4 *qs, float4 *ys, int ystride, long rs = 1) {
     if (V == 0)
         solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_QSD != 0>(N, par, fcol, ucol, F, qs, ys,
-                                                                                    ystride);
+                                                                                    ystride, rs);
     else
-        solve_bih_df_chain_t<4, 4, false>(N, par, fcol, ucol, F, qs, ys, ystride);
+        solve_bih_df_chain_t<4, 4, false>(N, par, fcol, ucol, F, qs, ys, ystride, rs);
 }
 
 // The output column's own rows of chain `par`, as a spill target (ystride 2).

@@ -60,18 +60,18 @@ __global__ void __launch_bounds__(128) solve_helmholtz_fp64_kernel(Plan p, const
     WorkItem w;
     if (!work_item(p, order, m0, count, w)) return;
     const double h = (p.d_class_z2[w.cls] + p.c) * kPi / 2;
-    const long off = 2 * w.col * p.N;
+    const long off = 2 * w.col * (p.wall_first ? 1L : (long)p.N), rs = p.wall_first ? p.n_modes : 1L;
     chains::solve_helm_fp64_chain(p.N, w.par, f + off, u + off,
-                                  p.d_fac_h + ((long)(w.cls * 2 + w.par) * p.rows_h) * kHelmF64, h);
+                                  p.d_fac_h + ((long)(w.cls * 2 + w.par) * p.rows_h) * kHelmF64, h, rs);
 }
 
 __global__ void __launch_bounds__(128) solve_biharmonic_fp64_kernel(Plan p, const int *order, long m0,
                                                                     long count, const double *f, double *u) {
     WorkItem w;
     if (!work_item(p, order, m0, count, w)) return;
-    const long off = 2 * w.col * p.N;
+    const long off = 2 * w.col * (p.wall_first ? 1L : (long)p.N), rs = p.wall_first ? p.n_modes : 1L;
     chains::solve_bih_fp64_chain(p.N, w.par, f + off, u + off,
-                                 p.d_fac_b + ((long)(w.cls * 2 + w.par) * p.rows_b) * kBiF64, p.tab.qk, p.tab.sk);
+                                 p.d_fac_b + ((long)(w.cls * 2 + w.par) * p.rows_b) * kBiF64, p.tab.qk, p.tab.sk, rs);
 }
 
 // ------------------------------------------------------------ RHS operators
@@ -182,7 +182,8 @@ cudaError_t launch_factor_biharmonic(const Plan &p, cudaStream_t s) {
 cudaError_t launch_solve_fp64(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                               cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    const int *order = (m0 == 0 && count == p.n_modes) ? p.d_order : nullptr;
+    // wall-index-first fields: modes in their own order, so that a warp's rows are contiguous
+    const int *order = (m0 == 0 && count == p.n_modes && !p.wall_first) ? p.d_order : nullptr;
     if (problem == SHEN_HELMHOLTZ)
         solve_helmholtz_fp64_kernel<<<blocks_for(2 * count, 128), 128, 0, s>>>(p, order, m0, count, f, u);
     else

@@ -105,7 +105,8 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
                            unsigned flags, void *stream) {
     if (!out) return SHEN_ERR_ARG;
     *out = nullptr;
-    if ((flags & ~(SHEN_PLAN_DF_ONLY | SHEN_PLAN_GL)) != 0 || N < 8 || N > 4096 || n_modes < 1 ||
+    if ((flags & ~(SHEN_PLAN_DF_ONLY | SHEN_PLAN_GL | SHEN_PLAN_WALL_FIRST)) != 0 || N < 8 || N > 4096 ||
+        n_modes < 1 ||
         n_modes > (1L << 30) || !z2)
         return SHEN_ERR_ARG;
     if (!(nu > 0) || !(dt > 0) || !std::isfinite(nu) || !std::isfinite(dt)) return SHEN_ERR_ARG;
@@ -167,6 +168,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     int stride = 0;
     const bool gl = (flags & SHEN_PLAN_GL) != 0;
     p.gl = gl;
+    p.wall_first = (flags & SHEN_PLAN_WALL_FIRST) != 0;
     build_row_tables(N, tab, tab32, stride, gl);
 
     cudaStream_t s = as_stream(stream);
@@ -260,6 +262,8 @@ bool overlap_ok(const double *a, const double *b, long n_doubles) {
 
 shen_status check_precision(const Plan &p, int problem, int precision) {
     if (p.df_only && precision != SHEN_DF)
+        return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
+    if (p.wall_first && precision != SHEN_DF && precision != SHEN_FP64)   // mixed kernels: mode-major only
         return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
     if (precision == SHEN_FP64 || precision == SHEN_DF) return SHEN_OK;
     if (precision < SHEN_FP32_R1 || precision > SHEN_DF_R2) return SHEN_ERR_ARG;
@@ -359,6 +363,7 @@ shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, c
         return precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2 ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
     if (precision == SHEN_FP64) return shen_rhs_matvec(plan, problem, x, y, beta, out, stream);
     if (!plan || !x || !out) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
@@ -373,6 +378,7 @@ shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, c
 shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, double *v, double *w, double *f,
                           int precision, void *stream) {
     if (!plan || !u || !g || !v || !w) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (precision == SHEN_AUTO) precision = SHEN_DF;
     if (precision != SHEN_DF)
         return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
@@ -398,6 +404,7 @@ shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double
                              const double *load_g, double *u_new, double *g_new, double *v, double *w,
                              int precision, void *stream) {
     if (!plan || !u_old || !g_old || !u_new || !g_new || !v || !w) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     Plan &p = plan->p;
     if (p.grid_Nz <= 0) return SHEN_ERR_UNSUPPORTED;            // the velocity step needs (m, n)
     const long nd = 2 * p.n_modes * (long)p.N;
@@ -440,6 +447,7 @@ shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double
 shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
                              double *out, void *stream) {
     if (!plan || !x || !out) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
@@ -453,6 +461,7 @@ shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, con
 
 shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *in, double *out, void *stream) {
     if (!plan || !in || !out) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (kind < SHEN_TRANSFORM_INVERSE || kind > SHEN_TRANSFORM_FORWARD) return SHEN_ERR_ARG;
     if (space < SHEN_SPACE_CHEBYSHEV || space > SHEN_SPACE_BIHARMONIC) return SHEN_ERR_ARG;
     const Plan &p = plan->p;
@@ -466,6 +475,7 @@ shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *
 shen_status shen_residual(shen_plan_t plan, int problem, const double *f, const double *u, double *rel,
                           void *stream) {
     if (!plan || !f || !u) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(f) || !aligned16(u) || (rel && (reinterpret_cast<uintptr_t>(rel) & 7u))) return SHEN_ERR_ARG;
     SHEN_CUDA_TRY(launch_residual_df(plan->p, problem, f, u, rel, as_stream(stream)));
@@ -490,6 +500,7 @@ shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, l
 shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
                             double *out, void *stream) {
     if (!plan || !x || !out) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
@@ -529,6 +540,7 @@ void shen_plan_destroy(shen_plan_t plan) {
 shen_status shen_solve_host(shen_plan_t plan, int problem, const double *f_host, double *u_host, int precision,
                             void *stream) {
     if (!plan || !f_host || !u_host) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     const long nd = 2 * plan->p.n_modes * (long)plan->p.N;
     if (!overlap_ok(f_host, u_host, nd)) return SHEN_ERR_ARG;

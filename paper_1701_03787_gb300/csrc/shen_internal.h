@@ -76,6 +76,7 @@ struct Plan {
     // runs, and the row-block shape of the float-float kernels
     bool df_only = false;                 // SHEN_PLAN_DF_ONLY: float64 factors freed after conversion
     bool gl = false;                      // SHEN_PLAN_GL: Gauss-Lobatto scalar product
+    bool wall_first = false;              // SHEN_PLAN_WALL_FIRST: fields stored Chebyshev-index-major
     // float-float kernels: fixed grid of resident blocks per [problem][shape], and the
     // per-problem spill scratch of the forward result, [warp slot][chain row][lane]
     int df_grid[2][2] = {{0, 0}, {0, 0}};
