@@ -75,7 +75,7 @@ def test_null_plan_and_pointers_rejected(L):
     z = (ctypes.c_double * 2)(0.0, -1.0)
     h = ctypes.c_void_p()
     assert L.shen_plan_create_z2(ctypes.byref(h), 64, 2, ctypes.cast(z, ctypes.c_void_p), 1e-3, 1e-3, 0, None) == 1
-    for bad_flags in (4, 5, 0x80000000):                                                  # unknown flags
+    for bad_flags in (8, 9, 0x80000000):                                                  # unknown flags
         assert L.shen_plan_create(ctypes.byref(h), 64, 32, 32, 1e-3, 1e-3, 6.28, 3.14, bad_flags, None) == 1
 
 
