@@ -59,26 +59,40 @@ def n_modes_of(w):
     return (w["Nx"] // 2 + 1) * w["Nz"]
 
 
+# CUDA sources each profiled kernel is built from (its traffic figure is valid while they hash
+# to the value stored with it)
+TRAFFIC_SOURCES = {
+    "df": ("kernels_df.cu", "chains.cuh", "df.cuh"),
+    "velocity": ("velocity.cu", "chains.cuh", "df.cuh"),
+    "matvec": ("matvec_df.cu", "df.cuh"),
+}
+
+
+def sources_sha1(names):
+    import hashlib
+    h = hashlib.sha1()
+    for name in sorted(names):
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_1701_03787_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def measured_traffic(kind, rows):
     """DRAM bytes of one launch of `kind` ("problem:precision") over `rows` complex rows,
     scaled from the per-row figure of an ncu capture (profiles/traffic.json); None if the
-    CUDA sources have changed since that capture."""
-    import glob
-    import hashlib
+    kernel's CUDA sources have changed since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         t = json.load(fh)
-    h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1701_03787_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
-    if h.hexdigest() != t.get("sources_sha1") or kind not in t.get("bytes_per_row", {}):
+    entry = t.get("bytes_per_row", {}).get(kind)
+    group = "velocity" if kind.startswith("velocity") else ("matvec" if kind.startswith("matvec") else "df")
+    hashes = t.get("sources_sha1")
+    if entry is None or not isinstance(hashes, dict) or hashes.get(group) != sources_sha1(TRAFFIC_SOURCES[group]):
         return None
-    return t["bytes_per_row"][kind] * rows
+    return entry * rows
 
 
 def gpu_pci_id(dev):

@@ -256,9 +256,24 @@ __device__ __forceinline__ CarryMap shuffle_map(const CarryMap &m, int d, int w)
 // scratch.  LP lanes per parity chain (16: lanes 0-15 / 16-31 of one warp; 32: warp 0 of
 // the caller for parity 0, warp 1 for parity 1); chunk length K, padding shift psh.
 // Table rows of the serial passes are fetched in blocks of PB ahead of their use.
+// x -> M x + c applied to the state (t0, t1)
+template <int BW>
+__device__ __forceinline__ void apply_map(const CarryMap &m, Z t0, Z t1, Z &r0, Z &r1) {
+    r0 = zfma(m.m00, t0, m.c0);
+    if (BW == 2) {
+        r0 = zfma(m.m01, t1, r0);
+        r1 = zfma(m.m11, t1, zfma(m.m10, t0, m.c1));
+    } else {
+        r1 = kZero;
+    }
+}
+
+// LP = 64: each parity chain spans two warps (chunks 0-31 and 32-63); the warps' scans are
+// joined through two float4 slots per direction in the spare tail of X and W and a group
+// barrier, so every thread of the (four-warp) group must call.
 template <int BW>
 __device__ void mass_solve(float4 *X, float4 *W, int n, int K, int psh, const float4 *T, int RM, int h, int j,
-                           int LP) {
+                           int LP, const Group &grp, int stride) {
     constexpr int PB = 4;
     const int R = (n - h + 1) / 2;
     const int s = j * K, e = min(R, s + K) - 1;
@@ -317,13 +332,31 @@ __device__ void mass_solve(float4 *X, float4 *W, int n, int K, int psh, const fl
         }
     }
     if (BW == 1) mp.m01 = mp.m10 = mp.m11 = kNil;
-    // inclusive scan of the chunk maps, chunk 0 first
-    for (int d = 1; d < LP; d <<= 1) {
-        const CarryMap o = shuffle_map<BW, true>(mp, d, LP);
-        if (j >= d) mp = compose<BW>(mp, o);
+    // inclusive scan of the chunk maps within each warp segment, chunk 0 first
+    const int SW = min(LP, 32), jw = j % SW, seg = j / SW;
+    for (int d = 1; d < SW; d <<= 1) {
+        const CarryMap o = shuffle_map<BW, true>(mp, d, SW);
+        if (jw >= d) mp = compose<BW>(mp, o);
     }
-    Z Y1 = shup(mp.c0, 1, LP), Y2 = BW == 2 ? shup(mp.c1, 1, LP) : kZero;
-    if (j == 0) Y1 = Y2 = kZero;
+    Z Y1, Y2;
+    {
+        CarryMap ex = shuffle_map<BW, true>(mp, 1, SW);         // exclusive prefix: lane jw - 1
+        if (jw == 0) ex = CarryMap{kOne, kNil, kNil, kOne, kZero, kZero};
+        Z t0 = kZero, t1 = kZero;                                // state entering the segment
+        if (LP == 64) {
+            float4 *xf = X + stride - 4 + 2 * h;
+            if (seg == 0 && jw == SW - 1) {
+                stz(xf, 0, mp.c0);
+                stz(xf, 1, mp.c1);
+            }
+            grp.sync();
+            if (seg == 1) {
+                t0 = ldz(xf, 0);
+                t1 = ldz(xf, 1);
+            }
+        }
+        apply_map<BW>(ex, t0, t1, Y1, Y2);
+    }
     if (act) {
 #pragma unroll 4
         for (int i = s; i <= e; i++) {
@@ -385,13 +418,30 @@ __device__ void mass_solve(float4 *X, float4 *W, int n, int K, int psh, const fl
         }
     }
     if (BW == 1) mq.m01 = mq.m10 = mq.m11 = kNil;
-    // inclusive scan from the last chunk down
-    for (int d = 1; d < LP; d <<= 1) {
-        const CarryMap o = shuffle_map<BW, false>(mq, d, LP);
-        if (j + d < LP) mq = compose<BW>(mq, o);
+    // inclusive scan from the last chunk down, within each warp segment
+    for (int d = 1; d < SW; d <<= 1) {
+        const CarryMap o = shuffle_map<BW, false>(mq, d, SW);
+        if (jw + d < SW) mq = compose<BW>(mq, o);
     }
-    Z X1 = shdn(mq.c0, 1, LP), X2 = BW == 2 ? shdn(mq.c1, 1, LP) : kZero;
-    if (j == LP - 1) X1 = X2 = kZero;
+    Z X1, X2;
+    {
+        CarryMap ex = shuffle_map<BW, false>(mq, 1, SW);        // exclusive: lane jw + 1
+        if (jw == SW - 1) ex = CarryMap{kOne, kNil, kNil, kOne, kZero, kZero};
+        Z t0 = kZero, t1 = kZero;
+        if (LP == 64) {
+            float4 *xb = W + stride - 4 + 2 * h;
+            if (seg == 1 && jw == 0) {
+                stz(xb, 0, mq.c0);
+                stz(xb, 1, mq.c1);
+            }
+            grp.sync();
+            if (seg == 0) {
+                t0 = ldz(xb, 0);
+                t1 = ldz(xb, 1);
+            }
+        }
+        apply_map<BW>(ex, t0, t1, X1, X2);
+    }
     if (act) {
 #pragma unroll 4
         for (int i = s; i <= e; i++) {
@@ -460,7 +510,8 @@ constexpr int nbuf_of(int kind, int space) { return (kind == 2 && space != 0) ? 
 
 // KIND: 0 inverse, 1 scalar product, 2 forward.  SPACE: 0 T_k, 1 phi_k, 2 psi_k.
 template <int KIND, int SPACE>
-__global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *in, double *out) {
+__global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
+    transform_kernel(TrArgs a, const double *in, double *out) {
     extern __shared__ float4 sm[];
     const int N = a.N, lg = a.lg, half = N >> 1;
     const float4 *tw = sm;
@@ -581,10 +632,12 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 } else {
                     for (int l = g.t; l < N; l += g.nt) stz(Bf, l + (l >> a.psh), S(l));
                     g.sync();
-                    // lanes per parity: a warp each when the group has two or more, else half a warp
-                    const int LP = g.nt >= 64 ? 32 : 16;
+                    // lanes per parity: two warps each in a four-warp group, one warp each in a
+                    // two-warp group, half a warp in a one-warp group
+                    const int LP = g.nt >= 128 ? 64 : (g.nt >= 64 ? 32 : 16);
                     if (g.t < 2 * LP)
-                        mass_solve<SPACE == 1 ? 1 : 2>(Bf, A, n, a.K, a.psh, a.mass, a.RM, g.t / LP, g.t % LP, LP);
+                        mass_solve<SPACE == 1 ? 1 : 2>(Bf, A, n, a.K, a.psh, a.mass, a.RM, g.t / LP, g.t % LP, LP, g,
+                                                       a.stride);
                     g.sync();
                     for (int k = g.t; k < N; k += g.nt)
                         y[k] = k < n ? ztof64(ldz(Bf, k + (k >> a.psh))) : make_double2(0.0, 0.0);
@@ -632,7 +685,7 @@ int chunk_len(int n, int LP) {
 // Warps per mode group of an N-mode plan (more threads per column for larger N), and the
 // mass solve's lanes per parity chain that go with it.
 int group_warps(int N) { return std::max(1, std::min(4, N / 256)); }
-int lanes_per_parity(int N) { return group_warps(N) >= 2 ? 32 : 16; }
+int lanes_per_parity(int N) { return group_warps(N) >= 4 ? 64 : (group_warps(N) >= 2 ? 32 : 16); }
 
 // Mass-solve tables of one space in the five planes mass_solve reads (B rows: diagonal,
 // +1, +2 per parity chain), from the unpivoted LU of each parity chain of B in long double
@@ -767,7 +820,8 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     for (int kind = 0; kind < 3; kind++)
         for (int space = 0; space < 3; space++) {
             const long per_group = (long)nbuf_of(kind, space) * stride * sizeof(float4);
-            const int groups = (int)std::min<long>(std::min(8, 24 / G), (smem_max - fixed) / per_group);
+            const int max_threads = nbuf_of(kind, space) == 3 ? 512 : 768;   // the kernel's bound
+            const int groups = (int)std::min<long>(std::min(8, max_threads / (32 * G)), (smem_max - fixed) / per_group);
             p.tr_groups[kind][space] = 0;
             if (groups < 1) continue;
             const int smem = (int)(fixed + groups * per_group);
