@@ -270,9 +270,42 @@ def cpu_baseline(w, precision_note, seconds_target=8.0, seed=0):
         if time.perf_counter() - t0 > seconds_target or reps >= 50:
             break
     value = reps * 2 * n_sample * N / t_total
-    return {"value": value, "unit": "solves*N/s", "cores": on.max_threads(), "kind": "oracle",
+    cores = on.max_threads()
+    # the same solves on one core (a quarter of the sample, once)
+    n1 = max(64, n_sample // 4)
+    prev = on.set_threads(1)
+    try:
+        t = time.perf_counter()
+        on.solve_modes("helmholtz", N, z2[:n1], c, F[:n1])
+        on.solve_modes("biharmonic", N, z2[:n1], c, F[:n1])
+        single = 2 * n1 * N / (time.perf_counter() - t)
+    finally:
+        on.set_threads(prev)
+    return {"value": value, "unit": "solves*N/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_sample} of {z2_all.size} modes (evenly spaced), Helmholtz + biharmonic, "
-                      f"{reps} repetitions, O(N) C oracle (Sec. 4 algorithms), float64"}
+                      f"{reps} repetitions, O(N) C oracle (Sec. 4 algorithms), float64",
+            "single_core": {"value": single, "unit": "solves*N/s", "cores": 1,
+                            "sample": f"the first {n1} modes of that sample, once"}}
+
+
+def cpu_transforms(N, n_cols=256, seed=0):
+    """The transforms oracle (oracle/transforms.py: dense basis matrices at the Gauss points,
+    numpy / BLAS on the host cores) on `n_cols` columns of N: complex points per second of the
+    inverse transform and of the scalar products in the Dirichlet space."""
+    from oracle import transforms as tr
+    from paper_1701_03787_gb300 import inputs
+    C = inputs.rhs_numpy(n_cols, N, seed)
+    C[:, N - 2:] = 0
+    tr.inverse("dirichlet", C[:2])                                      # warm (basis matrices)
+    tr.scalar("dirichlet", C[:2])
+    out = {}
+    for kind, fn in (("inverse_dirichlet", tr.inverse), ("scalar_dirichlet", tr.scalar)):
+        t = time.perf_counter()
+        fn("dirichlet", C)
+        out[kind] = {"points_per_s": n_cols * N / (time.perf_counter() - t)}
+    out["sample"] = f"{n_cols} columns of N = {N}, dense float64 matrices (O(N^2) per column), numpy BLAS"
+    out["cores"] = len(os.sched_getaffinity(0))
+    return out
 
 
 def cpu_baseline_batch(w, seconds_target=8.0, seed=0):
@@ -593,6 +626,8 @@ def main():
                     mt = float(np.mean([ev_t[s].elapsed_time(ev_t[s + 1]) for s in range(5)]))
                     trs[f"{kind}_{space}"] = {"ms": mt, "points_per_s": rows / (mt * 1e-3),
                                               "frac_hbm": rows * 32 / (mt * 1e-3) / 1e9 / pk}
+            if rank == 0 and not args.no_cpu:
+                trs["cpu_oracle"] = cpu_transforms(N)
             mv["transforms"] = trs
             del tr_out
     ms, = max_over_ranks([ms], pg, "cuda")

@@ -39,6 +39,8 @@ def lib():
         _lib.on_biharmonic_solve_dense_lu.argtypes = [i, d, d, P, P, P]
         _lib.on_helmholtz_solve_modes.argtypes = [i, l, P, P, P]
         _lib.on_biharmonic_solve_modes.argtypes = [i, l, P, P, P, P]
+        _lib.on_set_threads.argtypes = [i]
+        _lib.on_set_threads.restype = None
         for f in ("on_helmholtz_solve", "on_biharmonic_solve", "on_biharmonic_solve_dense_lu",
                   "on_helmholtz_solve_modes", "on_biharmonic_solve_modes", "on_max_threads"):
             getattr(_lib, f).restype = ctypes.c_int
@@ -51,6 +53,13 @@ def _ptr(a):
 
 def max_threads():
     return int(lib().on_max_threads())
+
+
+def set_threads(n):
+    """Threads of the mode batches (OpenMP); returns the previous count."""
+    prev = max_threads()
+    lib().on_set_threads(int(n))
+    return prev
 
 
 def solve_modes(problem, N, z2, c, F):

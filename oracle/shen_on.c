@@ -288,6 +288,16 @@ int on_max_threads(void)
 #endif
 }
 
+/* Thread count of the mode batches below (timing the baseline on one core). */
+void on_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* f, u: n_modes columns of N complex (2N doubles) each; coef per mode. */
 int on_helmholtz_solve_modes(int N, long n_modes, const double *alpha, const double *f, double *u)
 {
