@@ -217,8 +217,9 @@ shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, do
 /* ---- Wall-normal transforms (Sec. 2, Eqs. ifft, sst1, sst2, fstB; Algorithms fst, ifst) ----
  *
  * For every mode column of the plan, between the values at the N Chebyshev-Gauss points
- * x_i = cos((2i+1) pi / (2N)), i = 0 .. N-1 (weights pi / N), and the coefficients of one
- * of three spaces:
+ * x_i = cos((2i+1) pi / (2N)), i = 0 .. N-1 (weights pi / N) -- or, for SHEN_PLAN_GL plans,
+ * the N Chebyshev-Gauss-Lobatto points x_i = cos(i pi / (N-1)) (weights pi / (N-1), half
+ * at the two ends) -- and the coefficients of one of three spaces:
  *   SHEN_SPACE_CHEBYSHEV   T_k, k = 0 .. N-1                              (Eq. Tk)
  *   SHEN_SPACE_DIRICHLET   phi_k = T_k - T_{k+2}, k = 0 .. N-3            (Eq. phiD)
  *   SHEN_SPACE_BIHARMONIC  psi_k = T_k - 2(k+2)/(k+3) T_{k+2} + (k+1)/(k+3) T_{k+4},
@@ -231,18 +232,20 @@ shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, do
  *   SHEN_TRANSFORM_FORWARD  out = B^{-1} (u, phi)_sigma with the space's mass matrix B
  *                           (Eqs. sst2, fstB; Table tab:matrices), the sigma-orthogonal
  *                           projection of u on the space (entries beyond written 0)
- * Each cosine sum is one complex FFT of length N per column (Makhoul's reordering), run
- * in float-float arithmetic (about 48 significant bits) in shared memory; the mass
+ * Each cosine sum is one complex FFT per column, of length N on Gauss points (Makhoul's
+ * reordering, DCT-II / DCT-III) or 2 (N-1) on Gauss-Lobatto points (the even extension,
+ * DCT-I), run in float-float arithmetic (about 48 significant bits) in shared memory; the mass
  * solves use the float64 LU of B (the same for every mode) as per-N tables.  Relative
  * errors are of order 1e-14 for the inverse and scalar transforms; the forward transform
  * adds the conditioning of B (about 1e9 for the biharmonic B at N = 1024, so inputs far
  * from the space lose digits there, as a float64 solve of the same system does).
  *
  * in, out: DEVICE fields of n_modes * N complex values, mode-major like the solves'
- * (in == out allowed; other overlap SHEN_ERR_ARG).  Plans with N a power of two on
- * Gauss points only: other plans (Gauss-Lobatto, N not a power of two) return
- * SHEN_ERR_UNSUPPORTED, and so does a (kind, space) whose shared-memory buffers do not fit
- * one block (on GB300: the forward transform in phi or psi at N = 4096).  Asynchronous
+ * (in == out allowed; other overlap SHEN_ERR_ARG).  N must be a power of two on Gauss
+ * points and one more than a power of two on Gauss-Lobatto points (N - 1 intervals); other
+ * plans, and wall-index-first plans, return SHEN_ERR_UNSUPPORTED, as does a (kind, space)
+ * whose shared-memory buffers do not fit one block (on GB300: the forward transform in phi
+ * or psi at N = 4096, and at N = 2049 on Gauss-Lobatto points).  Asynchronous
  * on `stream`; no scratch memory: calls on one plan may overlap.  Each column is staged
  * in shared memory by a bulk asynchronous copy; a copy that does not complete within a
  * bounded wait stops the kernel and is reported by shen_plan_check as SHEN_ERR_CUDA. */

@@ -489,7 +489,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 struct TrArgs {
-    int N, lg;
+    int N, lg;               // Chebyshev modes; log2 of the FFT length (N, or 2 (N - 1) on Gauss-Lobatto points)
     int G, n_groups;         // warps per mode group, groups per block
     long n_modes;
     int stride;              // float4 per buffer
@@ -508,12 +508,13 @@ struct TrArgs {
 // issued as soon as R is free, so it overlaps the current mode's FFT.
 constexpr int nbuf_of(int kind, int space) { return (kind == 2 && space != 0) ? 3 : 2; }
 
-// KIND: 0 inverse, 1 scalar product, 2 forward.  SPACE: 0 T_k, 1 phi_k, 2 psi_k.
-template <int KIND, int SPACE>
+// KIND: 0 inverse, 1 scalar product, 2 forward.  SPACE: 0 T_k, 1 phi_k, 2 psi_k.  GL:
+// Gauss-Lobatto points (a compile-time choice, so the Gauss kernels carry none of its code).
+template <int KIND, int SPACE, bool GL>
 __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
     transform_kernel(TrArgs a, const double *in, double *out) {
     extern __shared__ float4 sm[];
-    const int N = a.N, lg = a.lg, half = N >> 1;
+    const int N = a.N, lg = a.lg, half = N >> 1, M = N - 1;
     const float4 *tw = sm;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + a.n_tw);
     for (int t = threadIdx.x; t < a.n_tw; t += blockDim.x) sm[t] = __ldg(a.tw + t);
@@ -571,6 +572,25 @@ __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
                 }
                 return t;
             };
+            if (GL) {
+                // Gauss-Lobatto points x_i = cos(i pi / M): u_i = sum_k t_k cos(pi k i / M), a
+                // DCT-I, from the FFT Y of the even extension (t_0 .. t_M, t_{M-1} .. t_1):
+                // u_i = (Y_i + t_0 + (-1)^i t_M) / 2
+                const Z t0 = tk(0), tM = tk(M);
+                for (int k = g.t; k <= M; k += g.nt) {
+                    const Z t = tk(k);
+                    stz(A, k, t);
+                    if (k >= 1 && k < M) stz(A, 2 * M - k, t);
+                }
+                prefetch_next(next);
+                fft_dif<false>(A, lg, tw, g);
+                for (int i = g.t; i < N; i += g.nt) {
+                    const Z e = zadd(t0, (i & 1) ? Z{dneg(tM.re), dneg(tM.im)} : tM);
+                    y[i] = ztof64(zhalf(zadd(ldz(A, dpos(i, lg)), e)));
+                }
+                g.sync();
+                continue;
+            }
             // pairs (k, N-k), 0 < k <= N/2, with w = e^{-i pi k/(2N)} = mk[k]:
             //   V_k     = conj(w) (t_k - i t_{N-k}) / 2
             //   V_{N-k} = i w (t_{N-k} - i t_k) / 2      (e^{i pi (N-k)/(2N)} = i w)
@@ -590,6 +610,18 @@ __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
                 y[m] = ztof64(ldz(A, dpos(src, lg)));
             }
         } else {
+            if (GL) {
+                // Gauss-Lobatto: the even extension (u_0 .. u_M, u_{M-1} .. u_1); its FFT gives
+                // Y_k = u_0 + (-1)^k u_M + 2 sum_interior u_i cos(pi k i / M), so that
+                // (u, T_k)_sigma = pi / (2M) Y_k with the GL weights (pi / M, half at the ends)
+                for (int m = g.t; m < N; m += g.nt) {
+                    const Z v = zfromf64(xs[m]);
+                    stz(A, m, v);
+                    if (m >= 1 && m < M) stz(A, 2 * M - m, v);
+                }
+                prefetch_next(next);
+                fft_dif<false>(A, lg, tw, g);
+            } else {
             // values -> Makhoul order in A; R free for the next column
             for (int m = g.t; m < N; m += g.nt) {
                 const int dst = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
@@ -608,12 +640,20 @@ __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
                 stz(A, pk, zhalf(zadd(P, Q)));
                 if (k != half) stz(A, pn, zhalf(zi(zsub(P, Q))));
             }
+            }
             g.sync();
             auto C = [&](int k) { return ldz(A, dpos(k, lg)); };
             if (KIND == 2 && SPACE == 0) {
-                // uhat_k = C_k 2 / (N c_k): B is diagonal, pi c_k / 2
-                const float sc = 2.0f / (float)N;
-                for (int k = g.t; k < N; k += g.nt) y[k] = ztof64(zpow2(C(k), k == 0 ? 0.5f * sc : sc));
+                // uhat_k = S_k / (pi c_k / 2): Gauss: C_k 2 / (N c_k) (c_0 = 2);
+                // Gauss-Lobatto: Y_k / (M c_k) (c_0 = c_M = 2); N, M powers of two
+                if (GL) {
+                    const float sc = 1.0f / (float)M;
+                    for (int k = g.t; k < N; k += g.nt)
+                        y[k] = ztof64(zpow2(C(k), (k == 0 || k == M) ? 0.5f * sc : sc));
+                } else {
+                    const float sc = 2.0f / (float)N;
+                    for (int k = g.t; k < N; k += g.nt) y[k] = ztof64(zpow2(C(k), k == 0 ? 0.5f * sc : sc));
+                }
             } else {
                 // scalar products S_l (Algorithm fst, forwardScalar)
                 auto S = [&](int l) -> Z {
@@ -648,18 +688,21 @@ __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
     }
 }
 
-template <int KIND, int SPACE>
+template <int KIND, int SPACE, bool GL>
 const void *kernel_ptr() {
-    return reinterpret_cast<const void *>(&transform_kernel<KIND, SPACE>);
+    return reinterpret_cast<const void *>(&transform_kernel<KIND, SPACE, GL>);
 }
 
-const void *kernel_of(int kind, int space) {
-    static const void *const k[3][3] = {
-        {kernel_ptr<0, 0>(), kernel_ptr<0, 1>(), kernel_ptr<0, 2>()},
-        {kernel_ptr<1, 0>(), kernel_ptr<1, 1>(), kernel_ptr<1, 2>()},
-        {kernel_ptr<2, 0>(), kernel_ptr<2, 1>(), kernel_ptr<2, 2>()},
+const void *kernel_of(int kind, int space, bool gl) {
+    static const void *const k[2][3][3] = {
+        {{kernel_ptr<0, 0, false>(), kernel_ptr<0, 1, false>(), kernel_ptr<0, 2, false>()},
+         {kernel_ptr<1, 0, false>(), kernel_ptr<1, 1, false>(), kernel_ptr<1, 2, false>()},
+         {kernel_ptr<2, 0, false>(), kernel_ptr<2, 1, false>(), kernel_ptr<2, 2, false>()}},
+        {{kernel_ptr<0, 0, true>(), kernel_ptr<0, 1, true>(), kernel_ptr<0, 2, true>()},
+         {kernel_ptr<1, 0, true>(), kernel_ptr<1, 1, true>(), kernel_ptr<1, 2, true>()},
+         {kernel_ptr<2, 0, true>(), kernel_ptr<2, 1, true>(), kernel_ptr<2, 2, true>()}},
     };
-    return k[kind][space];
+    return k[gl ? 1 : 0][kind][space];
 }
 
 inline float4 pair4(long double a, long double b) {
@@ -690,7 +733,7 @@ int lanes_per_parity(int N) { return group_warps(N) >= 4 ? 64 : (group_warps(N) 
 // Mass-solve tables of one space in the five planes mass_solve reads (B rows: diagonal,
 // +1, +2 per parity chain), from the unpivoted LU of each parity chain of B in long double
 // arithmetic, rounded to float-float pairs.
-void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T) {
+void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T, bool gl) {
     const long double pi = 3.141592653589793238462643383279502884L;
     const int n = space == 1 ? N - 2 : N - 4;
     T.assign((size_t)2 * RM * 5, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -699,12 +742,15 @@ void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T) {
         std::vector<long double> dg(R), s1(R, 0.0L), s2(R, 0.0L);
         for (int i = 0; i < R; i++) {
             const long double k = 2 * i + h, ck = (2 * i + h == 0) ? 2.0L : 1.0L;
+            // Gauss-Lobatto: c_{N-1} = 2 in the highest row (Table tab:matrices)
+            const long double ck2 = (gl && 2 * i + h + 2 == N - 1) ? 2.0L : 1.0L;
+            const long double ck4 = (gl && 2 * i + h + 4 == N - 1) ? 2.0L : 1.0L;
             if (space == 1) {
-                dg[i] = pi / 2 * (ck + 1);
+                dg[i] = pi / 2 * (ck + ck2);
                 if (i + 1 < R) s1[i] = -pi / 2;
             } else {
                 const long double r2 = (k + 2) / (k + 3), r1 = (k + 1) / (k + 3);
-                dg[i] = pi / 2 * (ck + 4 * r2 * r2 + r1 * r1);
+                dg[i] = pi / 2 * (ck + 4 * r2 * r2 + ck4 * r1 * r1);
                 if (i + 1 < R) s1[i] = -pi * (r2 + (k + 4) * (k + 1) / ((k + 5) * (k + 3)));
                 if (i + 2 < R) s2[i] = pi / 2 * r1;
             }
@@ -745,7 +791,16 @@ void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T) {
 
 }  // namespace
 
-bool transform_supported(const Plan &p) { return !p.gl && p.N >= 8 && (p.N & (p.N - 1)) == 0; }
+// Gauss points: N a power of two (FFT length N); Gauss-Lobatto points: N - 1 a power of two
+// (FFT length 2 (N - 1)).
+bool transform_supported(const Plan &p) {
+    const int L = p.gl ? p.N - 1 : p.N;
+    return p.N >= 8 && L >= 8 && (L & (L - 1)) == 0;
+}
+
+namespace {
+int fft_length(const Plan &p) { return p.gl ? 2 * (p.N - 1) : p.N; }
+}  // namespace
 
 // Number of float4 of the per-pass twiddle table: 3 Q per radix-4 pass.
 int twiddle_count(int N) {
@@ -762,12 +817,12 @@ int twiddle_count(int N) {
 //   then the mass-solve rows of phi (2 RMd 5) and of psi (2 RMb 5).
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
-    const int N = p.N, lg = ilog2(N);
+    const int N = p.N, NF = fft_length(p), lg = ilog2(NF);
     const long double pi = 3.141592653589793238462643383279502884L;
     const int LP = lanes_per_parity(N);
     const int Kd = chunk_len(N - 2, LP), Kb = chunk_len(N - 4, LP);
     const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
-    const int ntw = twiddle_count(N), nmk = N / 2 + 1;
+    const int ntw = twiddle_count(NF), nmk = N / 2 + 1;
     std::vector<float4> tab;
     tab.reserve((size_t)ntw + nmk + 2 * N);
     for (int lgL = lg, sh = 0; lgL >= 2; lgL -= 2, sh += 2) {
@@ -775,7 +830,7 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
         for (int j = 0; j < Q; j++)
             for (int m = 1; m <= 3; m++) {
                 const long t = ((long)m * j) << sh;                    // < 3N/4
-                const long double ang = -2 * pi * (long double)t / N;
+                const long double ang = -2 * pi * (long double)t / NF;
                 tab.push_back(pair4(cosl(ang), sinl(ang)));
             }
     }
@@ -791,8 +846,8 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
         tab.push_back(pair4(g1, g2));
     }
     std::vector<float4> md, mb;
-    mass_rows(N, 1, Kd, RMd, md);
-    mass_rows(N, 2, Kb, RMb, mb);
+    mass_rows(N, 1, Kd, RMd, md, p.gl);
+    mass_rows(N, 2, Kb, RMb, mb, p.gl);
     p.tr_off_mass = (int)tab.size();
     tab.insert(tab.end(), md.begin(), md.end());
     tab.insert(tab.end(), mb.begin(), mb.end());
@@ -812,7 +867,7 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
         return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int psh = std::min(ilog2(2 * Kd), ilog2(2 * Kb));
-    const int stride = N + (N >> psh) + 4;
+    const int stride = std::max(NF, N + (N >> psh)) + 4;
     p.tr_stride = stride;
     p.tr_psh = psh;
     const int G = group_warps(N);
@@ -825,7 +880,7 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
             p.tr_groups[kind][space] = 0;
             if (groups < 1) continue;
             const int smem = (int)(fixed + groups * per_group);
-            const void *k = kernel_of(kind, space);
+            const void *k = kernel_of(kind, space, p.gl);
             if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
                 return e;
             const int carve = (int)std::min<long>(100, (smem * 100L + smem_max - 1) / smem_max + 1);
@@ -851,7 +906,7 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, const double *i
     const int N = p.N;
     TrArgs a;
     a.N = N;
-    a.lg = ilog2(N);
+    a.lg = ilog2(fft_length(p));
     a.G = p.tr_G;
     a.n_groups = p.tr_groups[kind][space];
     a.n_modes = p.n_modes;
@@ -866,13 +921,13 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, const double *i
     a.coef = a.mk + (N / 2 + 1);
     const float4 *mass = p.d_tr + p.tr_off_mass;
     a.mass = space == 1 ? mass : mass + (size_t)2 * RMd * 5;
-    const double pn = kPi / N;
+    const double pn = p.gl ? kPi / (2.0 * (N - 1)) : kPi / N;   // weight of the point sum
     const float ph = (float)pn;
     a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
     a.err = p.d_err + 3;
     const dim3 grid((unsigned)p.tr_grid[kind][space]), block((unsigned)(32 * a.G * a.n_groups));
     void *args[] = {&a, &in, &out};
-    return cudaLaunchKernel(kernel_of(kind, space), grid, block, args, (size_t)p.tr_smem[kind][space], s);
+    return cudaLaunchKernel(kernel_of(kind, space, p.gl), grid, block, args, (size_t)p.tr_smem[kind][space], s);
 }
 
 }  // namespace shen

@@ -193,8 +193,50 @@ def test_unsupported_plans():
         with pytest.raises(ShenError) as e:
             plan.transform("inverse", "dirichlet", x)
         assert e.value.status == 5
-    with Plan(64, 4, 4, 1 / 180, 1e-3, gl=True) as plan:    # Gauss-Lobatto points
+    with Plan(64, 4, 4, 1 / 180, 1e-3, gl=True) as plan:    # Gauss-Lobatto points, N - 1 = 63
         x = torch.zeros((plan.n_modes, 64), dtype=torch.complex128, device="cuda")
         with pytest.raises(ShenError) as e:
             plan.transform("scalar", "chebyshev", x)
         assert e.value.status == 5
+
+
+# ---------------------------------------------------------------------------
+# Gauss-Lobatto points (N - 1 a power of two): DCT-I through the even extension
+# ---------------------------------------------------------------------------
+
+GL_N = [9, 17, 65, 129, 1025]
+
+
+@pytest.mark.parametrize("N", GL_N)
+@pytest.mark.parametrize("space", tr.SPACES)
+def test_gl_inverse_and_scalar_match_oracle(N, space):
+    with Plan(N, 4, 4, 1 / 180, 1e-3, gl=True) as plan:
+        C = inputs.rhs_numpy(plan.n_modes, N, seed=N + 13)
+        X = _values(plan.n_modes, N, seed=N + 14)
+        U = _run(plan, "inverse", space, C)
+        S = _run(plan, "scalar", space, X)
+    Cs = C.copy()
+    Cs[:, tr.dim(space, N):] = 0
+    Uref = tr.inverse_ref(space, Cs, gl=True)
+    Sref = tr.scalar_ref(space, X, gl=True)
+    for m in range(C.shape[0]):
+        assert np.abs(U[m] - Uref[m]).max() <= _bound(N - 1, Cs[m], weight=WEIGHT[space]), m
+        # GL weights pi / (N - 1), half at the ends
+        assert np.abs(S[m] - Sref[m]).max() <= _bound(N - 1, X[m], scale=np.pi / (N - 1), weight=WEIGHT[space]), m
+        assert np.all(S[m, tr.dim(space, N):] == 0)
+
+
+@pytest.mark.parametrize("N", [9, 65, 257, 1025])
+@pytest.mark.parametrize("space", tr.SPACES)
+def test_gl_forward_matches_refined_projection(N, space):
+    with Plan(N, 4, 4, 1 / 180, 1e-3, gl=True) as plan:
+        X = _values(plan.n_modes, N, seed=N + 15)
+        Uh = _run(plan, "forward", space, X)
+        C = inputs.rhs_numpy(plan.n_modes, N, seed=N + 16)
+        C[:, tr.dim(space, N):] = 0
+        V = tr.inverse_ref(space, C, gl=True)
+        Ch = _run(plan, "forward", space, V)
+    e, tol = _f64_factor_bound(N - 1, Uh, tr.forward_ref(space, X, gl=True), tr.forward(space, X, gl=True))
+    assert np.all(e <= tol), (e.max(), tol.min())
+    e, tol = _f64_factor_bound(N - 1, Ch, C, tr.forward(space, V, gl=True))
+    assert np.all(e <= tol), (e.max(), tol.min())
