@@ -300,6 +300,26 @@ shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, l
 shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, double *u, int *chosen,
                                float *ms, void *stream);
 
+/* Iterative refinement over float32 sweeps, the precision pattern of the workload this
+ * library serves (Sec. 4's algorithms in float32, the residual in higher precision):
+ *   u = H^-1 f                      float32 forward elimination and back substitution,
+ *                                   the float64 LU factors rounded to float32
+ *   repeat `steps` times (0, 1 or 2):
+ *     work = f - H u                residual in float64 (residual = SHEN_FP64) or in
+ *                                   float-float (SHEN_DF), through the operators of
+ *                                   shen_rhs_matvec with c -> -c (H_h = -R_h(-c),
+ *                                   H_b = R_b(-c))
+ *     u += H^-1 work                float32 sweeps, the sum in float64
+ * for every mode of the plan, problem SHEN_HELMHOLTZ or SHEN_BIHARMONIC.  f, u, work:
+ * DEVICE fields of the plan; work is the caller's scratch (overwritten); none of the three
+ * may overlap another (SHEN_ERR_ARG).  Uses the problem's float-float scratch like
+ * SHEN_DF solves (the same concurrency rule).  Measured accuracy against the oracle and
+ * time are in the library's tests and benchmark: on GB300 one float64 or float-float
+ * pass costs more than the float32 sweep it corrects, so SHEN_DF is the faster path at
+ * the same accuracy.  Mode-major plans only. */
+shen_status shen_solve_refine(shen_plan_t plan, int problem, const double *f, double *u, double *work, int steps,
+                              int residual, void *stream);
+
 /* Row-block shape of the plan's float-float sweeps for `problem` (the choice
  * shen_plan_autotune makes; every shape gives the same bits):
  *   0  rows prefetched in registers, 4 (biharmonic) / 8 (Helmholtz) per block, two blocks in

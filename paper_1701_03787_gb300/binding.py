@@ -50,6 +50,7 @@ def lib():
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_residual": ([P, I, P, P, P, P], I),
         "shen_transform": ([P, I, I, P, P, P], I),
+        "shen_solve_refine": ([P, I, P, P, P, I, I, P], I),
         "shen_plan_set_shape": ([P, I, I], I),
         "shen_plan_get_shape": ([P, I, P], I),
         "shen_velocity": ([P, P, P, P, P, P, I, P], I),
@@ -314,6 +315,19 @@ class Plan:
         check(lib().shen_velocity(self._h, _ptr(u), _ptr(g), _ptr(v), _ptr(w), _ptr(f), _prec(precision),
                                   _stream(stream)), "shen_velocity")
         return v, w
+
+    def solve_refine(self, problem, f, u=None, work=None, steps=1, residual="fp64", stream=None):
+        """Float32 sweeps plus `steps` refinement steps with a float64 ("fp64") or float-float
+        ("df") residual (shen_solve_refine); returns u."""
+        import torch
+        _field_ok(f, self.n_modes, self.N, "f")
+        u = torch.empty_like(f) if u is None else u
+        work = torch.empty_like(f) if work is None else work
+        _field_ok(u, self.n_modes, self.N, "u")
+        _field_ok(work, self.n_modes, self.N, "work")
+        check(lib().shen_solve_refine(self._h, _problem(problem), _ptr(f), _ptr(u), _ptr(work), int(steps),
+                                      _prec(residual), _stream(stream)), "shen_solve_refine")
+        return u
 
     def set_shape(self, problem, shape):
         """Row-block shape (0, 1, 2) of the float-float sweeps of `problem` (same bits)."""

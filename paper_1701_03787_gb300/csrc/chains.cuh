@@ -506,6 +506,141 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
         for (int k = n; k < N; k++) reinterpret_cast<double2 *>(ucol)[k * rs] = make_double2(0.0, 0.0);
 }
 
+// ------------------------------------------------------------ float32 sweeps
+
+// The paper's sweeps in float32 (the first and the correction solves of iterative
+// refinement): the factors are the hi parts of the float-float streams (the float64
+// factors rounded to float32), the right-hand side is rounded to float32, y is spilled
+// as float2 (.x, .y of the float4 scratch).  ACC: the result is added to the float64
+// column u (u += d, one float64 addition per value) instead of stored.
+__device__ __forceinline__ void put_f32(double *ucol, long idx, float2 v, bool acc) {
+    double2 *p = reinterpret_cast<double2 *>(ucol) + idx;
+    double2 o = make_double2(df::f32_to_f64_bits(v.x), df::f32_to_f64_bits(v.y));
+    if (acc) {
+        const double2 a = *p;
+        o.x = __dadd_rn(a.x, o.x);
+        o.y = __dadd_rn(a.y, o.y);
+    }
+    *p = o;
+}
+
+template <bool ACC>
+__device__ inline void solve_helm_f32_chain(int N, int par, const double *fcol, double *ucol, HelmDF F, float h,
+                                            float4 *ys, int ystride) {
+    constexpr int PB = 8;
+    const int n = N - 2;
+    const int rows = (n - par + 1) / 2;
+    float2 y = make_float2(0.f, 0.f);
+    for (int i0 = 0; i0 < rows; i0 += PB) {
+        double2 fb[PB];
+        float lb[PB];
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = min(i0 + q, rows - 1);
+            fb[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
+            lb[q] = F.f[(long)i * F.s].x;
+        }
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            if (i0 + q < rows) {
+                y.x = fmaf(-lb[q], y.x, df::hi_f64(fb[q].x));
+                y.y = fmaf(-lb[q], y.y, df::hi_f64(fb[q].y));
+                ys[(long)(i0 + q) * ystride] = make_float4(y.x, y.y, 0.f, 0.f);
+            }
+        }
+    }
+    float2 un = make_float2(0.f, 0.f), S = un;
+    for (int i0 = rows - 1; i0 >= 0; i0 -= PB) {
+        float4 yb[PB], ab[PB];
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = max(i0 - q, 0);
+            yb[q] = ys[(long)i * ystride];
+            ab[q] = F.b[(long)i * F.s];                     // (1/U0, U2) as (hi, lo) pairs
+        }
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            if (i0 - q >= 0) {
+                const float inv0 = ab[q].x, U2 = ab[q].z;
+                un.x = inv0 * fmaf(-U2, S.x, fmaf(h, un.x, yb[q].x));
+                un.y = inv0 * fmaf(-U2, S.y, fmaf(h, un.y, yb[q].y));
+                S.x += un.x;
+                S.y += un.y;
+                put_f32(ucol, 2 * (i0 - q) + par, un, ACC);
+            }
+        }
+    }
+    if (par == 0 && !ACC) {
+        reinterpret_cast<double2 *>(ucol)[n] = make_double2(0.0, 0.0);
+        reinterpret_cast<double2 *>(ucol)[n + 1] = make_double2(0.0, 0.0);
+    }
+}
+
+template <bool ACC>
+__device__ inline void solve_bih_f32_chain(int N, int par, const double *fcol, double *ucol, BihDF F,
+                                           const float4 *qs, float4 *ys, int ystride) {
+    constexpr int PB = 4;
+    const int n = N - 4;
+    const int rows = (n - par + 1) / 2;
+    float2 y1 = make_float2(0.f, 0.f), y2 = y1;
+    for (int i0 = 0; i0 < rows; i0 += PB) {
+        double2 fb[PB];
+        float4 lb[PB];
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = min(i0 + q, rows - 1);
+            fb[q] = reinterpret_cast<const double2 *>(fcol)[2 * i + par];
+            lb[q] = F.f[(long)i * F.s];                     // (L1, L2) as (hi, lo) pairs
+        }
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            if (i0 + q < rows) {
+                float2 y;
+                y.x = fmaf(-lb[q].x, y1.x, fmaf(-lb[q].z, y2.x, df::hi_f64(fb[q].x)));
+                y.y = fmaf(-lb[q].x, y1.y, fmaf(-lb[q].z, y2.y, df::hi_f64(fb[q].y)));
+                ys[(long)(i0 + q) * ystride] = make_float4(y.x, y.y, 0.f, 0.f);
+                y2 = y1;
+                y1 = y;
+            }
+        }
+    }
+    float2 u1 = make_float2(0.f, 0.f), u2 = u1, u3 = u1, Sq = u1, Ss = u1;
+    for (int i0 = rows - 1; i0 >= 0; i0 -= PB) {
+        float4 yb[PB], b0[PB], b1[PB];
+        float b2[PB];
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = max(i0 - q, 0);
+            const long r = (long)i * F.s;
+            yb[q] = ys[(long)i * ystride];
+            b0[q] = F.b0[r];                                // (1/U0, U1)
+            b1[q] = F.b1[r];                                // (U2, ta)
+            b2[q] = F.b2[r].x;                              // tb
+        }
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = i0 - q;
+            if (i >= 0) {
+                if (i + 3 < rows) {
+                    const float4 qv = __ldg(qs + 2 * i + par + 6);
+                    Sq.x = fmaf(qv.x, u3.x, Sq.x); Sq.y = fmaf(qv.x, u3.y, Sq.y);
+                    Ss.x = fmaf(qv.z, u3.x, Ss.x); Ss.y = fmaf(qv.z, u3.y, Ss.y);
+                }
+                const float inv0 = b0[q].x, U1 = b0[q].z, U2 = b1[q].x, ta = b1[q].z, tb = b2[q];
+                float2 ui;
+                ui.x = inv0 * fmaf(-U1, u1.x, fmaf(-U2, u2.x, fmaf(-tb, Ss.x, fmaf(-ta, Sq.x, yb[q].x))));
+                ui.y = inv0 * fmaf(-U1, u1.y, fmaf(-U2, u2.y, fmaf(-tb, Ss.y, fmaf(-ta, Sq.y, yb[q].y))));
+                put_f32(ucol, 2 * i + par, ui, ACC);
+                u3 = u2;
+                u2 = u1;
+                u1 = ui;
+            }
+        }
+    }
+    if (par == 0 && !ACC)
+        for (int k = n; k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
+}
+
 // Row-block shapes of the float-float chains, chosen per plan by the autotuner.  They
 // change only how many rows each thread keeps in flight (and so its registers and the
 // warps resident per SM), never the arithmetic: every shape gives the same bits.

@@ -74,6 +74,42 @@ __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, l
     }
 }
 
+// Float32 sweeps over every mode (the solves inside shen_solve_refine): same
+// decomposition and scratch as the float-float kernels.  ACC: u += H^-1 rhs.
+template <bool ACC>
+__global__ void __launch_bounds__(128) helm_f32_kernel(Plan p, const double *rhs, double *u, float4 *scr) {
+    const int lane = threadIdx.x & 31;
+    const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
+    float4 *ys = scr + slot * (long)p.rows_h * 32 + lane;
+    for (long t0 = slot * 32; t0 < 2 * p.n_modes; t0 += nslots * 32) {
+        WorkItem w;
+        if (!work_item(p, p.d_order, 0, p.n_modes, t0 + lane, w)) continue;
+        const long off = 2 * w.col * p.N;
+        const float h = (float)((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
+        const long ch = 2L * w.cls + w.par, nch = 2 * p.n_classes;
+        chains::solve_helm_f32_chain<ACC>(p.N, w.par, rhs + off, u + off,
+                                          chains::HelmDF{p.df_hb + ch, p.df_hf + ch, nch}, h, ys, 32);
+    }
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(128) bih_f32_kernel(Plan p, const double *rhs, double *u, float4 *scr) {
+    const int lane = threadIdx.x & 31;
+    const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const long nslots = ((long)gridDim.x * blockDim.x) >> 5;
+    float4 *ys = scr + slot * (long)p.rows_b * 32 + lane;
+    for (long t0 = slot * 32; t0 < 2 * p.n_modes; t0 += nslots * 32) {
+        WorkItem w;
+        if (!work_item(p, p.d_order, 0, p.n_modes, t0 + lane, w)) continue;
+        const long off = 2 * w.col * p.N;
+        const long ch = 2L * w.cls + w.par, nch = 2 * p.n_classes;
+        chains::solve_bih_f32_chain<ACC>(p.N, w.par, rhs + off, u + off,
+                                         chains::BihDF{p.df_bf + ch, p.df_bb0 + ch, p.df_bb1 + ch, p.df_bb2 + ch, nch},
+                                         p.df_qs, ys, 32);
+    }
+}
+
 __device__ __forceinline__ float2 split2(double x) {
     const float hi = (float)x;
     return make_float2(hi, (float)(x - (double)hi));
@@ -172,6 +208,20 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_solve_f32(const Plan &p, int problem, bool acc, const double *rhs, double *u, cudaStream_t s) {
+    if (p.n_modes <= 0) return cudaSuccess;
+    const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
+    const unsigned g = (unsigned)std::max(1, p.f32_grid[pb]);
+    if (problem == SHEN_HELMHOLTZ) {
+        if (acc) helm_f32_kernel<true><<<g, 128, 0, s>>>(p, rhs, u, p.d_ys[0]);
+        else helm_f32_kernel<false><<<g, 128, 0, s>>>(p, rhs, u, p.d_ys[0]);
+    } else {
+        if (acc) bih_f32_kernel<true><<<g, 128, 0, s>>>(p, rhs, u, p.d_ys[1]);
+        else bih_f32_kernel<false><<<g, 128, 0, s>>>(p, rhs, u, p.d_ys[1]);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t df_setup(Plan &p, long long &bytes) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -189,6 +239,14 @@ cudaError_t df_setup(Plan &p, long long &bytes) {
             if (e != cudaSuccess) return e;
             p.df_grid[pb][v] = std::min(std::max(1, per_sm) * sms, needed);
             most = std::max(most, p.df_grid[pb][v]);
+        }
+        // float32 sweeps (shen_solve_refine): their own residency, within the scratch
+        {
+            const void *kf = pb == 0 ? (const void *)helm_f32_kernel<true> : (const void *)bih_f32_kernel<true>;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 128, 0);
+            if (e != cudaSuccess) return e;
+            p.f32_grid[pb] = std::max(1, std::min(std::min(std::max(1, per_sm) * sms, needed), most));
         }
         const size_t n = (size_t)most * 4 * (pb == 0 ? p.rows_h : p.rows_b) * 32;   // float4
         bytes += (long long)(n * sizeof(float4));

@@ -615,6 +615,39 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
     return SHEN_OK;
 }
 
+shen_status shen_solve_refine(shen_plan_t plan, int problem, const double *f, double *u, double *work, int steps,
+                              int residual, void *stream) {
+    if (!plan || !f || !u || !work) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (steps < 0 || steps > 2) return SHEN_ERR_ARG;
+    if (residual != SHEN_FP64 && residual != SHEN_DF) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
+    for (const void *q : {(const void *)f, (const void *)u, (const void *)work})
+        if (!aligned16(q)) return SHEN_ERR_ARG;
+    const long nd = 2 * p.n_modes * (long)p.N;
+    // f is read at every step: u and work must not overlap it or each other
+    if (u == f || work == f || work == u || !overlap_ok(u, f, nd) || !overlap_ok(work, f, nd) ||
+        !overlap_ok(work, u, nd))
+        return SHEN_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    SHEN_CUDA_TRY(launch_solve_f32(p, problem, false, f, u, s));
+    // r = f - H u through the right-hand-side operators with c -> -c:
+    // H_h = -R_h(-c) and H_b = R_b(-c) (same matrices, the time-step sign flipped)
+    Plan q = p;
+    q.c = -p.c;
+    for (int step = 0; step < steps; step++) {
+        if (residual == SHEN_DF) {
+            if (problem == SHEN_HELMHOLTZ) SHEN_CUDA_TRY(launch_matvec_df(q, problem, u, f, 1.0, work, s));
+            else SHEN_CUDA_TRY(launch_matvec_neg_df(q, problem, u, f, 1.0, work, s));
+        } else {
+            SHEN_CUDA_TRY(launch_matvec_fp64(q, problem, u, f, 1.0, work, s, problem == SHEN_HELMHOLTZ ? 1.0 : -1.0));
+        }
+        SHEN_CUDA_TRY(launch_solve_f32(p, problem, true, work, u, s));
+    }
+    return SHEN_OK;
+}
+
 shen_status shen_plan_set_shape(shen_plan_t plan, int problem, int shape) {
     if (!plan) return SHEN_ERR_ARG;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;

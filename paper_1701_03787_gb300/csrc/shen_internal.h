@@ -80,6 +80,7 @@ struct Plan {
     // float-float kernels: fixed grid of resident blocks per [problem][shape], and the
     // per-problem spill scratch of the forward result, [warp slot][chain row][lane]
     int df_grid[2][2] = {{0, 0}, {0, 0}};
+    int f32_grid[2] = {0, 0};             // float32 sweeps of shen_solve_refine
     float4 *d_ys[2] = {nullptr, nullptr};
     int auto_prec[2] = {5, 5};            // SHEN_DF until tuned
     int df_variant[2] = {0, 0};
@@ -107,6 +108,8 @@ cudaError_t pack_df(Plan &p, cudaStream_t s);
 cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                             cudaStream_t s);
 cudaError_t df_setup(Plan &p, long long &bytes);   // grids and spill scratch of the float-float kernels
+cudaError_t launch_solve_f32(const Plan &p, int problem, bool acc, const double *rhs, double *u,
+                             cudaStream_t s);   // u = H^-1 rhs, or u += H^-1 rhs (acc), float32 sweeps
 
 // velocity.cu
 void build_velocity_table(int N, std::vector<float4> &T, bool gl);

@@ -1,0 +1,66 @@
+"""GPU parity of shen_solve_refine: float32 sweeps and 0, 1 or 2 steps of iterative
+refinement with a float64 or float-float residual, against the O(N) oracle.
+
+Bars (per-mode relative L2):
+  - no step: a float32-class approximation, checked loosely (<= 1e-3);
+  - each step contracts the error by the float32 solve's own accuracy until it reaches the
+    floor of the residual's arithmetic;
+  - float64 residual: one step and two steps meet the reduced-precision bar (1e-10) for
+    both problems;
+  - float-float residual: the Helmholtz problem meets 1e-10; the biharmonic operator's Q
+    tail (p_k q_j + r_k s_j) cancels between its two terms, so its float-float residual
+    is resolved to ~1e-12 of |f| (shen_residual's documented floor), which the solve
+    amplifies to ~1e-10: checked against 5e-10."""
+import numpy as np
+import pytest
+
+from oracle import on
+from oracle import solve as so
+from paper_1701_03787_gb300 import Plan, ShenError, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _errs(plan, problem, f, U, modes, Nx, Nz, N, nu, dt):
+    z2 = so.mode_z2(Nx, Nz)[modes]
+    R = on.solve_modes(problem, N, z2, so.c_of(nu, dt), f[modes].cpu().numpy())
+    n = so.n_unknowns(problem, N)
+    return np.array([so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))])
+
+
+@pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
+@pytest.mark.parametrize("residual", ["fp64", "df"])
+@pytest.mark.parametrize("N,Nx,Nz,nu,dt", [(128, 64, 64, 1 / 180, 5e-4), (1024, 256, 256, 1 / 2000, 1e-4)])
+def test_refine_steps(problem, residual, N, Nx, Nz, nu, dt):
+    import torch
+    with Plan(N, Nx, Nz, nu, dt) as plan:
+        f = inputs.rhs_torch(plan.n_modes, N, seed=N + 31)
+        z2 = so.mode_z2(Nx, Nz)
+        if N <= 128:
+            modes = list(range(plan.n_modes))
+        else:
+            modes = inputs.sample_modes(plan.n_modes, 3e-3, seed=4,
+                                        must_include=list(inputs.grid_modes(Nx, Nz).values()) + [int(z2.argmax())])
+        worst = []
+        for steps in (0, 1, 2):
+            u = plan.solve_refine(problem, f, steps=steps, residual=residual)
+            torch.cuda.synchronize()
+            U = u[modes].cpu().numpy()
+            n = so.n_unknowns(problem, N)
+            assert np.all(U[:, n:] == 0)
+            worst.append(_errs(plan, problem, f, U, modes, Nx, Nz, N, nu, dt).max())
+    assert worst[0] <= 1e-3, worst
+    assert worst[1] <= 1e-3 * worst[0], worst                       # one step contracts
+    bar = 5e-10 if (problem == "biharmonic" and residual == "df") else 1e-10
+    assert worst[1] <= bar and worst[2] <= bar, worst
+
+
+def test_refine_arguments():
+    import torch
+    with Plan(64, 8, 8, 1 / 180, 1e-3) as plan:
+        f = inputs.rhs_torch(plan.n_modes, 64, seed=1)
+        w = torch.empty_like(f)
+        for kw in ({"u": f}, {"work": f}, {"steps": 3}, {"residual": "df_r1"}):
+            with pytest.raises(ShenError) as e:
+                plan.solve_refine("biharmonic", f, **{"work": w, **kw})
+            assert e.value.status == 1
