@@ -263,6 +263,13 @@ typedef enum {
 
 shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *in, double *out, void *stream);
 
+/* The same for modes [mode_begin, mode_begin + mode_count) only: in and out point at the
+ * column of mode_begin (a shard of a larger field, as for shen_solve_modes).  The transforms
+ * do not depend on the mode, so a shard's columns are the full transform's columns bit for
+ * bit. */
+shen_status shen_transform_modes(shen_plan_t plan, int kind, int space, long mode_begin, long mode_count,
+                                 const double *in, double *out, void *stream);
+
 /* A posteriori check of a solve: for every mode, the relative residual
  * ||f - H u||_2 / ||f||_2 over the unknowns, H the Helmholtz or biharmonic system
  * matrix of the plan (Eqs. Helmholtz_matrix, Biharmonic_matrix in the scaled form of

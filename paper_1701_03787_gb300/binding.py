@@ -50,6 +50,7 @@ def lib():
         "shen_rhs_matvec_ex": ([P, I, P, P, D, P, I, P], I),
         "shen_residual": ([P, I, P, P, P, P], I),
         "shen_transform": ([P, I, I, P, P, P], I),
+        "shen_transform_modes": ([P, I, I, Lg, Lg, P, P, P], I),
         "shen_solve_refine": ([P, I, P, P, P, I, I, P], I),
         "shen_plan_set_shape": ([P, I, I], I),
         "shen_plan_get_shape": ([P, I, P], I),
@@ -351,6 +352,20 @@ class Plan:
         k = TRANSFORMS[kind] if isinstance(kind, str) else int(kind)
         sp = SPACES[space] if isinstance(space, str) else int(space)
         check(lib().shen_transform(self._h, k, sp, _ptr(x), _ptr(out), _stream(stream)), "shen_transform")
+        return out
+
+    def transform_modes(self, kind, space, mode_begin, x, out=None, stream=None):
+        """shen_transform on the modes [mode_begin, mode_begin + x.shape[0]) (a shard)."""
+        import torch
+        count = x.numel() // self.N
+        _field_ok(x, count, self.N, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        _field_ok(out, count, self.N, "out")
+        k = TRANSFORMS[kind] if isinstance(kind, str) else int(kind)
+        sp = SPACES[space] if isinstance(space, str) else int(space)
+        check(lib().shen_transform_modes(self._h, k, sp, int(mode_begin), int(count), _ptr(x), _ptr(out),
+                                         _stream(stream)), "shen_transform_modes")
         return out
 
     def residual(self, problem, f, u, rel=None, stream=None):

@@ -468,7 +468,22 @@ shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *
     if (!aligned16(in) || !aligned16(out)) return SHEN_ERR_ARG;
     if (!overlap_ok(in, out, 2 * p.n_modes * (long)p.N)) return SHEN_ERR_ARG;
     if (!transform_supported(p) || !transform_shape_ok(p, kind, space)) return SHEN_ERR_UNSUPPORTED;
-    SHEN_CUDA_TRY(launch_transform(p, kind, space, in, out, as_stream(stream)));
+    SHEN_CUDA_TRY(launch_transform(p, kind, space, p.n_modes, in, out, as_stream(stream)));
+    return SHEN_OK;
+}
+
+shen_status shen_transform_modes(shen_plan_t plan, int kind, int space, long mode_begin, long mode_count,
+                                 const double *in, double *out, void *stream) {
+    if (!plan || !in || !out) return SHEN_ERR_ARG;
+    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
+    if (kind < SHEN_TRANSFORM_INVERSE || kind > SHEN_TRANSFORM_FORWARD) return SHEN_ERR_ARG;
+    if (space < SHEN_SPACE_CHEBYSHEV || space > SHEN_SPACE_BIHARMONIC) return SHEN_ERR_ARG;
+    const Plan &p = plan->p;
+    if (mode_begin < 0 || mode_count < 0 || mode_begin + mode_count > p.n_modes) return SHEN_ERR_ARG;
+    if (!aligned16(in) || !aligned16(out)) return SHEN_ERR_ARG;
+    if (!overlap_ok(in, out, 2 * mode_count * (long)p.N)) return SHEN_ERR_ARG;
+    if (!transform_supported(p) || !transform_shape_ok(p, kind, space)) return SHEN_ERR_UNSUPPORTED;
+    SHEN_CUDA_TRY(launch_transform(p, kind, space, mode_count, in, out, as_stream(stream)));
     return SHEN_OK;
 }
 

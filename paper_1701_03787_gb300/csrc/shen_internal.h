@@ -121,7 +121,8 @@ cudaError_t velocity_setup(Plan &p, long long &bytes);   // grid and spill scrat
 bool transform_supported(const Plan &p);
 bool transform_shape_ok(const Plan &p, int kind, int space);   // the launch fits on this GPU
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s);   // tables and launch shape
-cudaError_t launch_transform(const Plan &p, int kind, int space, const double *in, double *out, cudaStream_t s);
+cudaError_t launch_transform(const Plan &p, int kind, int space, long count, const double *in, double *out,
+                             cudaStream_t s);   // count columns from in / out
 
 // matvec_df.cu
 size_t matvec_df_floats(const Plan &p);

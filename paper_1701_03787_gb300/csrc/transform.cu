@@ -901,15 +901,16 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
 
 bool transform_shape_ok(const Plan &p, int kind, int space) { return p.d_tr && p.tr_groups[kind][space] > 0; }
 
-cudaError_t launch_transform(const Plan &p, int kind, int space, const double *in, double *out, cudaStream_t s) {
-    if (p.n_modes <= 0) return cudaSuccess;
+cudaError_t launch_transform(const Plan &p, int kind, int space, long count, const double *in, double *out,
+                             cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
     const int N = p.N;
     TrArgs a;
     a.N = N;
     a.lg = ilog2(fft_length(p));
     a.G = p.tr_G;
     a.n_groups = p.tr_groups[kind][space];
-    a.n_modes = p.n_modes;
+    a.n_modes = count;
     a.stride = p.tr_stride;
     a.n_tw = p.tr_ntw;
     a.psh = p.tr_psh;
@@ -925,7 +926,9 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, const double *i
     const float ph = (float)pn;
     a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
     a.err = p.d_err + 3;
-    const dim3 grid((unsigned)p.tr_grid[kind][space]), block((unsigned)(32 * a.G * a.n_groups));
+    const long need = (count + a.n_groups - 1) / a.n_groups;
+    const dim3 grid((unsigned)std::max<long>(1, std::min<long>(p.tr_grid[kind][space], need))),
+        block((unsigned)(32 * a.G * a.n_groups));
     void *args[] = {&a, &in, &out};
     return cudaLaunchKernel(kernel_of(kind, space, p.gl), grid, block, args, (size_t)p.tr_smem[kind][space], s);
 }

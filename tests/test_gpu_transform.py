@@ -240,3 +240,20 @@ def test_gl_forward_matches_refined_projection(N, space):
     assert np.all(e <= tol), (e.max(), tol.min())
     e, tol = _f64_factor_bound(N - 1, Ch, C, tr.forward(space, V, gl=True))
     assert np.all(e <= tol), (e.max(), tol.min())
+
+
+@pytest.mark.parametrize("gl", [False, True])
+def test_transform_shards_equal_full(gl):
+    """shen_transform_modes on mode ranges (shards) gives the full transform's columns."""
+    import torch
+    N = 65 if gl else 64
+    with Plan(N, 12, 10, 1 / 180, 1e-3, gl=gl) as plan:
+        x = torch.as_tensor(_values(plan.n_modes, N, seed=77), device="cuda")
+        for kind in ("inverse", "scalar", "forward"):
+            full = plan.transform(kind, "biharmonic", x)
+            parts = [plan.transform_modes(kind, "biharmonic", a, x[a:b].contiguous())
+                     for a, b in ((0, 7), (7, 30), (30, plan.n_modes))]
+            torch.cuda.synchronize()
+            assert torch.equal(torch.cat(parts), full), kind
+        with pytest.raises(ShenError):
+            plan.transform_modes("inverse", "dirichlet", plan.n_modes - 2, x[:5].contiguous())
