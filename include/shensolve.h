@@ -109,7 +109,7 @@ typedef enum {
     SHEN_AUTO = 6
 } shen_precision;
 
-/* Create a plan for one channel: N Chebyshev modes (8 <= N <= 4096), Fourier grid
+/* Create a plan for one channel: N Chebyshev modes (8 <= N <= 8192), Fourier grid
  * Nx x Nz (even, >= 2), viscosity nu > 0, time step dt > 0, box lengths Lx, Lz > 0
  * (the paper's Re_tau = 2000 box is Lx = 2 pi, Lz = pi).  Builds the per-N tables,
  * groups modes by z2 (modes with equal z2 share one factorisation) and computes the
@@ -385,7 +385,7 @@ void shen_plan_destroy(shen_plan_t plan);
 typedef struct shen_batch_s *shen_batch_t;
 
 typedef struct {
-    int N;                /* Chebyshev modes, 8 <= N <= 4096 */
+    int N;                /* Chebyshev modes, 8 <= N <= 8192 */
     int Nx, Nz;           /* Fourier grid, even, >= 2 */
     double nu, dt;        /* viscosity and time step, > 0 */
     double Lx, Lz;        /* box lengths, > 0 */

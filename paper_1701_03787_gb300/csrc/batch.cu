@@ -225,7 +225,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
     long mode0 = 0, col0 = 0;
     for (int i = 0; i < n_inst; i++) {
         const shen_instance_desc &d = descs[i];
-        if (d.N < 8 || d.N > 4096 || d.Nx < 2 || d.Nz < 2 || (d.Nx & 1) || (d.Nz & 1)) return SHEN_ERR_ARG;
+        if (d.N < 8 || d.N > 8192 || d.Nx < 2 || d.Nz < 2 || (d.Nx & 1) || (d.Nz & 1)) return SHEN_ERR_ARG;
         if (!(d.nu > 0) || !(d.dt > 0) || !(d.Lx > 0) || !(d.Lz > 0) || !std::isfinite(d.nu) ||
             !std::isfinite(d.dt) || !std::isfinite(d.Lx) || !std::isfinite(d.Lz))
             return SHEN_ERR_ARG;

@@ -105,7 +105,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
                            unsigned flags, void *stream) {
     if (!out) return SHEN_ERR_ARG;
     *out = nullptr;
-    if ((flags & ~(SHEN_PLAN_DF_ONLY | SHEN_PLAN_GL | SHEN_PLAN_WALL_FIRST)) != 0 || N < 8 || N > 4096 ||
+    if ((flags & ~(SHEN_PLAN_DF_ONLY | SHEN_PLAN_GL | SHEN_PLAN_WALL_FIRST)) != 0 || N < 8 || N > 8192 ||
         n_modes < 1 ||
         n_modes > (1L << 30) || !z2)
         return SHEN_ERR_ARG;

@@ -40,7 +40,7 @@ def test_status_strings_and_version(L):
 
 @pytest.mark.parametrize("args", [
     (7, 32, 32, 1e-3, 1e-3),        # N below 8
-    (4097, 32, 32, 1e-3, 1e-3),     # N above 4096
+    (8193, 32, 32, 1e-3, 1e-3),     # N above 8192
     (64, 31, 32, 1e-3, 1e-3),       # odd Nx
     (64, 32, 0, 1e-3, 1e-3),        # Nz < 2
     (64, 32, 32, 0.0, 1e-3),        # nu = 0
