@@ -716,7 +716,7 @@ def main():
         stream.synchronize()
         # each step timed on its own; the median step is the figure (the host link is
         # shared with the machine's other jobs, which show up as outlying steps)
-        k = max(3, min(args.steps, 5))
+        k = max(3, min(args.steps, 9))
         ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         if pg:
             pg.barrier()
