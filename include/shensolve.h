@@ -243,9 +243,10 @@ shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, do
  * in, out: DEVICE fields of n_modes * N complex values, mode-major like the solves'
  * (in == out allowed; other overlap SHEN_ERR_ARG).  N must be a power of two on Gauss
  * points and one more than a power of two on Gauss-Lobatto points (N - 1 intervals); other
- * plans, and wall-index-first plans, return SHEN_ERR_UNSUPPORTED, as does a (kind, space)
- * whose shared-memory buffers do not fit one block (on GB300: the forward transform in phi
- * or psi at N = 4096, and at N = 2049 on Gauss-Lobatto points).  Asynchronous
+ * plans, and wall-index-first plans, return SHEN_ERR_UNSUPPORTED, as do FFT lengths whose
+ * two shared-memory buffers do not fit one block (on GB300: N = 8192, and N = 4097 on
+ * Gauss-Lobatto points).  The forward transforms in phi and psi run the scalar products and
+ * then the mass solve in place on `out` (a second kernel).  Asynchronous
  * on `stream`; no scratch memory: calls on one plan may overlap.  Each column is staged
  * in shared memory by a bulk asynchronous copy; a copy that does not complete within a
  * bounded wait stops the kernel and is reported by shen_plan_check as SHEN_ERR_CUDA. */

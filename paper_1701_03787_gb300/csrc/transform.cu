@@ -19,20 +19,23 @@
 //   DCT-III  u_n = sum_k t_k cos(pi k (2n+1) / (2N)):  V_0 = t_0,
 //            V_k = e^{i pi k/(2N)} (t_k - i t_{N-k}) / 2,  v = sum_k V_k e^{2 pi i k n/N},
 //            u_{2n} = v_n, u_{2n+1} = v_{N-1-n}.
+// On Gauss-Lobatto points (x_i = cos(i pi / M), M = N - 1) the cosine sums are DCT-I: one
+// FFT of length 2M of the even extension (x_0 .. x_M, x_{M-1} .. x_1).
 // The FFT is an in-place decimation-in-frequency radix-4 (and one radix-2) pass sequence
 // in shared memory; its output sits in digit-reversed positions, which the post-processing
-// reads through dpos().  The mass solve B uhat = S (tridiagonal per parity for phi,
-// pentadiagonal per parity for psi, the same for every mode) runs as chunked scans: 16
-// lanes per parity chain each solve a contiguous chunk with zero carries, a shuffle scan
-// composes the chunks' affine carry maps, and a fix-up adds the carried part through the
-// precomputed homogeneous solutions of each chunk (per-N tables from the float64 LU of B).
+// reads through dpos().  The forward transforms in phi and psi add the mass solve
+// B uhat = S (tridiagonal per parity for phi, pentadiagonal for psi, the same for every
+// mode) as a second kernel, one thread per parity chain in place on the output column, with
+// the LU rows of B as per-N tables.
 //
-// One warp per mode column, persistent blocks; float-float arithmetic (pairs of float32,
-// df.cuh), float64 (complex128) in and out.  Power-of-two N only.
+// One group of warps per mode column, persistent blocks; float-float arithmetic (pairs of
+// float32, df.cuh), float64 (complex128) in and out.  N a power of two (Gauss) or one more
+// than a power of two (Gauss-Lobatto).
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "chains.cuh"
 #include "df.cuh"
 #include "shen_internal.h"
 
@@ -183,275 +186,8 @@ __device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
     }
 }
 
-// ------------------------------------------------------------------ mass solve
-
-// Shuffles of float-float / complex values within segments of `w` lanes (16 or 32).
-__device__ __forceinline__ F2 shup(F2 v, int d, int w) {
-    return F2{__shfl_up_sync(0xffffffffu, v.hi, d, w), __shfl_up_sync(0xffffffffu, v.lo, d, w)};
-}
-__device__ __forceinline__ F2 shdn(F2 v, int d, int w) {
-    return F2{__shfl_down_sync(0xffffffffu, v.hi, d, w), __shfl_down_sync(0xffffffffu, v.lo, d, w)};
-}
-__device__ __forceinline__ Z shup(Z v, int d, int w) { return Z{shup(v.re, d, w), shup(v.im, d, w)}; }
-__device__ __forceinline__ Z shdn(Z v, int d, int w) { return Z{shdn(v.re, d, w), shdn(v.im, d, w)}; }
-__device__ __forceinline__ F2 dmul(F2 a, F2 b) { return nrm(df::mul(a, b)); }
-__device__ __forceinline__ F2 dfma2(F2 a, F2 b, F2 c, F2 d) {   // a b + c d
-    return df::add(df::mul(a, b), df::mul(c, d));
-}
 __device__ __forceinline__ F2 lo2(float4 v) { return F2{v.x, v.y}; }
 __device__ __forceinline__ F2 hi2(float4 v) { return F2{v.z, v.w}; }
-__device__ __forceinline__ Z znrm(Z v) { return Z{nrm(v.re), nrm(v.im)}; }
-
-// Affine carry map of a chunk on the state (s0, s1) (BW = 2) or s0 (BW = 1):
-//   state -> M state + c.
-struct CarryMap {
-    F2 m00, m01, m10, m11;
-    Z c0, c1;
-};
-
-// (M, c) o (M', c'):  x -> M (M' x + c') + c
-template <int BW>
-__device__ __forceinline__ CarryMap compose(const CarryMap &a, const CarryMap &b) {
-    CarryMap r;
-    if (BW == 1) {
-        r.m00 = dmul(a.m00, b.m00);
-        r.c0 = zfma(a.m00, b.c0, a.c0);
-        r.m01 = r.m10 = r.m11 = kNil;
-        r.c1 = kZero;
-    } else {
-        r.m00 = dfma2(a.m00, b.m00, a.m01, b.m10);
-        r.m01 = dfma2(a.m00, b.m01, a.m01, b.m11);
-        r.m10 = dfma2(a.m10, b.m00, a.m11, b.m10);
-        r.m11 = dfma2(a.m10, b.m01, a.m11, b.m11);
-        r.c0 = zfma(a.m01, b.c1, zfma(a.m00, b.c0, a.c0));
-        r.c1 = zfma(a.m11, b.c1, zfma(a.m10, b.c0, a.c1));
-    }
-    return r;
-}
-
-template <int BW, bool UP>
-__device__ __forceinline__ CarryMap shuffle_map(const CarryMap &m, int d, int w) {
-    CarryMap r;
-    auto sh = [&](F2 v) { return UP ? shup(v, d, w) : shdn(v, d, w); };
-    auto shz = [&](Z v) { return UP ? shup(v, d, w) : shdn(v, d, w); };
-    r.m00 = sh(m.m00);
-    r.c0 = shz(m.c0);
-    if (BW == 2) {
-        r.m01 = sh(m.m01); r.m10 = sh(m.m10); r.m11 = sh(m.m11); r.c1 = shz(m.c1);
-    } else {
-        r.m01 = r.m10 = r.m11 = kNil; r.c1 = kZero;
-    }
-    return r;
-}
-
-// Per-N mass-solve tables, five planes of float4 (float-float pairs), plane f, parity h,
-// row i at [(2 f + h) RM + i]:
-//   f = 0 (l1, l2)   L_{i,i-1}, L_{i,i-2} of B's LU (unit lower)
-//   f = 1 (G1, G2)   chunk-local homogeneous forward solutions for the carries
-//                    (y_{s-1}, y_{s-2}) = (1, 0), (0, 1)
-//   f = 2 (1/d, f1)  1/U_ii and U_{i,i+1} / U_ii
-//   f = 3 (f2, 0)    U_{i,i+2} / U_ii
-//   f = 4 (H1, H2)   chunk-local homogeneous backward solutions for (x_{e+1}, x_{e+2})
-// Solve B x = S for the column: S in X (padded positions), x written back to X; W is
-// scratch.  LP lanes per parity chain (16: lanes 0-15 / 16-31 of one warp; 32: warp 0 of
-// the caller for parity 0, warp 1 for parity 1); chunk length K, padding shift psh.
-// Table rows of the serial passes are fetched in blocks of PB ahead of their use.
-// x -> M x + c applied to the state (t0, t1)
-template <int BW>
-__device__ __forceinline__ void apply_map(const CarryMap &m, Z t0, Z t1, Z &r0, Z &r1) {
-    r0 = zfma(m.m00, t0, m.c0);
-    if (BW == 2) {
-        r0 = zfma(m.m01, t1, r0);
-        r1 = zfma(m.m11, t1, zfma(m.m10, t0, m.c1));
-    } else {
-        r1 = kZero;
-    }
-}
-
-// LP = 64: each parity chain spans two warps (chunks 0-31 and 32-63); the warps' scans are
-// joined through two float4 slots per direction in the spare tail of X and W and a group
-// barrier, so every thread of the (four-warp) group must call.
-template <int BW>
-__device__ void mass_solve(float4 *X, float4 *W, int n, int K, int psh, const float4 *T, int RM, int h, int j,
-                           int LP, const Group &grp, int stride) {
-    constexpr int PB = 4;
-    const int R = (n - h + 1) / 2;
-    const int s = j * K, e = min(R, s + K) - 1;
-    const bool act = s < R;
-    auto P = [&](int i) {
-        const int k = 2 * i + h;
-        return k + (k >> psh);
-    };
-    const float4 *TL = T + (long)(0 + h) * RM, *TG = T + (long)(2 + h) * RM, *TB = T + (long)(4 + h) * RM;
-    const float4 *TF = T + (long)(6 + h) * RM, *TH = T + (long)(8 + h) * RM;
-
-    // forward elimination, chunk-local with zero carries: p_i = S_i - l1 p_{i-1} - l2 p_{i-2}
-    Z p1 = kZero, p2 = kZero;
-    CarryMap mp{kOne, kNil, kNil, kOne, kZero, kZero};
-    if (act) {
-        float4 la[PB], lb[PB];
-        auto load = [&](float4 (&l)[PB], int i0) {
-#pragma unroll
-            for (int q = 0; q < PB; q++) l[q] = __ldg(TL + min(i0 + q, e));
-        };
-        auto run = [&](const float4 (&l)[PB], int i0) {
-#pragma unroll
-            for (int q = 0; q < PB; q++) {
-                const int i = i0 + q;
-                if (i <= e) {
-                    Z y = zfma(dneg(lo2(l[q])), p1, ldz(X, P(i)));
-                    if (BW == 2) y = zfma(dneg(hi2(l[q])), p2, y);
-                    y = znrm(y);
-                    stz(W, P(i), y);
-                    p2 = p1;
-                    p1 = y;
-                }
-            }
-        };
-        load(la, s);
-        for (int i0 = s; i0 <= e; i0 += 2 * PB) {
-            load(lb, i0 + PB);
-            run(la, i0);
-            load(la, i0 + 2 * PB);
-            run(lb, i0 + PB);
-        }
-        const float4 ge = __ldg(TG + e);
-        mp.m00 = lo2(ge);
-        mp.c0 = p1;
-        if (BW == 2) {
-            mp.m01 = hi2(ge);
-            if (e - 1 >= s) {
-                const float4 g1 = __ldg(TG + e - 1);
-                mp.m10 = lo2(g1);
-                mp.m11 = hi2(g1);
-                mp.c1 = p2;
-            } else {                       // one-row chunk: y_{e-1} = y_{s-1} is the carry itself
-                mp.m10 = kOne;
-                mp.m11 = kNil;
-            }
-        }
-    }
-    if (BW == 1) mp.m01 = mp.m10 = mp.m11 = kNil;
-    // inclusive scan of the chunk maps within each warp segment, chunk 0 first
-    const int SW = min(LP, 32), jw = j % SW, seg = j / SW;
-    for (int d = 1; d < SW; d <<= 1) {
-        const CarryMap o = shuffle_map<BW, true>(mp, d, SW);
-        if (jw >= d) mp = compose<BW>(mp, o);
-    }
-    Z Y1, Y2;
-    {
-        CarryMap ex = shuffle_map<BW, true>(mp, 1, SW);         // exclusive prefix: lane jw - 1
-        if (jw == 0) ex = CarryMap{kOne, kNil, kNil, kOne, kZero, kZero};
-        Z t0 = kZero, t1 = kZero;                                // state entering the segment
-        if (LP == 64) {
-            float4 *xf = X + stride - 4 + 2 * h;
-            if (seg == 0 && jw == SW - 1) {
-                stz(xf, 0, mp.c0);
-                stz(xf, 1, mp.c1);
-            }
-            grp.sync();
-            if (seg == 1) {
-                t0 = ldz(xf, 0);
-                t1 = ldz(xf, 1);
-            }
-        }
-        apply_map<BW>(ex, t0, t1, Y1, Y2);
-    }
-    if (act) {
-#pragma unroll 4
-        for (int i = s; i <= e; i++) {
-            const float4 gv = __ldg(TG + i);
-            Z y = zfma(lo2(gv), Y1, ldz(W, P(i)));
-            if (BW == 2) y = zfma(hi2(gv), Y2, y);
-            stz(W, P(i), znrm(y));
-        }
-    }
-    // back substitution, chunk-local: q_i = y_i / d_i - f1 q_{i+1} - f2 q_{i+2}
-    Z q1 = kZero, q2 = kZero;
-    CarryMap mq{kOne, kNil, kNil, kOne, kZero, kZero};
-    if (act) {
-        float4 ba[PB], bb[PB], fa[PB], fb[PB];
-        auto load = [&](float4 (&b)[PB], float4 (&f)[PB], int i0) {
-#pragma unroll
-            for (int q = 0; q < PB; q++) {
-                const int i = max(i0 - q, s);
-                b[q] = __ldg(TB + i);
-                if (BW == 2) f[q] = __ldg(TF + i);
-            }
-        };
-        auto run = [&](const float4 (&b)[PB], const float4 (&f)[PB], int i0) {
-#pragma unroll
-            for (int q = 0; q < PB; q++) {
-                const int i = i0 - q;
-                if (i >= s) {
-                    Z x = zscale(ldz(W, P(i)), lo2(b[q]));
-                    x = zfma(dneg(hi2(b[q])), q1, x);
-                    if (BW == 2) x = zfma(dneg(lo2(f[q])), q2, x);
-                    x = znrm(x);
-                    stz(W, P(i), x);
-                    q2 = q1;
-                    q1 = x;
-                }
-            }
-        };
-        load(ba, fa, e);
-        for (int i0 = e; i0 >= s; i0 -= 2 * PB) {
-            load(bb, fb, i0 - PB);
-            run(ba, fa, i0);
-            load(ba, fa, i0 - 2 * PB);
-            run(bb, fb, i0 - PB);
-        }
-        const float4 hs = __ldg(TH + s);
-        mq.m00 = lo2(hs);
-        mq.c0 = q1;
-        if (BW == 2) {
-            mq.m01 = hi2(hs);
-            if (s + 1 <= e) {
-                const float4 h1 = __ldg(TH + s + 1);
-                mq.m10 = lo2(h1);
-                mq.m11 = hi2(h1);
-                mq.c1 = q2;
-            } else {                       // one-row chunk: x_{s+1} = x_{e+1} is the carry itself
-                mq.m10 = kOne;
-                mq.m11 = kNil;
-            }
-        }
-    }
-    if (BW == 1) mq.m01 = mq.m10 = mq.m11 = kNil;
-    // inclusive scan from the last chunk down, within each warp segment
-    for (int d = 1; d < SW; d <<= 1) {
-        const CarryMap o = shuffle_map<BW, false>(mq, d, SW);
-        if (jw + d < SW) mq = compose<BW>(mq, o);
-    }
-    Z X1, X2;
-    {
-        CarryMap ex = shuffle_map<BW, false>(mq, 1, SW);        // exclusive: lane jw + 1
-        if (jw == SW - 1) ex = CarryMap{kOne, kNil, kNil, kOne, kZero, kZero};
-        Z t0 = kZero, t1 = kZero;
-        if (LP == 64) {
-            float4 *xb = W + stride - 4 + 2 * h;
-            if (seg == 1 && jw == 0) {
-                stz(xb, 0, mq.c0);
-                stz(xb, 1, mq.c1);
-            }
-            grp.sync();
-            if (seg == 0) {
-                t0 = ldz(xb, 0);
-                t1 = ldz(xb, 1);
-            }
-        }
-        apply_map<BW>(ex, t0, t1, X1, X2);
-    }
-    if (act) {
-#pragma unroll 4
-        for (int i = s; i <= e; i++) {
-            const float4 hv = __ldg(TH + i);
-            Z x = zfma(lo2(hv), X1, ldz(W, P(i)));
-            if (BW == 2) x = zfma(hi2(hv), X2, x);
-            stz(X, P(i), znrm(x));
-        }
-    }
-}
 
 // ------------------------------------------------------------------ kernel
 
@@ -494,25 +230,24 @@ struct TrArgs {
     long n_modes;
     int stride;              // float4 per buffer
     int n_tw;                // float4 of the per-pass twiddle table (copied to shared memory)
-    int K, psh, RM;          // mass solve: chunk length, padding shift, rows per parity stride
     const float4 *tw;        // per-pass twiddles
     const float4 *mk;        // e^{-i pi k/(2N)}, k = 0 .. N/2
     const float4 *coef;      // per k: (g1i_k, g2i_k), (g1_k, g2_k)
-    const float4 *mass;      // mass-solve rows of the space
     int *err;                // set to 1 if a column copy did not complete
     F2 pi_over_N;
 };
 
-// Buffers of a mode group: 2 (inverse, scalar products, forward in T_k) or 3 (forward in
-// phi, psi) of `stride` float4.  The column copy lands in R; the next mode's copy is
-// issued as soon as R is free, so it overlaps the current mode's FFT.
-constexpr int nbuf_of(int kind, int space) { return (kind == 2 && space != 0) ? 3 : 2; }
+// Two buffers of `stride` float4 per mode group, A and R (= B).  The column copy lands in
+// R; the next mode's copy is issued as soon as R is free, so it overlaps the current
+// mode's FFT.
+constexpr int kBuffers = 2;
 
-// KIND: 0 inverse, 1 scalar product, 2 forward.  SPACE: 0 T_k, 1 phi_k, 2 psi_k.  GL:
-// Gauss-Lobatto points (a compile-time choice, so the Gauss kernels carry none of its code).
+// KIND: 0 inverse, 1 scalar products, 2 forward (the T_k space only: the forward transforms
+// in phi, psi are the scalar products followed by mass_sweep_kernel).  SPACE: 0 T_k, 1 phi_k,
+// 2 psi_k.  GL: Gauss-Lobatto points (a compile-time choice, so the Gauss kernels carry none
+// of its code).
 template <int KIND, int SPACE, bool GL>
-__global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
-    transform_kernel(TrArgs a, const double *in, double *out) {
+__global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *in, double *out) {
     extern __shared__ float4 sm[];
     const int N = a.N, lg = a.lg, half = N >> 1, M = N - 1;
     const float4 *tw = sm;
@@ -520,10 +255,9 @@ __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
     for (int t = threadIdx.x; t < a.n_tw; t += blockDim.x) sm[t] = __ldg(a.tw + t);
     const int gsize = 32 * a.G, gi = threadIdx.x / gsize;
     const Group g{(int)threadIdx.x - gi * gsize, gsize, 1 + gi};
-    constexpr int NB = nbuf_of(KIND, SPACE);
-    float4 *A = sm + a.n_tw + 8 + (long)gi * NB * a.stride;
+    float4 *A = sm + a.n_tw + 8 + (long)gi * kBuffers * a.stride;
     float4 *Bf = A + a.stride;
-    float4 *R = NB == 3 ? Bf + a.stride : Bf;
+    float4 *R = Bf;
     uint64_t *bar = bars + gi;
     const int n = SPACE == 0 ? N : (SPACE == 1 ? N - 2 : N - 4);
     const long groups_total = (long)gridDim.x * a.n_groups;
@@ -667,24 +401,89 @@ __global__ void __launch_bounds__(KIND == 2 && SPACE != 0 ? 512 : 768)
                     }
                     return zscale(v, a.pi_over_N);
                 };
-                if (KIND == 1) {
-                    for (int l = g.t; l < N; l += g.nt) y[l] = ztof64(S(l));
-                } else {
-                    for (int l = g.t; l < N; l += g.nt) stz(Bf, l + (l >> a.psh), S(l));
-                    g.sync();
-                    // lanes per parity: two warps each in a four-warp group, one warp each in a
-                    // two-warp group, half a warp in a one-warp group
-                    const int LP = g.nt >= 128 ? 64 : (g.nt >= 64 ? 32 : 16);
-                    if (g.t < 2 * LP)
-                        mass_solve<SPACE == 1 ? 1 : 2>(Bf, A, n, a.K, a.psh, a.mass, a.RM, g.t / LP, g.t % LP, LP, g,
-                                                       a.stride);
-                    g.sync();
-                    for (int k = g.t; k < N; k += g.nt)
-                        y[k] = k < n ? ztof64(ldz(Bf, k + (k >> a.psh))) : make_double2(0.0, 0.0);
-                }
+                for (int l = g.t; l < N; l += g.nt) y[l] = ztof64(S(l));
             }
         }
         g.sync();
+    }
+}
+
+// Forward transform in phi / psi, second pass: B uhat = S in place on every column (S from
+// the scalar-product pass).  B is the same for every mode, so its LU rows (mass_rows: planes
+// (l1, l2), (1/d, U_{i,i+1}/d), (U_{i,i+2}/d, 0)) serve all chains from L1 / L2.
+// One thread per (mode, parity) chain, as in the solves: the forward sweep overwrites each
+// row with y (float-float, 16 bytes, in the row's own slot), the back substitution
+// overwrites it with uhat (float64); rows are fetched PB at a time ahead of their stores.
+template <int BW, int PB>
+__global__ void __launch_bounds__(128) mass_sweep_kernel(const float4 *T, int RM, int N, int n, long count,
+                                                         double *col0) {
+    using chains::CF2;
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (tid >= 2 * count) return;
+    const long mode = tid >> 1;
+    const int h = (int)(tid & 1);
+    double2 *col = reinterpret_cast<double2 *>(col0) + mode * N;
+    float4 *ys = reinterpret_cast<float4 *>(col);
+    const int R = (n - h + 1) / 2;
+    const float4 *TL = T + (long)(0 + h) * RM, *TB = T + (long)(2 + h) * RM, *TF = T + (long)(4 + h) * RM;
+    const F2 zero{0.f, 0.f};
+    CF2 y1{zero, zero}, y2 = y1;
+    for (int i0 = 0; i0 < R; i0 += PB) {
+        double2 sb[PB];
+        float4 lb[PB];
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = min(i0 + q, R - 1);
+            sb[q] = col[2 * i + h];
+            lb[q] = __ldg(TL + i);
+        }
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            if (i0 + q < R) {
+                CF2 y;
+                y.re = df::from_f64(sb[q].x);
+                y.im = df::from_f64(sb[q].y);
+                if (BW == 2) {
+                    y.re = chains::fnma(hi2(lb[q]), y2.re, y.re);
+                    y.im = chains::fnma(hi2(lb[q]), y2.im, y.im);
+                }
+                y.re = chains::fnma(lo2(lb[q]), y1.re, y.re);
+                y.im = chains::fnma(lo2(lb[q]), y1.im, y.im);
+                ys[2 * (i0 + q) + h] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
+                y2 = y1;
+                y1 = y;
+            }
+        }
+    }
+    CF2 x1{zero, zero}, x2 = x1;
+    for (int i0 = R - 1; i0 >= 0; i0 -= PB) {
+        float4 yb[PB], bb[PB], fb[PB];
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = max(i0 - q, 0);
+            yb[q] = ys[2 * i + h];
+            bb[q] = __ldg(TB + i);
+            if (BW == 2) fb[q] = __ldg(TF + i);
+        }
+#pragma unroll
+        for (int q = 0; q < PB; q++) {
+            const int i = i0 - q;
+            if (i >= 0) {
+                const CF2 yi{F2{yb[q].x, yb[q].y}, F2{yb[q].z, yb[q].w}};
+                CF2 x;
+                x.re = nrm(df::mul(lo2(bb[q]), yi.re));
+                x.im = nrm(df::mul(lo2(bb[q]), yi.im));
+                if (BW == 2) {
+                    x.re = chains::fnma(lo2(fb[q]), x2.re, x.re);
+                    x.im = chains::fnma(lo2(fb[q]), x2.im, x.im);
+                }
+                x.re = chains::fnma(hi2(bb[q]), x1.re, x.re);
+                x.im = chains::fnma(hi2(bb[q]), x1.im, x.im);
+                col[2 * i + h] = make_double2(df::to_f64(x.re), df::to_f64(x.im));
+                x2 = x1;
+                x1 = x;
+            }
+        }
     }
 }
 
@@ -697,12 +496,12 @@ const void *kernel_of(int kind, int space, bool gl) {
     static const void *const k[2][3][3] = {
         {{kernel_ptr<0, 0, false>(), kernel_ptr<0, 1, false>(), kernel_ptr<0, 2, false>()},
          {kernel_ptr<1, 0, false>(), kernel_ptr<1, 1, false>(), kernel_ptr<1, 2, false>()},
-         {kernel_ptr<2, 0, false>(), kernel_ptr<2, 1, false>(), kernel_ptr<2, 2, false>()}},
+         {kernel_ptr<2, 0, false>(), kernel_ptr<1, 1, false>(), kernel_ptr<1, 2, false>()}},
         {{kernel_ptr<0, 0, true>(), kernel_ptr<0, 1, true>(), kernel_ptr<0, 2, true>()},
          {kernel_ptr<1, 0, true>(), kernel_ptr<1, 1, true>(), kernel_ptr<1, 2, true>()},
-         {kernel_ptr<2, 0, true>(), kernel_ptr<2, 1, true>(), kernel_ptr<2, 2, true>()}},
+         {kernel_ptr<2, 0, true>(), kernel_ptr<1, 1, true>(), kernel_ptr<1, 2, true>()}},
     };
-    return k[gl ? 1 : 0][kind][space];
+    return k[gl ? 1 : 0][kind][space];   // forward phi / psi: their scalar-product kernels
 }
 
 inline float4 pair4(long double a, long double b) {
@@ -716,27 +515,18 @@ int ilog2(int v) {
     return l;
 }
 
-// Chunk length of the mass solve for n unknowns and LP lanes per parity chain: a power of
-// two >= 2 with LP chunks covering the longer parity chain.
-int chunk_len(int n, int LP) {
-    const int R0 = (n + 1) / 2;
-    int K = 2;
-    while (LP * K < R0) K <<= 1;
-    return K;
-}
-
-// Warps per mode group of an N-mode plan (more threads per column for larger N), and the
-// mass solve's lanes per parity chain that go with it.
+// Warps per mode group of an N-mode plan (more threads per column for larger N).
 int group_warps(int N) { return std::max(1, std::min(4, N / 256)); }
-int lanes_per_parity(int N) { return group_warps(N) >= 4 ? 64 : (group_warps(N) >= 2 ? 32 : 16); }
 
-// Mass-solve tables of one space in the five planes mass_solve reads (B rows: diagonal,
-// +1, +2 per parity chain), from the unpivoted LU of each parity chain of B in long double
-// arithmetic, rounded to float-float pairs.
-void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T, bool gl) {
+// Mass-solve tables of one space in the three planes mass_sweep_kernel reads (B rows:
+// diagonal, +1, +2 per parity chain), from the unpivoted LU of each parity chain of B in
+// long double arithmetic, rounded to float-float pairs: plane f, parity h, row i at
+// [(2 f + h) RM + i]:  f = 0 (l1, l2) = (L_{i,i-1}, L_{i,i-2});  f = 1 (1/d, U_{i,i+1}/d);
+// f = 2 (U_{i,i+2}/d, 0).
+void mass_rows(int N, int space, int RM, std::vector<float4> &T, bool gl) {
     const long double pi = 3.141592653589793238462643383279502884L;
     const int n = space == 1 ? N - 2 : N - 4;
-    T.assign((size_t)2 * RM * 5, make_float4(0.f, 0.f, 0.f, 0.f));
+    T.assign((size_t)2 * RM * 3, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int h = 0; h < 2; h++) {
         const int R = (n - h + 1) / 2;
         std::vector<long double> dg(R), s1(R, 0.0L), s2(R, 0.0L);
@@ -765,26 +555,10 @@ void mass_rows(int N, int space, int K, int RM, std::vector<float4> &T, bool gl)
             e2[i] = s2[i];
         }
         auto at = [&](int f, int i) -> float4 & { return T[(size_t)(2 * f + h) * RM + i]; };
-        for (int s = 0; s < R; s += K) {
-            const int e = std::min(R, s + K) - 1;
-            long double a1 = 1, a2 = 0, b1 = 0, b2 = 1;       // (G1, G2) at rows i-1, i-2
-            for (int i = s; i <= e; i++) {
-                const long double g1 = -l1[i] * a1 - l2[i] * b1, g2 = -l1[i] * a2 - l2[i] * b2;
-                at(1, i) = pair4(g1, g2);
-                b1 = a1; b2 = a2; a1 = g1; a2 = g2;
-            }
-            a1 = 1; a2 = 0; b1 = 0; b2 = 1;                    // (H1, H2) at rows i+1, i+2
-            for (int i = e; i >= s; i--) {
-                const long double f1 = e1[i] / d[i], f2 = e2[i] / d[i];
-                const long double x1 = -f1 * a1 - f2 * b1, x2 = -f1 * a2 - f2 * b2;
-                at(4, i) = pair4(x1, x2);
-                b1 = a1; b2 = a2; a1 = x1; a2 = x2;
-            }
-        }
         for (int i = 0; i < R; i++) {
             at(0, i) = pair4(l1[i], l2[i]);
-            at(2, i) = pair4(1.0L / d[i], e1[i] / d[i]);
-            at(3, i) = pair4(e2[i] / d[i], 0.0L);
+            at(1, i) = pair4(1.0L / d[i], e1[i] / d[i]);
+            at(2, i) = pair4(e2[i] / d[i], 0.0L);
         }
     }
 }
@@ -814,13 +588,11 @@ int twiddle_count(int N) {
 //   [ntw, ntw + N/2 + 1)    mk[k] = e^{-i pi k/(2N)}, k = 0 .. N/2
 //   then 2 N: per k, (2k/(k+1), (k-3)/(k-1)) (psi -> T coefficients, k >= 2 / 4) and
 //                    (2(k+2)/(k+3), (k+1)/(k+3)) (Eq. phiN weights, k < N-4)
-//   then the mass-solve rows of phi (2 RMd 5) and of psi (2 RMb 5).
+//   then the mass-solve rows of phi (2 RMd 3) and of psi (2 RMb 3).
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
     const int N = p.N, NF = fft_length(p), lg = ilog2(NF);
     const long double pi = 3.141592653589793238462643383279502884L;
-    const int LP = lanes_per_parity(N);
-    const int Kd = chunk_len(N - 2, LP), Kb = chunk_len(N - 4, LP);
     const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
     const int ntw = twiddle_count(NF), nmk = N / 2 + 1;
     std::vector<float4> tab;
@@ -846,8 +618,8 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
         tab.push_back(pair4(g1, g2));
     }
     std::vector<float4> md, mb;
-    mass_rows(N, 1, Kd, RMd, md, p.gl);
-    mass_rows(N, 2, Kb, RMb, mb, p.gl);
+    mass_rows(N, 1, RMd, md, p.gl);
+    mass_rows(N, 2, RMb, mb, p.gl);
     p.tr_off_mass = (int)tab.size();
     tab.insert(tab.end(), md.begin(), md.end());
     tab.insert(tab.end(), mb.begin(), mb.end());
@@ -866,16 +638,15 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int psh = std::min(ilog2(2 * Kd), ilog2(2 * Kb));
-    const int stride = std::max(NF, N + (N >> psh)) + 4;
+    const int stride = NF + 4;
     p.tr_stride = stride;
-    p.tr_psh = psh;
     const int G = group_warps(N);
     const long fixed = (long)(ntw + 8) * sizeof(float4);
     for (int kind = 0; kind < 3; kind++)
         for (int space = 0; space < 3; space++) {
-            const long per_group = (long)nbuf_of(kind, space) * stride * sizeof(float4);
-            const int max_threads = nbuf_of(kind, space) == 3 ? 512 : 768;   // the kernel's bound
+            if (kind == 2 && space != 0) continue;     // forward phi / psi: the scalar-product kernels
+            const long per_group = (long)kBuffers * stride * sizeof(float4);
+            const int max_threads = 768;                 // the kernel's bound
             const int groups = (int)std::min<long>(std::min(8, max_threads / (32 * G)), (smem_max - fixed) / per_group);
             p.tr_groups[kind][space] = 0;
             if (groups < 1) continue;
@@ -899,38 +670,47 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     return cudaSuccess;
 }
 
-bool transform_shape_ok(const Plan &p, int kind, int space) { return p.d_tr && p.tr_groups[kind][space] > 0; }
+bool transform_shape_ok(const Plan &p, int kind, int space) {
+    const int k = (kind == SHEN_TRANSFORM_FORWARD && space != SHEN_SPACE_CHEBYSHEV) ? SHEN_TRANSFORM_SCALAR : kind;
+    return p.d_tr && p.tr_groups[k][space] > 0;
+}
 
 cudaError_t launch_transform(const Plan &p, int kind, int space, long count, const double *in, double *out,
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int N = p.N;
+    // the forward transforms in phi, psi: the scalar products, then the mass solve in place
+    const bool mass = kind == SHEN_TRANSFORM_FORWARD && space != SHEN_SPACE_CHEBYSHEV;
+    const int k = mass ? SHEN_TRANSFORM_SCALAR : kind;
     TrArgs a;
     a.N = N;
     a.lg = ilog2(fft_length(p));
     a.G = p.tr_G;
-    a.n_groups = p.tr_groups[kind][space];
+    a.n_groups = p.tr_groups[k][space];
     a.n_modes = count;
     a.stride = p.tr_stride;
     a.n_tw = p.tr_ntw;
-    a.psh = p.tr_psh;
-    const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
-    a.K = space == 1 ? chunk_len(N - 2, lanes_per_parity(N)) : chunk_len(N - 4, lanes_per_parity(N));
-    a.RM = space == 1 ? RMd : RMb;
     a.tw = p.d_tr;
     a.mk = p.d_tr + p.tr_ntw;
     a.coef = a.mk + (N / 2 + 1);
-    const float4 *mass = p.d_tr + p.tr_off_mass;
-    a.mass = space == 1 ? mass : mass + (size_t)2 * RMd * 5;
     const double pn = p.gl ? kPi / (2.0 * (N - 1)) : kPi / N;   // weight of the point sum
     const float ph = (float)pn;
     a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
     a.err = p.d_err + 3;
     const long need = (count + a.n_groups - 1) / a.n_groups;
-    const dim3 grid((unsigned)std::max<long>(1, std::min<long>(p.tr_grid[kind][space], need))),
+    const dim3 grid((unsigned)std::max<long>(1, std::min<long>(p.tr_grid[k][space], need))),
         block((unsigned)(32 * a.G * a.n_groups));
     void *args[] = {&a, &in, &out};
-    return cudaLaunchKernel(kernel_of(kind, space, p.gl), grid, block, args, (size_t)p.tr_smem[kind][space], s);
+    cudaError_t e = cudaLaunchKernel(kernel_of(k, space, p.gl), grid, block, args, (size_t)p.tr_smem[k][space], s);
+    if (e != cudaSuccess || !mass) return e;
+    const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
+    const float4 *T = p.d_tr + p.tr_off_mass;
+    const unsigned blocks = (unsigned)((2 * count + 127) / 128);
+    if (space == SHEN_SPACE_DIRICHLET)
+        mass_sweep_kernel<1, 8><<<blocks, 128, 0, s>>>(T, RMd, N, N - 2, count, out);
+    else
+        mass_sweep_kernel<2, 4><<<blocks, 128, 0, s>>>(T + (size_t)2 * RMd * 3, RMb, N, N - 4, count, out);
+    return cudaGetLastError();
 }
 
 }  // namespace shen
