@@ -95,8 +95,6 @@ __device__ __forceinline__ Z zfromf64(double2 v) { return Z{df::from_f64(v.x), d
 __device__ __forceinline__ double2 ztof64(Z v) { return make_double2(df::to_f64(v.re), df::to_f64(v.im)); }
 
 constexpr Z kZero{F2{0.f, 0.f}, F2{0.f, 0.f}};
-constexpr F2 kOne{1.f, 0.f};
-constexpr F2 kNil{0.f, 0.f};
 
 // Position of frequency k after the in-place DIF passes (radix 4 first, then one radix 2
 // when log2 N is odd): the first pass puts k mod 4 in quarter (k mod 4), and so on, so
