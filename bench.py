@@ -770,18 +770,19 @@ def main():
         c2.record(stream)
         stream.synchronize()
         fp64_ms = {"helmholtz": a.elapsed_time(b), "biharmonic": b.elapsed_time(c2)}
-        # float32 sweeps + refinement (shen_solve_refine) for both problems: one step with a
-        # float64 residual, two with a float-float one
-        work = torch.empty_like(f_h)
-        for problem, fx, ux in (("helmholtz", f_h, u_h), ("biharmonic", f_b, u_b)):
-            for steps, resid in ((1, "fp64"), (2, "df")):
-                plan.solve_refine(problem, fx, ux, work, steps=steps, residual=resid, stream=stream)
-                a.record(stream)
-                plan.solve_refine(problem, fx, ux, work, steps=steps, residual=resid, stream=stream)
-                b.record(stream)
-                stream.synchronize()
-                fp64_ms[f"{problem}_f32_r{steps}_{resid}"] = a.elapsed_time(b)
-        del work
+        # float32 sweeps + refinement (shen_solve_refine, single-channel plans) for both
+        # problems: one step with a float64 residual, two with a float-float one
+        if not batched:
+            work = torch.empty_like(f_h)
+            for problem, fx, ux in (("helmholtz", f_h, u_h), ("biharmonic", f_b, u_b)):
+                for steps, resid in ((1, "fp64"), (2, "df")):
+                    plan.solve_refine(problem, fx, ux, work, steps=steps, residual=resid, stream=stream)
+                    a.record(stream)
+                    plan.solve_refine(problem, fx, ux, work, steps=steps, residual=resid, stream=stream)
+                    b.record(stream)
+                    stream.synchronize()
+                    fp64_ms[f"{problem}_f32_r{steps}_{resid}"] = a.elapsed_time(b)
+            del work
         # the warp-per-mode float32-sweep + one-refinement-step kernels of the Helmholtz problem
         for name in ("df_r1", "fp32_r1"):
             try:
