@@ -65,7 +65,22 @@ TRAFFIC_SOURCES = {
     "df": ("kernels_df.cu", "chains.cuh", "df.cuh"),
     "velocity": ("velocity.cu", "chains.cuh", "df.cuh"),
     "matvec": ("matvec_df.cu", "df.cuh"),
+    "transform": ("transform.cu", "df.cuh"),
 }
+
+
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def traffic_group(kind):
+    head = kind.split(":")[0]
+    if head.startswith("velocity"):
+        return "velocity"
+    if head.startswith("matvec"):
+        return "matvec"
+    if head == "transform":
+        return "transform"
+    return "df"
 
 
 def sources_sha1(names):
@@ -82,17 +97,79 @@ def measured_traffic(kind, rows):
     """DRAM bytes of one launch of `kind` ("problem:precision") over `rows` complex rows,
     scaled from the per-row figure of an ncu capture (profiles/traffic.json); None if the
     kernel's CUDA sources have changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = TRAFFIC_PATH
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         t = json.load(fh)
     entry = t.get("bytes_per_row", {}).get(kind)
-    group = "velocity" if kind.startswith("velocity") else ("matvec" if kind.startswith("matvec") else "df")
+    group = traffic_group(kind)
     hashes = t.get("sources_sha1")
     if entry is None or not isinstance(hashes, dict) or hashes.get(group) != sources_sha1(TRAFFIC_SOURCES[group]):
         return None
     return entry * rows
+
+
+# kernel name (as ncu prints it) -> traffic kinds its per-launch bytes stand for; the
+# forward transform in phi / psi is the scalar-product kernel plus one mass sweep
+TRAFFIC_KERNELS = (
+    (r"bih_df_kernel<0>", ("biharmonic:df",)),
+    (r"helm_df_kernel<0>", ("helmholtz:df",)),
+    (r"velocity_df_kernel", ("velocity:df",)),
+    (r"matvec_helmholtz_df_kernel<0>", ("matvec_helmholtz:df",)),
+    (r"matvec_biharmonic_df_kernel<0>", ("matvec_biharmonic:df",)),
+    (r"transform_kernel<0, 0, (0|false)>", ("transform:inverse_chebyshev",)),
+    (r"transform_kernel<0, 1, (0|false)>", ("transform:inverse_dirichlet",)),
+    (r"transform_kernel<0, 2, (0|false)>", ("transform:inverse_biharmonic",)),
+    (r"transform_kernel<1, 0, (0|false)>", ("transform:scalar_chebyshev",)),
+    (r"transform_kernel<1, 1, (0|false)>", ("transform:scalar_dirichlet", "transform:forward_dirichlet")),
+    (r"transform_kernel<1, 2, (0|false)>", ("transform:scalar_biharmonic", "transform:forward_biharmonic")),
+    (r"transform_kernel<2, 0, (0|false)>", ("transform:forward_chebyshev",)),
+    (r"mass_sweep_kernel<1, 8>", ("transform:forward_dirichlet",)),
+    (r"mass_sweep_kernel<2, 4>", ("transform:forward_biharmonic",)),
+)
+
+
+def write_traffic(csv_path, w):
+    """Rewrite profiles/traffic.json from an ncu CSV launch list with dram__bytes_read.sum and
+    dram__bytes_write.sum of the kernels above, taken on workload `w`: bytes per complex row
+    (averaged over the captured launches of each kernel), stamped with the current hashes
+    of each group's sources."""
+    import csv
+    import re
+    with open(csv_path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    rows = list(csv.reader(lines))
+    hdr = rows[0]
+    c_id, c_name = hdr.index("ID"), hdr.index("Kernel Name")
+    c_metric, c_val = hdr.index("Metric Name"), hdr.index("Metric Value")
+    per_launch = {}
+    for r in rows[1:]:
+        if r[c_metric] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            name, b = per_launch.get(r[c_id], (r[c_name], 0.0))
+            per_launch[r[c_id]] = (name, b + float(r[c_val].replace(",", "")))
+    n_rows = n_modes_of(w) * w["N"]
+    counts, per_kind = {}, {}
+    for pat, kinds in TRAFFIC_KERNELS:
+        launches = [b for name, b in per_launch.values() if re.search(pat, name)]
+        if launches:
+            counts[pat] = len(launches)
+            for k in kinds:
+                per_kind[k] = per_kind.get(k, 0.0) + sum(launches) / len(launches)
+    bpr = {k: round(v / n_rows, 2) for k, v in sorted(per_kind.items())}
+    out = {"note": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per complex row (n_modes * N rows) "
+                   "for one launch (the forward transform in phi / psi: its two kernels), from an ncu capture "
+                   f"on the N={w['N']}, {w['Nx']}x{w['Nz']} workload, written by bench.py --write-traffic; each "
+                   "figure is valid while its kernels' CUDA sources hash to sources_sha1[group] "
+                   "(groups and files: bench.py TRAFFIC_SOURCES)",
+           "workload": {k: w[k] for k in ("N", "Nx", "Nz")},
+           "launches": {pat: counts[pat] for pat, _ in TRAFFIC_KERNELS if counts.get(pat)},
+           "sources_sha1": {g: sources_sha1(names) for g, names in TRAFFIC_SOURCES.items()},
+           "bytes_per_row": bpr}
+    with open(TRAFFIC_PATH, "w") as fh:
+        json.dump(out, fh, indent=2)
+        fh.write("\n")
+    return out
 
 
 def gpu_pci_id(dev):
@@ -409,8 +486,13 @@ def main():
                     help="2: run the two solves concurrently on two streams")
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
                     help="replay the step as a captured CUDA graph (auto: on for the batch workload)")
+    ap.add_argument("--write-traffic", metavar="CSV",
+                    help="rewrite profiles/traffic.json from an ncu DRAM-bytes capture on --workload, then exit")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.write_traffic:
+        print(json.dumps(write_traffic(args.write_traffic, w)["bytes_per_row"]))
+        return
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -625,7 +707,8 @@ def main():
                     torch.cuda.synchronize()
                     mt = float(np.mean([ev_t[s].elapsed_time(ev_t[s + 1]) for s in range(5)]))
                     trs[f"{kind}_{space}"] = {"ms": mt, "points_per_s": rows / (mt * 1e-3),
-                                              "frac_hbm": rows * 32 / (mt * 1e-3) / 1e9 / pk}
+                                              "frac_hbm": rows * 32 / (mt * 1e-3) / 1e9 / pk,
+                                              "traffic": measured_traffic(f"transform:{kind}_{space}", rows)}
             if rank == 0 and not args.no_cpu:
                 trs["cpu_oracle"] = cpu_transforms(N)
             mv["transforms"] = trs

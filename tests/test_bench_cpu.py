@@ -1,0 +1,73 @@
+"""Host-side logic of bench.py that needs no GPU: the DRAM-traffic table written from an
+ncu CSV capture and read back, scaled, by the bench line's `traffic` fields."""
+import json
+
+import pytest
+
+import bench
+
+HDR = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+       '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+
+
+def _line(i, name, metric, value):
+    return (f'"{i}","1","python3.12","127.0.0.1","{name}","1","13","(128, 1, 1)","(516, 1, 1)","0","10.3",'
+            f'"Command line profiler metrics","{metric}","byte","{value}"')
+
+
+def _csv(tmp_path, launches):
+    lines = ["==PROF== Connected to process 1", HDR]
+    for i, (name, rd, wr) in enumerate(launches):
+        lines += [_line(i, name, "dram__bytes_read.sum", f"{rd:,}"), _line(i, name, "dram__bytes_write.sum", wr),
+                  _line(i, name, "gpu__time_duration.sum", 1000)]
+    p = tmp_path / "t.csv"
+    p.write_text("\n".join(lines) + "\n")
+    return str(p)
+
+
+W = dict(N=64, Nx=4, Nz=4, nu=1e-3, dt=1e-3)          # 3 x 4 = 12 modes, 768 rows
+
+
+def test_write_and_read_back(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(tmp_path / "traffic.json"))
+    rows = bench.n_modes_of(W) * W["N"]
+    assert rows == 768
+    path = _csv(tmp_path, [
+        # ncu prints nested template names in several forms: match on the base name
+        ("void unnamed>::bih_df_kernel<0>(Plan, const int *, long, long, const double *, double *, float4 *)",
+         768 * 40, 768 * 40),
+        ("void unnamed>::bih_df_kernel<0>(Plan, const int *, long, long, const double *, double *, float4 *)",
+         768 * 42, 768 * 40),
+        ("void unnamed>::bih_df_kernel<1>(Plan, const int *, long, long, const double *, double *, float4 *)",
+         1, 1),                                                          # other shape: not the table's
+        ("void shen::<unnamed>::transform_kernel<1, 1, 0>(shen::<unnamed>::TrArgs, const double *, double *)",
+         768 * 16, 768 * 16),
+        ("void unnamed>::mass_sweep_kernel<1, 8>(const float4 *, int, int, int, long, double *)",
+         768 * 30, 768 * 29),
+    ])
+    out = bench.write_traffic(path, W)
+    bpr = out["bytes_per_row"]
+    assert bpr["biharmonic:df"] == pytest.approx(81.0)                   # mean of 80 and 82
+    assert bpr["transform:scalar_dirichlet"] == pytest.approx(32.0)
+    assert bpr["transform:forward_dirichlet"] == pytest.approx(32.0 + 59.0)
+    assert "helmholtz:df" not in bpr
+    assert out["launches"]["bih_df_kernel<0>"] == 2
+    saved = json.loads((tmp_path / "traffic.json").read_text())
+    assert saved["sources_sha1"] == {g: bench.sources_sha1(n) for g, n in bench.TRAFFIC_SOURCES.items()}
+    # read back, scaled to another workload's rows
+    assert bench.measured_traffic("biharmonic:df", 1000) == pytest.approx(81000.0)
+    assert bench.measured_traffic("transform:forward_dirichlet", 10) == pytest.approx(910.0)
+    assert bench.measured_traffic("helmholtz:df", 10) is None
+
+
+def test_stale_sources_give_no_traffic(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(tmp_path / "traffic.json"))
+    bench.write_traffic(_csv(tmp_path, [("void unnamed>::velocity_df_kernel(Plan)", 768 * 50, 768 * 44)]), W)
+    assert bench.measured_traffic("velocity:df", 1) == pytest.approx(94.0)
+    t = json.loads((tmp_path / "traffic.json").read_text())
+    t["sources_sha1"]["velocity"] = "0" * 40                            # the kernel changed since the capture
+    (tmp_path / "traffic.json").write_text(json.dumps(t))
+    assert bench.measured_traffic("velocity:df", 1) is None
+    assert bench.traffic_group("matvec_helmholtz:df") == "matvec"
+    assert bench.traffic_group("transform:inverse_dirichlet") == "transform"
+    assert bench.traffic_group("helmholtz:df") == "df"
