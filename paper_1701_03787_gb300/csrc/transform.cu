@@ -57,7 +57,12 @@ __device__ __forceinline__ F2 dneg(F2 a) { return F2{-a.hi, -a.lo}; }
 __device__ __forceinline__ F2 nrm(F2 a) { return df::fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ Z zadd(Z a, Z b) { return Z{df::add(a.re, b.re), df::add(a.im, b.im)}; }
 // Sum without the final renormalisation: hi carries the float32 sum, lo the exact error of
-// it plus the low parts.  Only fed into a normalising add (never into a product).
+// it plus the low parts, so hi + lo is the float-float sum.  lo may exceed half an ulp of
+// hi (after cancellation), but the absolute error stays that of float32 arithmetic on lo,
+// about 2^-24 |lo| <= 2^-48 times the inputs' magnitude, and a later product or add of
+// such a pair keeps that absolute bound (a product drops only lo_x lo_y).  The FFT's
+// error is norm-wise (relative to the column's magnitude), so its passes run on raw pairs
+// (twice the error of renormalised sums in a float32 emulation, far inside the bound).
 __device__ __forceinline__ F2 add_raw(F2 x, F2 y) {
     const F2 s = df::two_sum(x.hi, y.hi);
     return F2{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
@@ -67,6 +72,12 @@ __device__ __forceinline__ Z zsub_raw(Z a, Z b) {
     return Z{add_raw(a.re, F2{-b.re.hi, -b.re.lo}), add_raw(a.im, F2{-b.im.hi, -b.im.lo})};
 }
 __device__ __forceinline__ Z zsub(Z a, Z b) { return Z{df::add(a.re, dneg(b.re)), df::add(a.im, dneg(b.im))}; }
+__device__ __forceinline__ Z zmul_raw(Z a, Z w) {    // a w, raw sums
+    return Z{add_raw(df::mul(a.re, w.re), dneg(df::mul(a.im, w.im))), add_raw(df::mul(a.re, w.im), df::mul(a.im, w.re))};
+}
+__device__ __forceinline__ Z zmulc_raw(Z a, Z w) {   // a conj(w), raw sums
+    return Z{add_raw(df::mul(a.re, w.re), df::mul(a.im, w.im)), add_raw(df::mul(a.im, w.re), dneg(df::mul(a.re, w.im)))};
+}
 __device__ __forceinline__ Z zmul(Z a, Z w) {        // a w
     return Z{df::add(df::mul(a.re, w.re), dneg(df::mul(a.im, w.im))),
              df::add(df::mul(a.re, w.im), df::mul(a.im, w.re))};
@@ -75,6 +86,7 @@ __device__ __forceinline__ Z zmulc(Z a, Z w) {       // a conj(w)
     return Z{df::add(df::mul(a.re, w.re), df::mul(a.im, w.im)),
              df::add(df::mul(a.im, w.re), dneg(df::mul(a.re, w.im)))};
 }
+__device__ __forceinline__ Z zneg(Z a) { return Z{dneg(a.re), dneg(a.im)}; }
 __device__ __forceinline__ Z zi(Z a) { return Z{dneg(a.im), a.re}; }      // i a
 __device__ __forceinline__ Z zmi(Z a) { return Z{a.im, dneg(a.re)}; }     // -i a
 __device__ __forceinline__ Z zhalf(Z a) {
@@ -87,6 +99,9 @@ __device__ __forceinline__ Z zscale(Z a, F2 s) { return Z{nrm(df::mul(a.re, s)),
 __device__ __forceinline__ Z zfma(F2 s, Z a, Z b) {  // b + s a
     return Z{df::add(b.re, df::mul(a.re, s)), df::add(b.im, df::mul(a.im, s))};
 }
+__device__ __forceinline__ Z zfma_raw(F2 s, Z a, Z b) {  // b + s a, raw sum
+    return Z{add_raw(b.re, df::mul(a.re, s)), add_raw(b.im, df::mul(a.im, s))};
+}
 __device__ __forceinline__ Z zld(const float4 *p) {
     const float4 v = __ldg(p);
     return Z{F2{v.x, v.y}, F2{v.z, v.w}};
@@ -95,6 +110,13 @@ __device__ __forceinline__ Z zfromf64(double2 v) { return Z{df::from_f64(v.x), d
 __device__ __forceinline__ double2 ztof64(Z v) { return make_double2(df::to_f64(v.re), df::to_f64(v.im)); }
 
 constexpr Z kZero{F2{0.f, 0.f}, F2{0.f, 0.f}};
+
+// Raw (unrenormalised) sums in the FFT passes of the scalar products too.  The inverse
+// transform always uses them.  The scalar products feed the forward transform's mass solve,
+// which amplifies their error by the conditioning of B: their Makhoul pair step and basis
+// combination stay renormalised (raw sums there raised the forward transform's error on
+// smooth spectra 15- to 300-fold, to the bound of its tests).
+constexpr bool kRawForward = true;
 
 // Position of frequency k after the in-place DIF passes (radix 4 first, then one radix 2
 // when log2 N is odd): the first pass puts k mod 4 in quarter (k mod 4), and so on, so
@@ -138,7 +160,7 @@ struct Group {
 // unnormalised, output in dpos() order.  tw: per radix-4 pass p (span L = N / 4^p,
 // Q = L/4), entries [3 j + m - 1] = e^{-2 pi i m j 4^p / N}, j < Q, m = 1, 2, 3, passes
 // stored one after the other, so a pass reads its twiddles contiguously.
-template <bool INV>
+template <bool INV, bool RAW>
 __device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
     const int N = 1 << lg, half = N >> 1;
     int lgL = lg;
@@ -151,19 +173,20 @@ __device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
             const int base = ((b >> lgQ) << lgL) + j;
             const Z a = ldz(A, base), bb = ldz(A, base + Q), c = ldz(A, base + 2 * Q), d = ldz(A, base + 3 * Q);
             const Z s0 = zadd_raw(a, c), s1 = zsub_raw(a, c), s2 = zadd_raw(bb, d), s3 = zsub_raw(bb, d);
-            Z y0 = zadd(s0, s2), y2 = zsub(s0, s2);
-            Z y1 = INV ? zadd(s1, zi(s3)) : zadd(s1, zmi(s3));
-            Z y3 = INV ? zadd(s1, zmi(s3)) : zadd(s1, zi(s3));
+            auto sum = [](Z u, Z v) { return RAW ? zadd_raw(u, v) : zadd(u, v); };
+            Z y0 = sum(s0, s2), y2 = sum(s0, zneg(s2));
+            Z y1 = sum(s1, INV ? zi(s3) : zmi(s3));
+            Z y3 = sum(s1, INV ? zmi(s3) : zi(s3));
             if (j != 0) {
                 Z w1 = ldz(twp, 3 * j), w2 = ldz(twp, 3 * j + 1), w3 = ldz(twp, 3 * j + 2);
                 if (INV) {
-                    y1 = zmulc(y1, w1);
-                    y2 = zmulc(y2, w2);
-                    y3 = zmulc(y3, w3);
+                    y1 = RAW ? zmulc_raw(y1, w1) : zmulc(y1, w1);
+                    y2 = RAW ? zmulc_raw(y2, w2) : zmulc(y2, w2);
+                    y3 = RAW ? zmulc_raw(y3, w3) : zmulc(y3, w3);
                 } else {
-                    y1 = zmul(y1, w1);
-                    y2 = zmul(y2, w2);
-                    y3 = zmul(y3, w3);
+                    y1 = RAW ? zmul_raw(y1, w1) : zmul(y1, w1);
+                    y2 = RAW ? zmul_raw(y2, w2) : zmul(y2, w2);
+                    y3 = RAW ? zmul_raw(y3, w3) : zmul(y3, w3);
                 }
             }
             stz(A, base, y0);
@@ -230,7 +253,8 @@ struct TrArgs {
     int n_tw;                // float4 of the per-pass twiddle table (copied to shared memory)
     const float4 *tw;        // per-pass twiddles
     const float4 *mk;        // e^{-i pi k/(2N)}, k = 0 .. N/2
-    const float4 *coef;      // per k: (g1i_k, g2i_k), (g1_k, g2_k)
+    const float4 *coef_i;    // per k: (g1i_k, g2i_k), psi -> T coefficients (inverse)
+    const float4 *coef_f;    // per k: (g1_k, g2_k), psi combination of the scalar products
     int *err;                // set to 1 if a column copy did not complete
     F2 pi_over_N;
 };
@@ -296,11 +320,11 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
             auto tk = [&](int k) -> Z {
                 if (k >= N) return kZero;
                 Z t = ldz(Bf, k);
-                if (SPACE == 1 && k >= 2) t = zsub(t, ldz(Bf, k - 2));
+                if (SPACE == 1 && k >= 2) t = zsub_raw(t, ldz(Bf, k - 2));
                 if (SPACE == 2 && k >= 2) {
-                    const float4 c = __ldg(a.coef + 2 * k);
-                    t = zfma(dneg(F2{c.x, c.y}), ldz(Bf, k - 2), t);
-                    if (k >= 4) t = zfma(F2{c.z, c.w}, ldz(Bf, k - 4), t);
+                    const float4 c = __ldg(a.coef_i + k);
+                    t = zfma_raw(dneg(F2{c.x, c.y}), ldz(Bf, k - 2), t);
+                    if (k >= 4) t = zfma_raw(F2{c.z, c.w}, ldz(Bf, k - 4), t);
                 }
                 return t;
             };
@@ -315,7 +339,7 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     if (k >= 1 && k < M) stz(A, 2 * M - k, t);
                 }
                 prefetch_next(next);
-                fft_dif<false>(A, lg, tw, g);
+                fft_dif<false, kRawForward>(A, lg, tw, g);
                 for (int i = g.t; i < N; i += g.nt) {
                     const Z e = zadd(t0, (i & 1) ? Z{dneg(tM.re), dneg(tM.im)} : tM);
                     y[i] = ztof64(zhalf(zadd(ldz(A, dpos(i, lg)), e)));
@@ -332,11 +356,11 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     continue;
                 }
                 const Z t1 = tk(k), t2 = tk(N - k), w = mkz(k);
-                stz(A, k, zhalf(zmulc(zadd(t1, zmi(t2)), w)));
-                if (k != half) stz(A, N - k, zhalf(zi(zmul(zadd(t2, zmi(t1)), w))));
+                stz(A, k, zhalf(zmulc_raw(zadd_raw(t1, zmi(t2)), w)));
+                if (k != half) stz(A, N - k, zhalf(zi(zmul_raw(zadd_raw(t2, zmi(t1)), w))));
             }
             prefetch_next(next);
-            fft_dif<true>(A, lg, tw, g);
+            fft_dif<true, true>(A, lg, tw, g);
             for (int m = g.t; m < N; m += g.nt) {
                 const int src = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
                 y[m] = ztof64(ldz(A, dpos(src, lg)));
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     if (m >= 1 && m < M) stz(A, 2 * M - m, v);
                 }
                 prefetch_next(next);
-                fft_dif<false>(A, lg, tw, g);
+                fft_dif<false, kRawForward>(A, lg, tw, g);
             } else {
             // values -> Makhoul order in A; R free for the next column
             for (int m = g.t; m < N; m += g.nt) {
@@ -360,7 +384,7 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 stz(A, dst, zfromf64(xs[m]));
             }
             prefetch_next(next);
-            fft_dif<false>(A, lg, tw, g);
+            fft_dif<false, kRawForward>(A, lg, tw, g);
             // C_k (DCT-II) in place: the pair (k, N-k) is read and written by one thread at
             // positions dpos(k), dpos(N-k)
             for (int k = g.t; k <= half; k += g.nt) {
@@ -393,7 +417,7 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     Z v = C(l);
                     if (SPACE == 1) v = zsub(v, C(l + 2));
                     if (SPACE == 2) {
-                        const float4 c = __ldg(a.coef + 2 * l + 1);
+                        const float4 c = __ldg(a.coef_f + l);
                         v = zfma(dneg(F2{c.x, c.y}), C(l + 2), v);
                         v = zfma(F2{c.z, c.w}, C(l + 4), v);
                     }
@@ -584,8 +608,9 @@ int twiddle_count(int N) {
 // Tables of the transforms of an N-mode plan (float4 units, float-float pairs):
 //   [0, ntw)                per-pass twiddles of fft_dif
 //   [ntw, ntw + N/2 + 1)    mk[k] = e^{-i pi k/(2N)}, k = 0 .. N/2
-//   then 2 N: per k, (2k/(k+1), (k-3)/(k-1)) (psi -> T coefficients, k >= 2 / 4) and
-//                    (2(k+2)/(k+3), (k+1)/(k+3)) (Eq. phiN weights, k < N-4)
+//   then N: per k, (2k/(k+1), (k-3)/(k-1)) (psi -> T coefficients, k >= 2 / 4), and
+//   N more: per k, (2(k+2)/(k+3), (k+1)/(k+3)) (Eq. phiN weights, k < N-4); two planes, so
+//   that a kernel's coefficients and mk share the L1 left beside its shared memory
 //   then the mass-solve rows of phi (2 RMd 3) and of psi (2 RMb 3).
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
@@ -610,10 +635,11 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     }
     for (int k = 0; k < N; k++) {
         const long double K = k;
-        const long double gi1 = k >= 2 ? 2 * K / (K + 1) : 0.0L, gi2 = k >= 4 ? (K - 3) / (K - 1) : 0.0L;
-        const long double g1 = k < N - 4 ? 2 * (K + 2) / (K + 3) : 0.0L, g2 = k < N - 4 ? (K + 1) / (K + 3) : 0.0L;
-        tab.push_back(pair4(gi1, gi2));
-        tab.push_back(pair4(g1, g2));
+        tab.push_back(pair4(k >= 2 ? 2 * K / (K + 1) : 0.0L, k >= 4 ? (K - 3) / (K - 1) : 0.0L));
+    }
+    for (int k = 0; k < N; k++) {
+        const long double K = k;
+        tab.push_back(pair4(k < N - 4 ? 2 * (K + 2) / (K + 3) : 0.0L, k < N - 4 ? (K + 1) / (K + 3) : 0.0L));
     }
     std::vector<float4> md, mb;
     mass_rows(N, 1, RMd, md, p.gl);
@@ -690,7 +716,8 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, long count, con
     a.n_tw = p.tr_ntw;
     a.tw = p.d_tr;
     a.mk = p.d_tr + p.tr_ntw;
-    a.coef = a.mk + (N / 2 + 1);
+    a.coef_i = a.mk + (N / 2 + 1);
+    a.coef_f = a.coef_i + N;
     const double pn = p.gl ? kPi / (2.0 * (N - 1)) : kPi / N;   // weight of the point sum
     const float ph = (float)pn;
     a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
