@@ -794,7 +794,7 @@ def main():
             stream.synchronize()
             return sum(d.numel() for d, _, _ in pairs) * 16 / (la.elapsed_time(lb) * 1e-3) / 1e9
 
-        link_before = link_test()
+        link_before = [link_test() for _ in range(3)]
         e2e_step()
         stream.synchronize()
         # each step timed on its own; the median step is the figure (the host link is
@@ -830,13 +830,13 @@ def main():
             pick = torch.as_tensor(np.linspace(0, nm - 1, 257).astype(np.int64))
             e2e["matches_device"] = bool(torch.equal(hu[pick], u_h[pick.cuda()].cpu())
                                          and torch.equal(hu2[pick], u_b[pick.cuda()].cpu()))
-        link_after = link_test()
-        link_gbs = max(link_before, link_after)
+        link_after = [link_test() for _ in range(3)]
+        link_gbs = max(link_before + link_after)
         e2e_gbs = 4 * rows * 16 / (e2e_ms * 1e-3) / 1e9
         e2e["roofline"] = {"bound": "host link (H2D + D2H concurrently)", "achieved": e2e_gbs, "peak": link_gbs,
                            "unit": "GB/s", "frac": e2e_gbs / link_gbs,
-                           "peak_kind": "measured in this run: plain copies, both directions at once, the better "
-                                        "of before and after the e2e steps",
+                           "peak_kind": "measured in this run: plain copies, both directions at once, the best "
+                                        "of three passes before and three after the e2e steps",
                            "link_gbs_before_after": [link_before, link_after]}
         del hf_h, hf_b, hu, hu2
 
