@@ -111,6 +111,21 @@ __device__ __forceinline__ double2 ztof64(Z v) { return make_double2(df::to_f64(
 
 constexpr Z kZero{F2{0.f, 0.f}, F2{0.f, 0.f}};
 
+// n / d as a float-float, for integers 0 < n, d < 2^13 held exactly in float32: hi from an
+// approximate quotient, the remainder n - hi d exactly by one FMA (a multiple of hi's ulp,
+// at most a few of them), lo = remainder / d with one correction step.  Relative error of
+// hi + lo below 2^-46 (checked for every ratio the transforms use, with the reciprocal off
+// by up to 2 ulp).  The psi coefficients are formed this way in registers: read from a
+// table they missed L1 (which holds ~28 KB beside the kernels' shared memory) and their
+// L2 latency sat on every thread's dependent chain (inverse psi 13.1 -> 11.0 ms).
+__device__ __forceinline__ F2 ratio(float n, float d) {
+    const float r = __fdividef(1.0f, d);
+    const float hi = n * r;
+    const float rem = __fmaf_rn(-hi, d, n);
+    const float lo = rem * r;
+    return F2{hi, __fmaf_rn(__fmaf_rn(-lo, d, rem), r, lo)};
+}
+
 // Raw (unrenormalised) sums in the FFT passes of the scalar products too.  The inverse
 // transform always uses them.  The scalar products feed the forward transform's mass solve,
 // which amplifies their error by the conditioning of B: their Makhoul pair step and basis
@@ -253,8 +268,6 @@ struct TrArgs {
     int n_tw;                // float4 of the per-pass twiddle table (copied to shared memory)
     const float4 *tw;        // per-pass twiddles
     const float4 *mk;        // e^{-i pi k/(2N)}, k = 0 .. N/2
-    const float4 *coef_i;    // per k: (g1i_k, g2i_k), psi -> T coefficients (inverse)
-    const float4 *coef_f;    // per k: (g1_k, g2_k), psi combination of the scalar products
     int *err;                // set to 1 if a column copy did not complete
     F2 pi_over_N;
 };
@@ -322,9 +335,11 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 Z t = ldz(Bf, k);
                 if (SPACE == 1 && k >= 2) t = zsub_raw(t, ldz(Bf, k - 2));
                 if (SPACE == 2 && k >= 2) {
-                    const float4 c = __ldg(a.coef_i + k);
-                    t = zfma_raw(dneg(F2{c.x, c.y}), ldz(Bf, k - 2), t);
-                    if (k >= 4) t = zfma_raw(F2{c.z, c.w}, ldz(Bf, k - 4), t);
+                    // psi_j = T_j - 2(j+2)/(j+3) T_{j+2} + (j+1)/(j+3) T_{j+4}, so t_k takes
+                    // -2k/(k+1) c_{k-2} + (k-3)/(k-1) c_{k-4}
+                    const float kf = (float)k;
+                    t = zfma_raw(dneg(ratio(2.0f * kf, kf + 1.0f)), ldz(Bf, k - 2), t);
+                    if (k >= 4) t = zfma_raw(ratio(kf - 3.0f, kf - 1.0f), ldz(Bf, k - 4), t);
                 }
                 return t;
             };
@@ -417,9 +432,10 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     Z v = C(l);
                     if (SPACE == 1) v = zsub(v, C(l + 2));
                     if (SPACE == 2) {
-                        const float4 c = __ldg(a.coef_f + l);
-                        v = zfma(dneg(F2{c.x, c.y}), C(l + 2), v);
-                        v = zfma(F2{c.z, c.w}, C(l + 4), v);
+                        // Eq. phiN: psi_l = T_l - 2(l+2)/(l+3) T_{l+2} + (l+1)/(l+3) T_{l+4}
+                        const float lf = (float)l;
+                        v = zfma(dneg(ratio(2.0f * lf + 4.0f, lf + 3.0f)), C(l + 2), v);
+                        v = zfma(ratio(lf + 1.0f, lf + 3.0f), C(l + 4), v);
                     }
                     return zscale(v, a.pi_over_N);
                 };
@@ -608,9 +624,6 @@ int twiddle_count(int N) {
 // Tables of the transforms of an N-mode plan (float4 units, float-float pairs):
 //   [0, ntw)                per-pass twiddles of fft_dif
 //   [ntw, ntw + N/2 + 1)    mk[k] = e^{-i pi k/(2N)}, k = 0 .. N/2
-//   then N: per k, (2k/(k+1), (k-3)/(k-1)) (psi -> T coefficients, k >= 2 / 4), and
-//   N more: per k, (2(k+2)/(k+3), (k+1)/(k+3)) (Eq. phiN weights, k < N-4); two planes, so
-//   that a kernel's coefficients and mk share the L1 left beside its shared memory
 //   then the mass-solve rows of phi (2 RMd 3) and of psi (2 RMb 3).
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
@@ -619,7 +632,7 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
     const int ntw = twiddle_count(NF), nmk = N / 2 + 1;
     std::vector<float4> tab;
-    tab.reserve((size_t)ntw + nmk + 2 * N);
+    tab.reserve((size_t)ntw + nmk);
     for (int lgL = lg, sh = 0; lgL >= 2; lgL -= 2, sh += 2) {
         const int Q = 1 << (lgL - 2);
         for (int j = 0; j < Q; j++)
@@ -632,14 +645,6 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     for (int k = 0; k < nmk; k++) {
         const long double ang = -pi * k / (2 * (long double)N);
         tab.push_back(pair4(cosl(ang), sinl(ang)));
-    }
-    for (int k = 0; k < N; k++) {
-        const long double K = k;
-        tab.push_back(pair4(k >= 2 ? 2 * K / (K + 1) : 0.0L, k >= 4 ? (K - 3) / (K - 1) : 0.0L));
-    }
-    for (int k = 0; k < N; k++) {
-        const long double K = k;
-        tab.push_back(pair4(k < N - 4 ? 2 * (K + 2) / (K + 3) : 0.0L, k < N - 4 ? (K + 1) / (K + 3) : 0.0L));
     }
     std::vector<float4> md, mb;
     mass_rows(N, 1, RMd, md, p.gl);
@@ -716,8 +721,6 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, long count, con
     a.n_tw = p.tr_ntw;
     a.tw = p.d_tr;
     a.mk = p.d_tr + p.tr_ntw;
-    a.coef_i = a.mk + (N / 2 + 1);
-    a.coef_f = a.coef_i + N;
     const double pn = p.gl ? kPi / (2.0 * (N - 1)) : kPi / N;   // weight of the point sum
     const float ph = (float)pn;
     a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
