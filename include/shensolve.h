@@ -146,7 +146,10 @@ shen_status shen_biharmonic_solve(shen_plan_t plan, const double *f, double *u, 
                                   void *stream);
 
 /* Solve modes [mode_begin, mode_begin + mode_count) only: f and u point at the
- * column of mode_begin (a shard of a larger field).  problem: shen_problem. */
+ * column of mode_begin (a shard of a larger field).  problem: shen_problem.
+ * mode_count = 0 (an empty shard, e.g. more ranks than modes) checks the plan, problem,
+ * precision and range, launches nothing and returns SHEN_OK; f and u are not read then
+ * and may be NULL. */
 shen_status shen_solve_modes(shen_plan_t plan, int problem, long mode_begin, long mode_count,
                              const double *f, double *u, int precision, void *stream);
 
@@ -267,7 +270,8 @@ shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *
 /* The same for modes [mode_begin, mode_begin + mode_count) only: in and out point at the
  * column of mode_begin (a shard of a larger field, as for shen_solve_modes).  The transforms
  * do not depend on the mode, so a shard's columns are the full transform's columns bit for
- * bit. */
+ * bit.  mode_count = 0 checks the arguments (SHEN_ERR_UNSUPPORTED as above), launches
+ * nothing and returns SHEN_OK; in and out may then be NULL. */
 shen_status shen_transform_modes(shen_plan_t plan, int kind, int space, long mode_begin, long mode_count,
                                  const double *in, double *out, void *stream);
 

@@ -289,16 +289,17 @@ namespace {
 
 shen_status solve_range(shen_plan_t plan, int problem, long m0, long count, const double *f, double *u,
                         int precision, void *stream) {
-    if (!plan || !f || !u) return SHEN_ERR_ARG;
+    if (!plan) return SHEN_ERR_ARG;
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (m0 < 0 || count < 0 || m0 + count > p.n_modes) return SHEN_ERR_ARG;
-    if (!aligned16(f) || !aligned16(u)) return SHEN_ERR_ARG;
-    if (!overlap_ok(f, u, 2 * count * (long)p.N)) return SHEN_ERR_ARG;
     if (precision == SHEN_AUTO) precision = p.auto_prec[problem];
     shen_status ps = check_precision(p, problem, precision);
     if (ps != SHEN_OK) return ps;
-    if (count == 0) return SHEN_OK;
+    if (count == 0) return SHEN_OK;                          // an empty range: f, u are not read
+    if (!f || !u) return SHEN_ERR_ARG;
+    if (!aligned16(f) || !aligned16(u)) return SHEN_ERR_ARG;
+    if (!overlap_ok(f, u, 2 * count * (long)p.N)) return SHEN_ERR_ARG;
     SHEN_CUDA_TRY(launch_solve_range(p, problem, precision, m0, count, f, u, as_stream(stream)));
     return SHEN_OK;
 }
@@ -474,15 +475,17 @@ shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *
 
 shen_status shen_transform_modes(shen_plan_t plan, int kind, int space, long mode_begin, long mode_count,
                                  const double *in, double *out, void *stream) {
-    if (!plan || !in || !out) return SHEN_ERR_ARG;
+    if (!plan) return SHEN_ERR_ARG;
     if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (kind < SHEN_TRANSFORM_INVERSE || kind > SHEN_TRANSFORM_FORWARD) return SHEN_ERR_ARG;
     if (space < SHEN_SPACE_CHEBYSHEV || space > SHEN_SPACE_BIHARMONIC) return SHEN_ERR_ARG;
     const Plan &p = plan->p;
     if (mode_begin < 0 || mode_count < 0 || mode_begin + mode_count > p.n_modes) return SHEN_ERR_ARG;
+    if (!transform_supported(p) || !transform_shape_ok(p, kind, space)) return SHEN_ERR_UNSUPPORTED;
+    if (mode_count == 0) return SHEN_OK;                     // an empty range: in, out are not read
+    if (!in || !out) return SHEN_ERR_ARG;
     if (!aligned16(in) || !aligned16(out)) return SHEN_ERR_ARG;
     if (!overlap_ok(in, out, 2 * mode_count * (long)p.N)) return SHEN_ERR_ARG;
-    if (!transform_supported(p) || !transform_shape_ok(p, kind, space)) return SHEN_ERR_UNSUPPORTED;
     SHEN_CUDA_TRY(launch_transform(p, kind, space, mode_count, in, out, as_stream(stream)));
     return SHEN_OK;
 }
