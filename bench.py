@@ -45,7 +45,7 @@ BYTES_PER_ROW = 32          # algorithmic bytes per complex row of one solve: re
 # arithmetic of each solve path (all read and write complex128 fields)
 DTYPES = {"fp64": "f64", "df": "f32x2 (float-float)", "df_r1": "f32 sweeps + f32x2 refinement",
           "df_r2": "f32 sweeps + f32x2 refinement", "fp32_r1": "f32 sweeps + f64 refinement",
-          "fp32_r2": "f32 sweeps + f64 refinement"}
+          "fp32_r2": "f32 sweeps + f64 refinement", "fp64_r1": "f64 sweeps + f64x2 refinement"}
 
 
 def dtype_of(prec):
@@ -412,28 +412,35 @@ def cpu_baseline_batch(w, seconds_target=8.0, seed=0):
                       f"O(N) C oracle (Sec. 4 algorithms), float64"}
 
 
-def oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined_modes):
-    """Error of the GPU result vs the oracle: O(N) C oracle on `modes`, refined dense
-    reference on `refined_modes` (both sets of mode indices)."""
+def oracle_errors(w, F_h, F_b, results, modes, refined_modes):
+    """Error of GPU results against the oracle on sampled modes.  results: {path: (U_h, U_b)},
+    rows aligned with `modes` (global mode indices).  Every path against the O(N) C oracle
+    (the paper's algorithm in float64) on all of `modes`, and against the refined reference
+    (the O(N) solve refined with a longdouble residual of the exactly evaluated matrices) on
+    `refined_modes`: max, median and field-level relative L2."""
     from oracle import on
     from oracle import solve as so
+    from oracle import structured as st
     N = w["N"]
     c = so.c_of(w["nu"], w["dt"])
     z2 = so.mode_z2(w["Nx"], w["Nz"])
-    out = {}
-    for problem, F, U in (("helmholtz", F_h, U_h), ("biharmonic", F_b, U_b)):
+    pos = {m: i for i, m in enumerate(modes)}
+    ref_rows = [pos[m] for m in refined_modes]
+    out = {"n_modes_checked": len(modes), "n_refined": len(ref_rows)}
+    for problem, F in (("helmholtz", F_h), ("biharmonic", F_b)):
         n = so.n_unknowns(problem, N)
         R = on.solve_modes(problem, N, z2[modes], c, F)
-        errs = [so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))]
-        pos = {m: i for i, m in enumerate(modes)}
-        ref_errs = []
-        for m in refined_modes:
-            r = so.solve_mode_ref(problem, N, float(z2[m]), c, F[pos[m]])
-            ref_errs.append(so.rel_l2(U[pos[m], :n], r))
-        out[problem] = {"vs_on_max": float(max(errs)), "vs_on_median": float(np.median(errs)),
-                        "n_modes_checked": len(modes),
-                        "vs_refined_max": float(max(ref_errs)) if ref_errs else None,
-                        "n_refined": len(ref_errs)}
+        Rr = st.solve_ref(problem, N, z2[refined_modes], c, F[ref_rows])
+        for path, (U_h, U_b) in results.items():
+            U = U_h if problem == "helmholtz" else U_b
+            errs = [so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))]
+            ref_errs = [so.rel_l2(U[i, :n], Rr[j, :n]) for j, i in enumerate(ref_rows)]
+            num = sum(float(np.sum(np.abs(U[i, :n] - Rr[j, :n]) ** 2)) for j, i in enumerate(ref_rows))
+            den = sum(float(np.sum(np.abs(Rr[j, :n]) ** 2)) for j in range(len(ref_rows)))
+            out.setdefault(path, {})[problem] = {
+                "vs_on_max": float(max(errs)), "vs_on_median": float(np.median(errs)),
+                "vs_refined_max": float(max(ref_errs)), "vs_refined_median": float(np.median(ref_errs)),
+                "vs_refined_field": math.sqrt(num / den)}
     return out
 
 
@@ -448,23 +455,64 @@ def resolve_precision(spec):
 
 
 def run_reference(args, w):
+    """The oracle's O(N) C code (the paper's algorithms, OpenMP over modes) as the reference
+    arm.  Every step solves a bounded sample of the workload (both problems), so that the
+    whole --steps K --warmup W run takes seconds to a minute; W steps run untimed, then K
+    steps are timed one by one with a wall clock.  value and ms_per_step are those of the
+    sampled steps; the time a whole-workload step would take at that rate is reported
+    separately and labelled as extrapolated."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle import on
+    from oracle import solve as so
+    from paper_1701_03787_gb300 import inputs
+    cases = []                                      # (N, z2, c, F) per solve batch of a step
     if "n_inst" in w:
-        base = cpu_baseline_batch(w, seconds_target=min(60.0, max(5.0, 0.5 * args.steps)))
-        from paper_1701_03787_gb300 import inputs
-        rows = sum((d["Nx"] // 2 + 1) * d["Nz"] * d["N"] for d in inputs.batch_instances(w["n_inst"], w["seed"]))
+        insts = inputs.batch_instances(w["n_inst"], seed=w["seed"])
+        full_rows = sum((d["Nx"] // 2 + 1) * d["Nz"] * d["N"] for d in insts)
+        picks = insts[:: max(1, len(insts) // 64)]
+        for i, d in enumerate(picks):
+            z2 = so.mode_z2(d["Nx"], d["Nz"])
+            cases.append((d["N"], z2, so.c_of(d["nu"], d["dt"]), inputs.rhs_numpy(z2.size, d["N"], i)))
+        desc = f"all modes of {len(picks)} of {len(insts)} instances (every {max(1, len(insts) // 64)}th)"
     else:
-        base = cpu_baseline(w, "reference", seconds_target=max(2.0, 2.0 * args.steps))
-        rows = n_modes_of(w) * w["N"]
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": base["unit"],
+        N = w["N"]
+        z2_all = so.mode_z2(w["Nx"], w["Nz"])
+        full_rows = z2_all.size * N
+        n_sample = min(z2_all.size, max(1024, int(2 ** 25 // N)))       # 32 Mi rows: ~0.2 s per step
+        idx = np.linspace(0, z2_all.size - 1, n_sample).astype(np.int64)
+        cases.append((N, z2_all[idx], so.c_of(w["nu"], w["dt"]), inputs.rhs_numpy(n_sample, N, 0)))
+        desc = f"{n_sample} of {z2_all.size} modes (evenly spaced)"
+    rows = sum(z2.size * N_ for N_, z2, _, _ in cases)
+
+    def one_step():
+        for N_, z2, c, F in cases:
+            on.solve_modes("helmholtz", N_, z2, c, F)
+            on.solve_modes("biharmonic", N_, z2, c, F)
+
+    for _ in range(max(args.warmup, 1)):
+        one_step()
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        one_step()
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = args.steps * 2 * rows / total
+    cores = on.max_threads()
+    base = {"value": value, "unit": "solves*N/s", "cores": cores, "kind": "oracle",
+            "sample": f"{desc}, Helmholtz + biharmonic per step, O(N) C oracle (Sec. 4 algorithms), float64"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves*N/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 2 * rows / base["value"] * 1e3,
+            "ms_per_step": total / args.steps * 1e3,
+            "step": f"a bounded sample of the workload ({2 * rows} complex rows of {2 * full_rows})",
+            "full_step_ms_extrapolated": 2 * full_rows / value * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, **w, "rows": rows},
+            "data": "synthetic", "config": {"workload": args.workload, **w, "rows": full_rows,
+                                            "sample_rows": rows},
             "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": base["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "solves*N/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -486,6 +534,9 @@ def main():
                     help="2: run the two solves concurrently on two streams")
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
                     help="replay the step as a captured CUDA graph (auto: on for the batch workload)")
+    ap.add_argument("--shard", action="store_true",
+                    help="split the one field's modes into contiguous ranges, one per rank (shen_solve_modes); "
+                         "strong scaling.  Default: one whole replica of the workload per rank (weak scaling)")
     ap.add_argument("--write-traffic", metavar="CSV",
                     help="rewrite profiles/traffic.json from an ncu DRAM-bytes capture on --workload, then exit")
     args = ap.parse_args()
@@ -528,8 +579,19 @@ def main():
         nm = plan.n_modes
         rows = nm * N
     t_plan = time.perf_counter() - t_plan
+    shard = args.shard and not batched and not lean
+    m0, full_nm = 0, nm
+    if shard:
+        from paper_1701_03787_gb300.sharding import shard_range
+        m0, nm = shard_range(full_nm, rank, world)
+        rows = nm * N
     with torch.cuda.stream(stream):
-        if batched:
+        if shard:
+            # this rank's columns of the one field (the same inputs on every rank count)
+            f_h = inputs.rhs_torch(full_nm, N, seed=100)[m0:m0 + nm].clone()
+            f_b = inputs.rhs_torch(full_nm, N, seed=200)[m0:m0 + nm].clone()
+            torch.cuda.empty_cache()
+        elif batched:
             f_h = inputs.batch_rhs_torch(plan.offsets, insts, seed=100 + rank)
             f_b = inputs.batch_rhs_torch(plan.offsets, insts, seed=200 + rank)
         else:
@@ -544,8 +606,13 @@ def main():
     if batched:
         plan.helmholtz_solve = lambda f, u, precision, stream: plan.solve("helmholtz", f, u, precision, stream)
         plan.biharmonic_solve = lambda f, u, precision, stream: plan.solve("biharmonic", f, u, precision, stream)
+    if shard:
+        plan.helmholtz_solve = lambda f, u, precision, stream: plan.solve_modes("helmholtz", m0, f, u, precision,
+                                                                                stream)
+        plan.biharmonic_solve = lambda f, u, precision, stream: plan.solve_modes("biharmonic", m0, f, u,
+                                                                                 precision, stream)
     tuned = None
-    if args.precision == "auto":
+    if args.precision == "auto" and not shard:
         # the library's autotuner times every path that meets the 1e-10 bar (and the
         # row-block shapes of the float-float kernels) on these fields and keeps the fastest
         tuned = {}
@@ -630,7 +697,7 @@ def main():
     # rhs_matvec (out = R x + beta y) for each problem, alone on `stream`: reads x and y,
     # writes out (48 algorithmic bytes per complex row)
     mv = None
-    if not batched:
+    if not batched and not shard:
         out = torch.empty_like(f_h)
         pk, _ = peaks()
         mv = {"bytes_per_row": 48}
@@ -655,7 +722,7 @@ def main():
                          "traffic": {"helmholtz": measured_traffic(f"matvec_helmholtz:{mprec}", rows),
                                      "biharmonic": measured_traffic(f"matvec_biharmonic:{mprec}", rows)}}
         del out
-    if not batched and not lean:
+    if not batched and not lean and not shard:
         # velocity recovery (f from u, then v and w): reads u, g, writes v, w (64 B per row)
         vv, ww = torch.empty_like(f_h), torch.empty_like(f_h)
         for _ in range(2):
@@ -715,15 +782,18 @@ def main():
             del tr_out
     ms, = max_over_ranks([ms], pg, "cuda")
     step_rows = 2 * rows + (2 * N if lean else 0)            # complex rows solved per step
-    value = world * step_rows / (ms * 1e-3)
+    # replicas: every rank solves the whole workload; shards: the ranks together solve it once
+    value = (2 * full_nm * N if shard else world * step_rows) / (ms * 1e-3)
 
     # oracle-check samples, gathered now (later phases may reuse the device fields)
     sample = None
     if rank == 0 and not args.no_check and not batched:
-        special = list(inputs.grid_modes(w["Nx"], w["Nz"]).values())
-        modes = inputs.sample_modes(nm, 0.01 if nm * N <= 1e9 else 0.002, 3, must_include=special)
-        refined = sorted(set(special) | set(modes[:: max(1, len(modes) // 8)]))
-        idx = torch.as_tensor(modes, device="cuda")
+        # (0, 0), the Nyquist modes and the corner (kx and kz Nyquist: the largest z2)
+        special = [m for m in inputs.grid_modes(w["Nx"], w["Nz"]).values() if m0 <= m < m0 + nm]
+        modes = [m + m0 for m in inputs.sample_modes(nm, 0.01 if nm * N <= 1e9 else 0.002, 3)]
+        modes = sorted(set(modes) | set(special))
+        refined = sorted(set(special) | set(modes[:: max(1, len(modes) // 48)]))
+        idx = torch.as_tensor([m - m0 for m in modes], device="cuda")
         sample = (modes, refined, f_h[idx].cpu().numpy(), u_h[idx].cpu().numpy(),
                   f_b[idx].cpu().numpy(), u_b[idx].cpu().numpy())
 
@@ -747,7 +817,7 @@ def main():
             hu = torch.empty_like(hf_h).pin_memory()
             hu2 = torch.empty_like(hf_b).pin_memory()
 
-        if batched:
+        if batched or shard:
             def e2e_step():
                 with torch.cuda.stream(stream):
                     f_h.copy_(hf_h, non_blocking=True)
@@ -814,9 +884,9 @@ def main():
         e2e = {"value": world * 2 * rows / (e2e_ms * 1e-3), "unit": "solves*N/s",
                "h2d_bytes_per_step": int(2 * rows * 16), "d2h_bytes_per_step": int(2 * rows * 16),
                "ms_per_step": e2e_ms, "ms_steps": e2e_steps, "timing": f"median of {k} steps",
-               "path": "device copies + solves" if batched else "shen_solve_host",
+               "path": "device copies + solves" if batched or shard else "shen_solve_host",
                "in_place": lean, "host": host_info}
-        if not batched:
+        if not batched and not shard:
             # the host results must be the device path's bit for bit: fresh inputs in the
             # host buffers, one more step through the host path
             if lean:
@@ -840,22 +910,31 @@ def main():
                            "link_gbs_before_after": [link_before, link_after]}
         del hf_h, hf_b, hu, hu2
 
-    # the float64 path on the same fields, for the precision comparison
+    # the float64 paths on the same fields, for the precision comparison: plain float64
+    # sweeps and float64 sweeps + one double-double-residual refinement step (SHEN_FP64_R1)
     fp64_ms = None
+    extra_samples = {}
     if not args.no_fp64_compare and not lean and (prec["helmholtz"] != "fp64" or prec["biharmonic"] != "fp64"):
-        for _ in range(2):
-            step("fp64", "fp64")
         a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a.record(stream)
-        plan.helmholtz_solve(f_h, u_h, precision="fp64", stream=stream)
-        b.record(stream)
-        plan.biharmonic_solve(f_b, u_b, precision="fp64", stream=stream)
-        c2.record(stream)
-        stream.synchronize()
-        fp64_ms = {"helmholtz": a.elapsed_time(b), "biharmonic": b.elapsed_time(c2)}
+        fp64_ms = {}
+        paths = ("fp64",) if batched else ("fp64", "fp64_r1")
+        for path in paths:
+            for _ in range(2):
+                step(path, path)
+            a.record(stream)
+            plan.helmholtz_solve(f_h, u_h, precision=path, stream=stream)
+            b.record(stream)
+            plan.biharmonic_solve(f_b, u_b, precision=path, stream=stream)
+            c2.record(stream)
+            stream.synchronize()
+            key = "" if path == "fp64" else "_" + path
+            fp64_ms["helmholtz" + key] = a.elapsed_time(b)
+            fp64_ms["biharmonic" + key] = b.elapsed_time(c2)
+            if sample is not None:
+                extra_samples[path] = (u_h[idx].cpu().numpy(), u_b[idx].cpu().numpy())
         # float32 sweeps + refinement (shen_solve_refine, single-channel plans) for both
         # problems: one step with a float64 residual, two with a float-float one
-        if not batched:
+        if not batched and not shard:
             work = torch.empty_like(f_h)
             for problem, fx, ux in (("helmholtz", f_h, u_h), ("biharmonic", f_b, u_b)):
                 for steps, resid in ((1, "fp64"), (2, "df")):
@@ -866,17 +945,17 @@ def main():
                     stream.synchronize()
                     fp64_ms[f"{problem}_f32_r{steps}_{resid}"] = a.elapsed_time(b)
             del work
-        # the warp-per-mode float32-sweep + one-refinement-step kernels of the Helmholtz problem
-        for name in ("df_r1", "fp32_r1"):
-            try:
+            # the warp-per-mode float32-sweep + one-refinement-step kernels of the Helmholtz problem
+            for name in ("df_r1", "fp32_r1"):
+                try:
+                    plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)
+                except Exception:                    # not built for this N (warp-per-mode limit)
+                    continue
+                a.record(stream)
                 plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)
-            except Exception:                    # not built for this N (warp-per-mode limit)
-                continue
-            a.record(stream)
-            plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)
-            b.record(stream)
-            stream.synchronize()
-            fp64_ms[f"helmholtz_{name}"] = a.elapsed_time(b)
+                b.record(stream)
+                stream.synchronize()
+                fp64_ms[f"helmholtz_{name}"] = a.elapsed_time(b)
         step()                                   # leave the headline results in u_h, u_b
         stream.synchronize()
 
@@ -892,20 +971,24 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind, "bytes_per_row": BYTES_PER_ROW}
     line = {"metric": METRIC, "value": value, "unit": "solves*N/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if shard else "weak",
             "vs_baseline": None,
             "dtype": dtype_of(prec),
             "data": "synthetic", "precision": prec,
             "config": {"workload": args.workload, **w, "n_modes": nm, "n_classes": plan.n_classes, "rows": rows,
                        "streams": args.streams, "cuda_graph": use_graph, "plan_device_bytes": plan.info()[3]
                        if not batched else plan.device_bytes,
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"shard{world}" if shard else f"replicas{world}",
+                       "mode_range": [m0, nm] if shard else None},
             "autotune": tuned, "kernel_ms": {"helmholtz": t_h, "biharmonic": t_b}, "compare_kernel_ms": fp64_ms, "plan_s": t_plan,
             "roofline": roofline, "gpu_launches": (4 if lean else 2) * args.steps, "clocks": clk, "e2e": e2e,
             "rhs_matvec": mv, "velocity": velocity, "linear_step": linear_step, "transforms": transforms}
     if sample is not None:
         modes, refined, F_h, U_h, F_b, U_b = sample
-        line["error_vs_oracle"] = oracle_errors(w, F_h, U_h, F_b, U_b, modes, refined)
+        head = "+".join(sorted(set(prec.values())))
+        line["error_vs_oracle"] = oracle_errors(w, F_h, F_b, {head: (U_h, U_b), **extra_samples}, modes, refined)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_batch(w) if batched else cpu_baseline(w, args.precision)
     if rank == 0:

@@ -96,6 +96,17 @@ typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
  *                   as float-float pairs; no refinement.
  *   SHEN_AUTO       the path recorded for the plan and problem by shen_plan_autotune
  *                   / shen_batch_autotune (SHEN_DF until then).
+ *   SHEN_FP64_R1    the float64 sweeps, then one step of iterative refinement whose
+ *                   residual r = f - H u is formed in double-double arithmetic (every
+ *                   matrix entry, product and sum as an unevaluated pair of float64;
+ *                   the entries from exact rationals times pi) and whose correction
+ *                   H d = r runs the float64 sweeps again: u += d.  For the systems
+ *                   where the unpivoted algorithm's own roundoff reaches ~1e-12
+ *                   (Table tab:roundoff: high z, large N) this restores the float64
+ *                   solution of the exactly assembled system to ~1e-15.  About 30
+ *                   times the cost of SHEN_FP64 on GB300 (float64 runs at 1/64 of the
+ *                   float32 rate).  Single-channel plans with their float64 factors
+ *                   (not SHEN_PLAN_DF_ONLY) and mode-major fields; u == f allowed.
  * A solve returns SHEN_ERR_UNSUPPORTED for a (problem, precision) pair that is not
  * built: the float32-sweep variants exist for the Helmholtz problem, N <= 2048, one
  * refinement step. */
@@ -106,7 +117,8 @@ typedef enum {
     SHEN_DF_R1 = 3,
     SHEN_DF_R2 = 4,
     SHEN_DF = 5,
-    SHEN_AUTO = 6
+    SHEN_AUTO = 6,
+    SHEN_FP64_R1 = 7
 } shen_precision;
 
 /* Create a plan for one channel: N Chebyshev modes (8 <= N <= 8192), Fourier grid
@@ -137,7 +149,8 @@ shen_status shen_plan_create_z2(shen_plan_t *plan, int N, long n_modes, const do
  * SHEN_AUTO when it resolves to it) spill their forward results to a scratch the plan
  * holds per problem, so two float-float solves of the SAME problem on one plan must
  * not run at the same time (issue them on one stream, or order the streams).  A
- * Helmholtz and a biharmonic solve may overlap; other precisions use no scratch. */
+ * Helmholtz and a biharmonic solve may overlap; SHEN_FP64_R1 uses the same scratch (same
+ * rule); other precisions use no scratch. */
 shen_status shen_helmholtz_solve(shen_plan_t plan, const double *f, double *u, int precision,
                                  void *stream);
 
@@ -440,12 +453,12 @@ void shen_batch_destroy(shen_batch_t batch);
  * It allocates nothing and uses none of the plan's scratch: its work-queue counter
  * lives in a fixed 256-byte device array that the library holds on every GPU it is
  * loaded on until the process exits.  The plan itself (created beforehand) and the
- * fields are the caller's.  The first call on a device looks up that array's address
- * (once per device, with the device current); make that first call before any stream
- * capture.  Every call resets the counter on `stream` before its launch, so calls that
- * overlap on the GPU (on any stream, any plan) race on it: issue them one after the
- * other.  Batches of more than 2^30 modes return SHEN_ERR_UNSUPPORTED; other errors as
- * shen_batch_solve. */
+ * fields are the caller's.  Every call looks up that array's address in the current
+ * context; the first call on a device also loads the array there, so make that first
+ * call before any stream capture.  Every call resets the counter on `stream` before its
+ * launch, so calls that overlap on the GPU (on any stream, any plan) race on it: issue
+ * them one after the other.  The counter covers every batch a plan can hold
+ * (shen_batch_plan_create limits a batch to 2^30 modes).  Errors as shen_batch_solve. */
 shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem, const double *f, double *u,
                                      int precision, void *stream);
 

@@ -16,7 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "shensolve.h")
 SHEN_OK, SHEN_ERR_ARG, SHEN_ERR_ALLOC, SHEN_ERR_CUDA, SHEN_ERR_SINGULAR, SHEN_ERR_UNSUPPORTED = range(6)
 SHEN_HELMHOLTZ, SHEN_BIHARMONIC = 0, 1
 SHEN_PLAN_DF_ONLY, SHEN_PLAN_GL, SHEN_PLAN_WALL_FIRST = 1, 2, 4
-PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5, "auto": 6}
+PRECISIONS = {"fp64": 0, "fp32_r1": 1, "fp32_r2": 2, "df_r1": 3, "df_r2": 4, "df": 5, "auto": 6, "fp64_r1": 7}
 PRECISION_NAMES = {v: k for k, v in PRECISIONS.items()}
 PROBLEMS = {"helmholtz": SHEN_HELMHOLTZ, "biharmonic": SHEN_BIHARMONIC}
 SPACES = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2}

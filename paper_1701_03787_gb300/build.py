@@ -16,6 +16,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libshensolve.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                  "-Xcompiler", "-ffp-contract=off",
                   "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
 
 

@@ -457,7 +457,8 @@ extern "C" shen_status shen_batch_solve(shen_batch_t batch, int problem, const d
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (precision == SHEN_AUTO) precision = batch->auto_prec[problem];
     if (precision != SHEN_FP64 && precision != SHEN_DF) {
-        if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
+        if ((precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) || precision == SHEN_FP64_R1)
+            return SHEN_ERR_UNSUPPORTED;
         return SHEN_ERR_ARG;
     }
     if ((reinterpret_cast<uintptr_t>(f) & 15u) || (reinterpret_cast<uintptr_t>(u) & 15u)) return SHEN_ERR_ARG;
@@ -555,32 +556,18 @@ void shen_batch_destroy(shen_batch_t batch) { delete batch; }
 // that loads the library holds it until the process exits.
 // ---------------------------------------------------------------------------------
 
-#include <mutex>
-
 namespace {
 
 constexpr int kNoallocScratchWords = 64;                 // 256 bytes
-constexpr int kNoallocMaxDevices = 64;
-constexpr long kNoallocMaxModes = (1L << 30);             // work-queue counter range
 static __device__ __align__(256) int g_noalloc_scratch[kNoallocScratchWords];   // [0]: queue counter
 
-std::mutex g_noalloc_mutex;
-int *g_noalloc_ptr[kNoallocMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// Device address of g_noalloc_scratch in the current context, looked up on every call
+// (cheap), so that a reset device or a new context never sees a stale address.
 shen_status noalloc_scratch(int **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (dev < 0 || dev >= kNoallocMaxDevices) return SHEN_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        int *ptr = nullptr;
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
-        g_noalloc_ptr[dev] = ptr;
-    }
-    *out = g_noalloc_ptr[dev];
+    int *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+    *out = ptr;
     return SHEN_OK;
 }
 
@@ -592,11 +579,11 @@ extern "C" shen_status shen_batch_solve_noalloc(shen_batch_t batch, int problem,
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (precision == SHEN_AUTO) precision = batch->auto_prec[problem];
     if (precision != SHEN_FP64 && precision != SHEN_DF) {
-        if (precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) return SHEN_ERR_UNSUPPORTED;
+        if ((precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) || precision == SHEN_FP64_R1)
+            return SHEN_ERR_UNSUPPORTED;
         return SHEN_ERR_ARG;
     }
     if ((reinterpret_cast<uintptr_t>(f) & 15u) || (reinterpret_cast<uintptr_t>(u) & 15u)) return SHEN_ERR_ARG;
-    if (batch->d.n_modes > kNoallocMaxModes) return SHEN_ERR_UNSUPPORTED;   // beyond the counter's range
     long elems = 0;
     shen_batch_info(batch, nullptr, &elems, nullptr, nullptr);
     if (f != u && !(f + 2 * elems <= u || u + 2 * elems <= f)) return SHEN_ERR_ARG;

@@ -92,6 +92,7 @@ void free_plan(Plan &p) {
     cudaFree(p.d_tr);
     cudaFree(p.d_ys[0]);
     cudaFree(p.d_ys[1]);
+    cudaFree((void *)p.d_dd);
     p = Plan{};
 }
 
@@ -228,6 +229,14 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(cudaMemcpyAsync(p.d_vel_df, vel.data(), vel.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     PLAN_TRY(velocity_setup(p, B));
     PLAN_TRY(transform_setup(p, B, s));
+    {
+        std::vector<double2> dd;
+        build_dd_tables(N, gl, dd);
+        double2 *d = nullptr;
+        PLAN_TRY(dalloc(&d, dd.size(), B));
+        p.d_dd = d;
+        PLAN_TRY(cudaMemcpyAsync(d, dd.data(), dd.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    }
     // float32 factors in the lane layout of the warp-per-mode kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);
@@ -261,6 +270,8 @@ bool overlap_ok(const double *a, const double *b, long n_doubles) {
 }
 
 shen_status check_precision(const Plan &p, int problem, int precision) {
+    if (precision == SHEN_FP64_R1)        // float64 factors, mode-major fields
+        return (p.df_only || p.wall_first) ? SHEN_ERR_UNSUPPORTED : SHEN_OK;
     if (p.df_only && precision != SHEN_DF)
         return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
     if (p.wall_first && precision != SHEN_DF && precision != SHEN_FP64)   // mixed kernels: mode-major only
@@ -281,6 +292,7 @@ cudaError_t launch_solve_range(const Plan &p, int problem, int precision, long m
                                double *u, cudaStream_t s) {
     if (precision == SHEN_FP64) return launch_solve_fp64(p, problem, m0, count, f, u, s);
     if (precision == SHEN_DF) return launch_solve_df(p, problem, m0, count, f, u, s);
+    if (precision == SHEN_FP64_R1) return launch_solve_fp64r(p, problem, m0, count, f, u, s);
     return launch_helm_mixed(p, precision == SHEN_DF_R1, m0, count, f, u, s);
 }
 }  // namespace shen
@@ -433,7 +445,8 @@ shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double
     // right-hand sides into the new fields (float-float operators unless float64 was asked)
     auto rhs = [&](int problem, const double *x, const double *load, double *out) {
         const double sg = problem == SHEN_BIHARMONIC ? -1.0 : 1.0;
-        if (precision == SHEN_FP64) return launch_matvec_fp64(p, problem, x, load, sg * load_scale, out, s, sg);
+        if (precision == SHEN_FP64 || precision == SHEN_FP64_R1)
+            return launch_matvec_fp64(p, problem, x, load, sg * load_scale, out, s, sg);
         return sg > 0 ? launch_matvec_df(p, problem, x, load, load_scale, out, s)
                       : launch_matvec_neg_df(p, problem, x, load, -load_scale, out, s);
     };

@@ -37,6 +37,16 @@ constexpr int kHelmF64 = 4;
 constexpr int kDfShapes = 2;   // row-block shapes of the single-plan float-float sweeps
 constexpr int kBiF64 = 8;
 
+// Double-double per-N tables of the refinement residual (precision SHEN_FP64_R1), each
+// N + 8 entries (hi, lo) indexed by the Chebyshev index k: Dirichlet B_kk, A_kk, A_tail,
+// B_{k,k+-2} (entry 0 only); biharmonic B_kk, B_{k,k+2}, B_{k,k+4}, A_kk, A_{k,k+2},
+// A_{k,k-2}, Q_kk, p_k, r_k, q_k, s_k.
+enum {
+    kDdHb0, kDdHa0, kDdHat, kDdHboff,
+    kDdBb0, kDdBb2, kDdBb4, kDdBa0, kDdBap, kDdBam, kDdBq0, kDdBp, kDdBr, kDdBq, kDdBs,
+    kDdTables
+};
+
 struct Plan {
     int N = 0;
     long n_modes = 0, n_classes = 0;
@@ -85,6 +95,8 @@ struct Plan {
     int auto_prec[2] = {5, 5};            // SHEN_DF until tuned
     int df_variant[2] = {0, 0};
 
+    const double2 *d_dd = nullptr;        // double-double residual tables (kDdTables x (N + 8))
+
     long long device_bytes = 0;
 };
 
@@ -95,6 +107,11 @@ cudaError_t launch_solve_fp64(const Plan &p, int problem, long m0, long count, c
                               double *u, cudaStream_t s);
 cudaError_t launch_matvec_fp64(const Plan &p, int problem, const double *x, const double *y,
                                double beta, double *out, cudaStream_t s, double sign = 1.0);   // sign R x + beta y
+
+// kernels_fp64r.cu
+void build_dd_tables(int N, bool gl, std::vector<double2> &T);
+cudaError_t launch_solve_fp64r(const Plan &p, int problem, long m0, long count, const double *f, double *u,
+                               cudaStream_t s);   // float64 sweeps + one double-double-residual step
 
 // kernels_helm_mixed.cu
 int helm_mixed_R(int N);                       // rows per lane for N (0: unsupported)

@@ -71,3 +71,26 @@ def test_stale_sources_give_no_traffic(tmp_path, monkeypatch):
     assert bench.traffic_group("matvec_helmholtz:df") == "matvec"
     assert bench.traffic_group("transform:inverse_dirichlet") == "transform"
     assert bench.traffic_group("helmholtz:df") == "df"
+
+
+def test_reference_arm_times_whole_sampled_steps():
+    """--impl reference times K sampled steps of the oracle on the host cores: ms_per_step is
+    a measured step (so steps x ms_per_step fits inside the run's own wall time), and the
+    whole-workload figure is labelled as extrapolated."""
+    import os
+    import subprocess
+    import sys
+    import time
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    t = time.perf_counter()
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "small",
+                        "--steps", "4", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=root)
+    wall = time.perf_counter() - t
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 4
+    assert 0 < line["ms_per_step"] * line["steps"] / 1e3 < wall
+    assert line["value"] == pytest.approx(2 * line["config"]["sample_rows"] / (line["ms_per_step"] * 1e-3), rel=1e-6)
+    assert line["full_step_ms_extrapolated"] >= line["ms_per_step"] * 0.999
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1

@@ -7,10 +7,12 @@ Bars (per-mode relative L2):
     floor of the residual's arithmetic;
   - float64 residual: one step and two steps meet the reduced-precision bar (1e-10) for
     both problems;
-  - float-float residual: the Helmholtz problem meets 1e-10; the biharmonic operator's Q
-    tail (p_k q_j + r_k s_j) cancels between its two terms, so its float-float residual
-    is resolved to ~1e-12 of |f| (shen_residual's documented floor), which the solve
-    amplifies to ~1e-10: checked against 5e-10."""
+  - float-float residual: the Helmholtz problem meets 1e-10.  The biharmonic one does NOT
+    meet it at N = 1024: its residual is resolved to ~2^-48 of the terms of H u, which
+    cancel by orders of magnitude at high z (the mass and stiffness stencils applied to a
+    smooth solution), and the solve amplifies that floor to ~1e-10 (measured 1.3e-10 on
+    the 1024 x 1024 grid).  That case is held to the same 1e-10 bar and marked as an
+    expected failure, so a run reports it as failing the bar."""
 import numpy as np
 import pytest
 
@@ -31,8 +33,11 @@ def _errs(plan, problem, f, U, modes, Nx, Nz, N, nu, dt):
 @pytest.mark.parametrize("problem", ["helmholtz", "biharmonic"])
 @pytest.mark.parametrize("residual", ["fp64", "df"])
 @pytest.mark.parametrize("N,Nx,Nz,nu,dt", [(128, 64, 64, 1 / 180, 5e-4), (1024, 256, 256, 1 / 2000, 1e-4)])
-def test_refine_steps(problem, residual, N, Nx, Nz, nu, dt):
+def test_refine_steps(problem, residual, N, Nx, Nz, nu, dt, request):
     import torch
+    if problem == "biharmonic" and residual == "df" and N >= 1024:
+        request.applymarker(pytest.mark.xfail(
+            reason="float-float residual of the biharmonic operator: floor near the 1e-10 bar"))
     with Plan(N, Nx, Nz, nu, dt) as plan:
         f = inputs.rhs_torch(plan.n_modes, N, seed=N + 31)
         z2 = so.mode_z2(Nx, Nz)
@@ -51,8 +56,7 @@ def test_refine_steps(problem, residual, N, Nx, Nz, nu, dt):
             worst.append(_errs(plan, problem, f, U, modes, Nx, Nz, N, nu, dt).max())
     assert worst[0] <= 1e-3, worst
     assert worst[1] <= 1e-3 * worst[0], worst                       # one step contracts
-    bar = 5e-10 if (problem == "biharmonic" and residual == "df") else 1e-10
-    assert worst[1] <= bar and worst[2] <= bar, worst
+    assert worst[1] <= 1e-10 and worst[2] <= 1e-10, worst
 
 
 def test_refine_arguments():
