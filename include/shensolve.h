@@ -312,8 +312,8 @@ shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, l
  * bar against the float64 oracle in the library's parity tests:
  *   Helmholtz:  SHEN_FP64, SHEN_DF, SHEN_DF_R1, SHEN_FP32_R1;
  *   biharmonic: SHEN_FP64, SHEN_DF.
- * Each float-float candidate is timed in both of its row-block shapes (rows each
- * thread keeps in flight; the shapes give identical results).  The chosen shape then
+ * Each float-float candidate is timed in each of its shapes (see shen_plan_set_shape;
+ * shapes 2 and 3 on mode-major plans only).  The chosen shape then
  * serves every float-float solve of the plan and problem.  No candidate changes the
  * method or its accuracy class beyond that bar.
  *
@@ -345,13 +345,24 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
 shen_status shen_solve_refine(shen_plan_t plan, int problem, const double *f, double *u, double *work, int steps,
                               int residual, void *stream);
 
-/* Row-block shape of the plan's float-float sweeps for `problem` (the choice
- * shen_plan_autotune makes; every shape gives the same bits):
- *   0  rows prefetched in registers, 4 (biharmonic) / 8 (Helmholtz) per block, two blocks in
- *      flight;
- *   1  the same with 4 + 4 rows (biharmonic) / 4 rows (Helmholtz) per block.
- * shen_plan_set_shape returns SHEN_ERR_ARG for another shape; the setting lasts until the
- * next call or shen_plan_autotune.  A property of the library, not of the method. */
+/* Shape of the plan's float-float sweeps for `problem` (the choice shen_plan_autotune
+ * makes):
+ *   0  one thread per (mode, parity) chain, real and imaginary parts together, rows
+ *      prefetched in registers, 4 (biharmonic) / 8 (Helmholtz) per block, two blocks in
+ *      flight; the forward result spilled to a plan scratch in global memory;
+ *   1  the same with 4 + 4 rows (biharmonic) / 4 rows (Helmholtz) per block (same bits
+ *      as 0);
+ *   2  one lane per real chain (the real or imaginary part of one parity chain), one
+ *      CTA of 4 warps per SM, the forward result of each chain kept in Tensor Memory
+ *      (its last 256 rows) and shared memory (the 224 rows before them), only the rest
+ *      spilled to global memory; each row's float-float sum renormalised once;
+ *   3  as 2 without the Tensor Memory part.
+ * Shapes 2 and 3 round differently from 0 and 1 (same terms, same order, one
+ * renormalisation per row instead of one per term): the results agree to the
+ * float-float rounding.  Mode-major plans only (SHEN_ERR_UNSUPPORTED on a
+ * SHEN_PLAN_WALL_FIRST plan).  shen_plan_set_shape returns SHEN_ERR_ARG for another
+ * shape; the setting lasts until the next call or shen_plan_autotune.  A property of the
+ * library, not of the method. */
 shen_status shen_plan_set_shape(shen_plan_t plan, int problem, int shape);
 shen_status shen_plan_get_shape(shen_plan_t plan, int problem, int *shape);
 

@@ -331,7 +331,7 @@ class Plan:
         return u
 
     def set_shape(self, problem, shape):
-        """Row-block shape (0, 1, 2) of the float-float sweeps of `problem` (same bits)."""
+        """Shape (0..3) of the float-float sweeps of `problem` (see shen_plan_set_shape)."""
         check(lib().shen_plan_set_shape(self._h, _problem(problem), int(shape)), "shen_plan_set_shape")
 
     def shape(self, problem):

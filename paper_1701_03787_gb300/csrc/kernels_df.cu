@@ -196,13 +196,14 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
     const int *order = (m0 == 0 && count == p.n_modes && !p.wall_first) ? p.d_order : nullptr;
     const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
     const int v = p.df_variant[pb];
+    if (v >= 2 && !p.wall_first) return launch_solve_df2(p, problem, v == 2, m0, count, f, u, s);
     // never more blocks than the scratch has warp slots for (df_setup sized it for this grid)
-    const unsigned g = (unsigned)std::min<long>(nblocks(2 * count, 128), p.df_grid[pb][v]);
+    const unsigned g = (unsigned)std::min<long>(nblocks(2 * count, 128), p.df_grid[pb][v & 1]);
     if (problem == SHEN_HELMHOLTZ) {
-        if (v == 0) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[0]);
+        if (v != 1) helm_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[0]);
         else helm_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[0]);
     } else {
-        if (v == 0) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[1]);
+        if (v != 1) bih_df_kernel<0><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[1]);
         else bih_df_kernel<1><<<g, 128, 0, s>>>(p, order, m0, count, f, u, p.d_ys[1]);
     }
     return cudaGetLastError();
@@ -227,13 +228,13 @@ cudaError_t df_setup(Plan &p, long long &bytes) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const void *kern[2][kDfShapes] = {{(const void *)helm_df_kernel<0>, (const void *)helm_df_kernel<1>},
+    const void *kern[2][2] = {{(const void *)helm_df_kernel<0>, (const void *)helm_df_kernel<1>},
                                       {(const void *)bih_df_kernel<0>, (const void *)bih_df_kernel<1>}};
     // a launch covers at most all the plan's chains: no more blocks than that
     const int needed = (int)std::min<long>(nblocks(2 * p.n_modes, 128), 1L << 30);
     for (int pb = 0; pb < 2; pb++) {
         int most = 1;
-        for (int v = 0; v < kDfShapes; v++) {
+        for (int v = 0; v < 2; v++) {
             int per_sm = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[pb][v], 128, 0);
             if (e != cudaSuccess) return e;

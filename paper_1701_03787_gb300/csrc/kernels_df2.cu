@@ -1,0 +1,404 @@
+// Float-float sweeps with the forward result kept on chip (row-block shape 2 of the
+// single-plan float-float solves).
+//
+// The paper's O(N) sweeps (Sec. 4: the Helmholtz odd/even LU; Algorithm LUSolveBiharmonic
+// with the tail of Eq. ab) run serially down each parity chain and back up, so the forward
+// result y of every row must be kept until the back substitution reaches it: 8 bytes per
+// row of each real chain in float-float.  The thread-per-chain kernels (shape 0 and 1) run
+// 16 warps per SM, which puts ~600 MB of y in flight and sends it through DRAM (32 of
+// their ~82 bytes per complex row).  Here:
+//   - each lane runs ONE real chain (the real or the imaginary part of one parity chain of
+//     one mode: lane = 4 j + 2 parity + part, 8 modes per warp), which halves the y each
+//     lane holds while the four lanes of a mode still read and write whole 32-byte sectors;
+//   - one CTA of 4 warps per SM (one warp per scheduler) keeps 128 chains in flight, and
+//     their y lives in Tensor Memory (256 rows per lane) and shared memory (224 rows per
+//     lane) before any of it goes to a global spill: at N = 1024 (510 rows per chain) 94 %
+//     of y stays on chip;
+//   - each row's float-float sum is accumulated with one renormalisation (sweep2.cuh),
+//     and the column, factor and spill streams are prefetched into L2 ahead of the
+//     register double-buffering, since 4 warps cannot hide DRAM latency by occupancy.
+// Same arithmetic as the other float-float shapes, same ordering of the terms within a
+// row up to the accumulation (so results agree to rounding, not bit for bit).
+#include <algorithm>
+
+#include "chains.cuh"
+#include "sweep2.cuh"
+
+namespace shen {
+namespace {
+
+using df::F2;
+using sw2::Acc;
+
+constexpr int kRB = 4;                 // rows per block (both sweeps)
+constexpr int kThreads = 128;          // 4 warps: one per SM sub-partition
+constexpr int kPfBlocks = 8;           // L2 prefetch distance, in blocks
+
+// cp.async.bulk.prefetch.L2: bring [ptr, ptr + bytes) toward L2 (a hint; 16-byte aligned
+// address, size a multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void *ptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
+// Where the forward result of block b lives: global spill [0, GB), shared memory
+// [GB, GB + SB), Tensor Memory [GB + SB, nb).
+struct Tiers {
+    int nb, GB, SB, TB;
+};
+
+__device__ __forceinline__ Tiers tiers_of(int rows_max, int tmem_blocks, int smem_blocks) {
+    Tiers t;
+    t.nb = (rows_max + kRB - 1) / kRB;
+    t.TB = min(t.nb, tmem_blocks);
+    t.SB = min(t.nb - t.TB, smem_blocks);
+    t.GB = t.nb - t.TB - t.SB;
+    return t;
+}
+
+// This lane's chain in group g of 8 modes: lane = 4 j + 2 parity + part.
+struct Lane {
+    bool active;          // the lane's mode exists
+    int par, ri;          // parity chain, real (0) / imaginary (1) part
+    int rows;             // rows of the lane's chain
+    int cls;
+    long ch;              // chain index 2 class + parity
+    long col;             // column of the mode relative to the field pointers
+};
+
+__device__ __forceinline__ Lane lane_of(const Plan &p, const int *order, long m0, long count, long g, int lane,
+                                        int n) {
+    Lane L;
+    const long it = g * 8 + (lane >> 2);
+    L.par = (lane >> 1) & 1;
+    L.ri = lane & 1;
+    L.active = it < count;
+    const long mode = L.active ? (order ? (long)order[it] : m0 + it) : m0;
+    L.col = mode - m0;
+    L.cls = p.d_mode_class[mode];
+    L.ch = 2L * L.cls + L.par;
+    L.rows = (n - L.par + 1) / 2;
+    return L;
+}
+
+// Factor rows of one block (per lane), and the forward result of the block when it comes
+// from the global spill or from Tensor Memory.
+template <int PB>
+struct FwdBuf {
+    double f[kRB];
+    float4 l[kRB];            // biharmonic (L1, L2); Helmholtz (l, -) in .x .y
+};
+
+struct BwdBuf {
+    float4 b0[kRB];           // biharmonic (1/U0, U1); Helmholtz (1/U0, U2)
+    float4 b1[kRB];           // biharmonic (U2, ta)
+    float2 b2[kRB];           // biharmonic tb
+    float2 yg[kRB];           // y from the global spill
+    uint32_t yt[2 * kRB];     // y from Tensor Memory (valid after tmem_wait_ld)
+};
+
+// One launch covers modes [m0, m0 + count) (order: the plan's class order, full plan only).
+// gsp: the per-warp global spill, GB blocks of [row][lane] float2 per warp slot.
+// TM: keep the last tmem_blocks blocks of every chain in Tensor Memory (tcols columns per CTA).
+template <int PB, bool TM>
+__global__ void __launch_bounds__(kThreads, 1)
+    df2_kernel(Plan p, const int *order, long m0, long count, const double *f, double *u, float2 *gsp,
+               int tmem_blocks, int smem_blocks, int tcols) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *tm_slot = reinterpret_cast<uint32_t *>(smem_raw);
+    float2 *ysm = reinterpret_cast<float2 *>(smem_raw + 16);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t tbase = 0;
+    if (TM) {
+        if (warp == 0) sw2::tmem_alloc(tm_slot, (uint32_t)tcols);
+        sw2::tmem_fence_before();
+        __syncthreads();
+        sw2::tmem_fence_after();
+        tbase = *tm_slot + ((uint32_t)(32 * warp) << 16);
+    }
+    const int N = p.N;
+    const int n = PB == 0 ? N - 2 : N - 4;
+    const int rows_max = (n + 1) / 2;
+    const Tiers T = tiers_of(rows_max, TM ? tmem_blocks : 0, smem_blocks);
+    const long slot = blockIdx.x * (long)(kThreads / 32) + warp;
+    const long nslots = (long)gridDim.x * (kThreads / 32);
+    float2 *gw = gsp + slot * (long)T.GB * kRB * 32;            // this warp's spill, [b][r][lane]
+    const long nch = 2 * p.n_classes;
+    const long ngroups = (count + 7) / 8;
+    const F2 zero{0.f, 0.f};
+    for (long g = slot; g < ngroups; g += nslots) {
+        const Lane L = lane_of(p, order, m0, count, g, lane, n);
+        const double *fp = f + 2 * L.col * (long)N + L.ri;        // part of element k at fp[2 k]
+        double *up = u + 2 * L.col * (long)N + L.ri;
+        // the warp's span of chains, for the L2 prefetch of factor rows
+        const int chmin = __reduce_min_sync(0xffffffffu, L.active ? (int)L.ch : 0x7fffffff);
+        const int chmax = __reduce_max_sync(0xffffffffu, L.active ? (int)L.ch : -1);
+        const int span = chmax - chmin + 1;
+        const bool pf_fac = span > 0 && span <= 64;
+        F2 h = zero;                                               // Helmholtz: alpha pi / 2
+        if (PB == 0) h = sw2::from_f64((p.d_class_z2[L.cls] + p.c) * (kPi / 2));
+
+        // ---------------------------------------------------------------- forward sweep
+        F2 y1 = zero, y2 = zero;
+        auto fload = [&](FwdBuf<PB> &B, int b) {
+            if (b >= T.nb) return;
+#pragma unroll
+            for (int r = 0; r < kRB; r++) {
+                const int i = b * kRB + r;
+                const bool ok = L.active && i < L.rows;
+                const long k = 2L * i + L.par;
+                B.f[r] = ok ? fp[2 * k] : 0.0;
+                if (PB == 0) {
+                    const float2 l = ok ? p.df_hf[(long)i * nch + L.ch] : make_float2(0.f, 0.f);
+                    B.l[r] = make_float4(l.x, l.y, 0.f, 0.f);
+                } else {
+                    B.l[r] = ok ? p.df_bf[(long)i * nch + L.ch] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            const int bp = b + kPfBlocks;
+            if (bp < T.nb) {
+                const int ip = bp * kRB;
+                // 2 kRB complex rows of the column, inside it
+                if (L.active && L.par == 0 && L.ri == 0 && 2 * ip + 2 * kRB <= N)
+                    prefetch_l2(f + 2 * L.col * (long)N + 4L * ip, 2 * kRB * 16);
+                // factor rows before the last one (the rounded-up float2 span stays inside the stream)
+                if (pf_fac && lane < kRB && ip + lane < rows_max - 1) {
+                    const long row = (long)(ip + lane) * nch + chmin;
+                    if (PB == 0) {
+                        const long a0 = row & ~1L;                 // float2 entries: 16-byte aligned start
+                        prefetch_l2(p.df_hf + a0, (uint32_t)(((row - a0 + span + 1) / 2) * 16));
+                    } else {
+                        prefetch_l2(p.df_bf + row, (uint32_t)span * 16);
+                    }
+                }
+            }
+        };
+        auto frun = [&](const FwdBuf<PB> &B, int b) {
+            if (b >= T.nb) return;
+            float yv[2 * kRB];
+#pragma unroll
+            for (int r = 0; r < kRB; r++) {
+                Acc a = sw2::acc_start(sw2::from_f64(B.f[r]));
+                if (PB == 0) {
+                    sw2::acc_sub_mul(a, F2{B.l[r].x, B.l[r].y}, y1);
+                } else {
+                    sw2::acc_sub_mul(a, F2{B.l[r].z, B.l[r].w}, y2);       // the y_{i-2} term first
+                    sw2::acc_sub_mul(a, F2{B.l[r].x, B.l[r].y}, y1);
+                }
+                const F2 y = sw2::acc_done(a);
+                y2 = y1;
+                y1 = y;
+                yv[2 * r] = y.hi;
+                yv[2 * r + 1] = y.lo;
+            }
+            if (b < T.GB) {
+#pragma unroll
+                for (int r = 0; r < kRB; r++) gw[(b * kRB + r) * 32 + lane] = make_float2(yv[2 * r], yv[2 * r + 1]);
+            } else if (b < T.GB + T.SB) {
+#pragma unroll
+                for (int r = 0; r < kRB; r++)
+                    ysm[((b - T.GB) * kRB + r) * kThreads + threadIdx.x] = make_float2(yv[2 * r], yv[2 * r + 1]);
+            } else if (TM) {
+                __syncwarp();
+                sw2::tmem_st8(tbase + 8u * (uint32_t)(b - T.GB - T.SB), yv);
+            }
+        };
+        {
+            FwdBuf<PB> A, B;
+            fload(A, 0);
+            for (int b = 0; b < T.nb; b += 2) {
+                fload(B, b + 1);
+                frun(A, b);
+                fload(A, b + 2);
+                frun(B, b + 1);
+            }
+        }
+        if (TM) sw2::tmem_wait_st();
+
+        // ---------------------------------------------------------------- back substitution
+        // biharmonic: u_i = (y_i - ta Sq - tb Ss - U2 u_{i+2} - U1 u_{i+1}) / U0,
+        //             Sq = sum_{j >= i+3} q_j u_j, Ss = sum_{j >= i+3} s_j u_j;
+        // Helmholtz:  u_i = (y_i + h u_{i+1} - U2 S) / U0, S = sum_{j > i} u_j.
+        F2 u1 = zero, u2 = zero, u3 = zero, Sq = zero, Ss = zero;
+        float2 *gwb = gsp + slot * (long)T.GB * kRB * 32;         // warp base of the spill
+        auto bload = [&](BwdBuf &B, int b) {
+            if (b < 0) return;
+#pragma unroll
+            for (int r = 0; r < kRB; r++) {
+                const int i = b * kRB + r;
+                const bool ok = L.active && i < L.rows;
+                const long o = (long)i * nch + L.ch;
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (PB == 0) {
+                    B.b0[r] = ok ? p.df_hb[o] : z4;
+                } else {
+                    B.b0[r] = ok ? p.df_bb0[o] : z4;
+                    B.b1[r] = ok ? p.df_bb1[o] : z4;
+                    B.b2[r] = ok ? p.df_bb2[o] : make_float2(0.f, 0.f);
+                }
+            }
+            if (b < T.GB) {
+#pragma unroll
+                for (int r = 0; r < kRB; r++) B.yg[r] = gw[(b * kRB + r) * 32 + lane];
+            } else if (TM && b >= T.GB + T.SB) {
+                __syncwarp();
+                sw2::tmem_ld8(tbase + 8u * (uint32_t)(b - T.GB - T.SB), B.yt);
+            }
+            const int bp = b - kPfBlocks;
+            if (bp >= 0) {
+                const int ip = bp * kRB;
+                if (pf_fac && lane < kRB && ip + lane < rows_max - 1) {
+                    const long row = (long)(ip + lane) * nch + chmin;
+                    if (PB == 0) {
+                        prefetch_l2(p.df_hb + row, (uint32_t)span * 16);
+                    } else {
+                        prefetch_l2(p.df_bb0 + row, (uint32_t)span * 16);
+                        prefetch_l2(p.df_bb1 + row, (uint32_t)span * 16);
+                        const long a0 = row & ~1L;
+                        prefetch_l2(p.df_bb2 + a0, (uint32_t)(((row - a0 + span + 1) / 2) * 16));
+                    }
+                }
+                if (bp < T.GB && lane == kRB)                      // 4 rows x 32 lanes of the spill
+                    prefetch_l2(gwb + (long)bp * kRB * 32, kRB * 32 * 8);
+            }
+        };
+        auto brun = [&](BwdBuf &B, int b) {
+            if (b < 0) return;
+            float yv[2 * kRB];
+            if (b < T.GB) {
+#pragma unroll
+                for (int r = 0; r < kRB; r++) {
+                    yv[2 * r] = B.yg[r].x;
+                    yv[2 * r + 1] = B.yg[r].y;
+                }
+            } else if (b < T.GB + T.SB) {
+#pragma unroll
+                for (int r = 0; r < kRB; r++) {
+                    const float2 v = ysm[((b - T.GB) * kRB + r) * kThreads + threadIdx.x];
+                    yv[2 * r] = v.x;
+                    yv[2 * r + 1] = v.y;
+                }
+            } else if (TM) {
+                __syncwarp();
+                sw2::tmem_wait_ld(B.yt);
+#pragma unroll
+                for (int q = 0; q < 2 * kRB; q++) yv[q] = __uint_as_float(B.yt[q]);
+            }
+#pragma unroll
+            for (int r = kRB - 1; r >= 0; r--) {
+                const int i = b * kRB + r;
+                const bool ok = L.active && i < L.rows;
+                const F2 yi{yv[2 * r], yv[2 * r + 1]};
+                F2 ui;
+                if (PB == 0) {
+                    const F2 inv0{B.b0[r].x, B.b0[r].y}, U2{B.b0[r].z, B.b0[r].w};
+                    Acc a = sw2::acc_start(yi);
+                    sw2::acc_sub_mul(a, U2, Sq);                     // Sq holds S = sum_{j > i} u_j
+                    sw2::acc_add_mul(a, h, u1);
+                    ui = sw2::mul_n(inv0, sw2::acc_done(a));
+                    if (!ok) ui = zero;
+                    Sq = df::add(Sq, ui);
+                } else {
+                    if (i + 3 < L.rows) {
+                        const float4 qv = __ldg(p.df_qs + 2 * i + L.par + 6);
+                        Sq = sw2::add_mul(Sq, F2{qv.x, qv.y}, u3);
+                        Ss = sw2::add_mul(Ss, F2{qv.z, qv.w}, u3);
+                    }
+                    const F2 inv0{B.b0[r].x, B.b0[r].y}, U1{B.b0[r].z, B.b0[r].w};
+                    const F2 U2{B.b1[r].x, B.b1[r].y}, ta{B.b1[r].z, B.b1[r].w}, tb{B.b2[r].x, B.b2[r].y};
+                    Acc a = sw2::acc_start(yi);
+                    sw2::acc_sub_mul(a, ta, Sq);
+                    sw2::acc_sub_mul(a, tb, Ss);
+                    sw2::acc_sub_mul(a, U2, u2);
+                    sw2::acc_sub_mul(a, U1, u1);
+                    ui = sw2::mul_n(inv0, sw2::acc_done(a));
+                    if (!ok) ui = zero;
+                }
+                if (ok) up[2 * (2L * i + L.par)] = sw2::to_f64(ui);
+                u3 = u2;
+                u2 = u1;
+                u1 = ui;
+            }
+        };
+        {
+            BwdBuf A, B;
+            bload(A, T.nb - 1);
+            for (int b = T.nb - 1; b >= 0; b -= 2) {
+                bload(B, b - 1);
+                brun(A, b);
+                bload(A, b - 2);
+                brun(B, b - 1);
+            }
+        }
+        // rows beyond the unknowns are written as 0
+        if (L.active && L.par == 0)
+            for (int k = n; k < N; k++) up[2L * k] = 0.0;
+    }
+    if (TM) {
+        sw2::tmem_fence_before();
+        __syncthreads();
+        sw2::tmem_fence_after();
+        if (warp == 0) sw2::tmem_dealloc(*tm_slot, (uint32_t)tcols);
+    }
+}
+
+constexpr int kSmemLimit = 232448;                                  // 227 KB per block
+constexpr int kSmemBlocks = (kSmemLimit - 16) / (kRB * kThreads * 8);   // 56 blocks of y rows per lane
+constexpr int kTmemCols = 512;
+
+inline size_t smem_bytes(int blocks) { return 16 + (size_t)blocks * kRB * kThreads * 8; }
+
+template <int PB, bool TM>
+const void *kern() {
+    return (const void *)df2_kernel<PB, TM>;
+}
+
+}  // namespace
+
+// Grid (one CTA per SM) and the per-problem spill of the on-chip float-float sweeps.
+cudaError_t df2_setup(Plan &p, long long &bytes) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const void *ks[4] = {kern<0, false>(), kern<0, true>(), kern<1, false>(), kern<1, true>()};
+    for (const void *k : ks) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(kSmemBlocks));
+        if (e != cudaSuccess) return e;
+    }
+    p.df2_grid = sms;
+    for (int pb = 0; pb < 2; pb++) {
+        const int n = pb == 0 ? p.N - 2 : p.N - 4;
+        const int nb = ((n + 1) / 2 + kRB - 1) / kRB;
+        const int GB = std::max(0, nb - kSmemBlocks);             // the larger spill: no Tensor Memory tier
+        const size_t cnt = (size_t)sms * (kThreads / 32) * GB * kRB * 32;
+        p.df2_gb[pb] = GB;
+        if (cnt == 0) continue;
+        bytes += (long long)(cnt * sizeof(float2));
+        e = cudaMalloc((void **)&p.d_gsp[pb], cnt * sizeof(float2));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_solve_df2(const Plan &p, int problem, bool tmem, long m0, long count, const double *f,
+                             double *u, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int *order = (m0 == 0 && count == p.n_modes) ? p.d_order : nullptr;
+    const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
+    const long ngroups = (count + 7) / 8;
+    const unsigned g = (unsigned)std::max(1L, std::min<long>(p.df2_grid, (ngroups + 3) / 4));
+    const int tb = tmem ? kTmemCols / 8 : 0;
+    const size_t sm = smem_bytes(kSmemBlocks);
+    float2 *gsp = p.d_gsp[pb];
+    if (pb == 0) {
+        if (tmem) df2_kernel<0, true><<<g, kThreads, sm, s>>>(p, order, m0, count, f, u, gsp, tb, kSmemBlocks, kTmemCols);
+        else df2_kernel<0, false><<<g, kThreads, sm, s>>>(p, order, m0, count, f, u, gsp, 0, kSmemBlocks, kTmemCols);
+    } else {
+        if (tmem) df2_kernel<1, true><<<g, kThreads, sm, s>>>(p, order, m0, count, f, u, gsp, tb, kSmemBlocks, kTmemCols);
+        else df2_kernel<1, false><<<g, kThreads, sm, s>>>(p, order, m0, count, f, u, gsp, 0, kSmemBlocks, kTmemCols);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace shen
+

@@ -93,6 +93,8 @@ void free_plan(Plan &p) {
     cudaFree(p.d_ys[0]);
     cudaFree(p.d_ys[1]);
     cudaFree((void *)p.d_dd);
+    cudaFree(p.d_gsp[0]);
+    cudaFree(p.d_gsp[1]);
     p = Plan{};
 }
 
@@ -221,6 +223,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(dalloc(&p.d_fac_df, df_table_floats(p), B));
     PLAN_TRY(pack_df(p, s));
     PLAN_TRY(df_setup(p, B));
+    PLAN_TRY(df2_setup(p, B));
     PLAN_TRY(dalloc(&p.d_mv_df, matvec_df_floats(p), B));
     PLAN_TRY(pack_matvec_df(p, p.d_mv_df, s));
     std::vector<float4> vel;
@@ -593,9 +596,10 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
         int prec, variant;
     };
     std::vector<Cand> cands;
-    for (Cand c : {Cand{SHEN_FP64, 0}, Cand{SHEN_DF, 0}, Cand{SHEN_DF, 1}, Cand{SHEN_DF_R1, 0},
-                   Cand{SHEN_FP32_R1, 0}})
-        if (check_precision(p, problem, c.prec) == SHEN_OK) cands.push_back(c);
+    for (Cand c : {Cand{SHEN_FP64, 0}, Cand{SHEN_DF, 0}, Cand{SHEN_DF, 1}, Cand{SHEN_DF, 2}, Cand{SHEN_DF, 3},
+                   Cand{SHEN_DF_R1, 0}, Cand{SHEN_FP32_R1, 0}})
+        if (check_precision(p, problem, c.prec) == SHEN_OK && !(c.variant >= 2 && p.wall_first))
+            cands.push_back(c);
     cudaStream_t s = as_stream(stream);
     cudaEvent_t ev[4];
     for (int i = 0; i < 4; i++)
@@ -683,6 +687,7 @@ shen_status shen_plan_set_shape(shen_plan_t plan, int problem, int shape) {
     if (!plan) return SHEN_ERR_ARG;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (shape < 0 || shape >= kDfShapes) return SHEN_ERR_ARG;
+    if (shape >= 2 && plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     plan->p.df_variant[problem] = shape;
     return SHEN_OK;
 }

@@ -34,7 +34,8 @@ struct RowTables {
 //       U1 = U_{i,i+1}, U2 = U_{i,i+2}, ta, tb (tail U_ij = ta_i q_j + tb_i s_j,
 //       j >= i+3; Eq. ab), 0
 constexpr int kHelmF64 = 4;
-constexpr int kDfShapes = 2;   // row-block shapes of the single-plan float-float sweeps
+constexpr int kDfShapes = 4;   // shapes of the single-plan float-float sweeps (0, 1: thread per
+                               // chain; 2, 3: lane per real chain, y on chip, with / without TMEM)
 constexpr int kBiF64 = 8;
 
 // Double-double per-N tables of the refinement residual (precision SHEN_FP64_R1), each
@@ -89,13 +90,18 @@ struct Plan {
     bool wall_first = false;              // SHEN_PLAN_WALL_FIRST: fields stored Chebyshev-index-major
     // float-float kernels: fixed grid of resident blocks per [problem][shape], and the
     // per-problem spill scratch of the forward result, [warp slot][chain row][lane]
-    int df_grid[2][2] = {{0, 0}, {0, 0}};
+    int df_grid[2][2] = {{0, 0}, {0, 0}};   // shapes 0 and 1
     int f32_grid[2] = {0, 0};             // float32 sweeps of shen_solve_refine
     float4 *d_ys[2] = {nullptr, nullptr};
     int auto_prec[2] = {5, 5};            // SHEN_DF until tuned
     int df_variant[2] = {0, 0};
 
     const double2 *d_dd = nullptr;        // double-double residual tables (kDdTables x (N + 8))
+    // on-chip float-float sweeps (shapes 2 and 3): one CTA per SM, per-problem global spill of
+    // the forward results that do not fit on chip ([warp slot][block][row][lane] float2)
+    int df2_grid = 0;
+    int df2_gb[2] = {0, 0};
+    float2 *d_gsp[2] = {nullptr, nullptr};
 
     long long device_bytes = 0;
 };
@@ -112,6 +118,11 @@ cudaError_t launch_matvec_fp64(const Plan &p, int problem, const double *x, cons
 void build_dd_tables(int N, bool gl, std::vector<double2> &T);
 cudaError_t launch_solve_fp64r(const Plan &p, int problem, long m0, long count, const double *f, double *u,
                                cudaStream_t s);   // float64 sweeps + one double-double-residual step
+
+// kernels_df2.cu
+cudaError_t df2_setup(Plan &p, long long &bytes);
+cudaError_t launch_solve_df2(const Plan &p, int problem, bool tmem, long m0, long count, const double *f,
+                             double *u, cudaStream_t s);
 
 // kernels_helm_mixed.cu
 int helm_mixed_R(int N);                       // rows per lane for N (0: unsupported)

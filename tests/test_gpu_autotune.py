@@ -1,9 +1,10 @@
 """GPU tests of the autotuner and of precision "auto".
 
-The autotuner picks among paths that all meet the 1e-10 bar, and its row-block shapes
-never change the arithmetic; so after tuning, an "auto" solve must equal the solve
-with the chosen precision bit for bit, and the float-float result must be the same
-bits as before tuning.
+The autotuner picks among paths that all meet the 1e-10 bar; so after tuning, an "auto"
+solve must equal the solve with the chosen precision bit for bit.  Shapes 0 and 1 of the
+float-float sweeps run the same arithmetic (same bits); shapes 2 and 3 renormalise once per
+row instead of once per term, so a float-float result after tuning equals the one before
+it bit for bit when the tuner kept shape 0 or 1, and to the float-float rounding otherwise.
 """
 import pytest
 
@@ -32,7 +33,11 @@ def test_plan_autotune_and_auto_precision(problem):
         after = plan.solve(problem, f, precision="df")
         torch.cuda.synchronize()
         assert torch.equal(u_auto, u_named)
-        assert torch.equal(after, before)                              # shapes keep the bits
+        if plan.shape(problem) in (0, 1):
+            assert torch.equal(after, before)                          # shapes 0, 1 keep the bits
+        else:
+            d = torch.linalg.vector_norm(after - before, dim=1) / torch.linalg.vector_norm(before, dim=1)
+            assert float(d.max()) < 1e-11
         # the tuned result still meets the bar against the O(N) oracle
         z2 = so.mode_z2(48, 32)
         modes = [0, 5, plan.n_modes // 2, plan.n_modes - 1]
@@ -91,7 +96,7 @@ def test_every_shape_gives_the_same_bits(problem, N):
         n = so.n_unknowns(problem, N)
         assert max(so.rel_l2(U[i, :n], R[i, :n]) for i in range(len(modes))) < 1e-10
         with pytest.raises(ShenError):
-            plan.set_shape(problem, 2)
+            plan.set_shape(problem, 4)
 
 
 def test_autotune_rejects_in_place_and_bad_problem():
