@@ -32,13 +32,6 @@ using sw2::Acc;
 
 constexpr int kRB = 4;                 // rows per block (both sweeps)
 constexpr int kThreads = 128;          // 4 warps: one per SM sub-partition
-constexpr int kPfBlocks = 8;           // L2 prefetch distance, in blocks
-
-// cp.async.bulk.prefetch.L2: bring [ptr, ptr + bytes) toward L2 (a hint; 16-byte aligned
-// address, size a multiple of 16)
-__device__ __forceinline__ void prefetch_l2(const void *ptr, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
-}
 
 // Where the forward result of block b lives: global spill [0, GB), shared memory
 // [GB, GB + SB), Tensor Memory [GB + SB, nb).
@@ -80,33 +73,46 @@ __device__ __forceinline__ Lane lane_of(const Plan &p, const int *order, long m0
     return L;
 }
 
-// Factor rows of one block (per lane), and the forward result of the block when it comes
-// from the global spill or from Tensor Memory.
-template <int PB>
-struct FwdBuf {
-    double f[kRB];
-    float4 l[kRB];            // biharmonic (L1, L2); Helmholtz (l, -) in .x .y
-};
+// cp.async (global -> shared, bypassing registers): 8-byte copies through L1, 16-byte ones
+// to L2 only; groups committed per block and waited for in order.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int D>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(D) : "memory");
+}
 
-struct BwdBuf {
-    float4 b0[kRB];           // biharmonic (1/U0, U1); Helmholtz (1/U0, U2)
-    float4 b1[kRB];           // biharmonic (U2, ta)
-    float2 b2[kRB];           // biharmonic tb
-    float2 yg[kRB];           // y from the global spill
-    uint32_t yt[2 * kRB];     // y from Tensor Memory (valid after tmem_wait_ld)
-};
+// Per-warp streaming ring in shared memory: the rows of the next blocks of every lane's
+// chain, copied ahead with cp.async.  Forward slot: f (8 B) and the forward factors (16 B)
+// per row and lane; backward slot: the three backward factor rows (16 + 16 + 8 B) and, for
+// spilled blocks, y (8 B) per row and lane.
+constexpr int kDf = 10;                                   // forward slots: 40 rows in flight
+constexpr int kDb = 5;                                    // backward slots: 20 rows in flight
+constexpr int kFwdSlot = kRB * 32 * (8 + 16);            // 3 KB
+constexpr int kBwdSlot = kRB * 32 * (16 + 16 + 8 + 8);   // 6 KB
+constexpr int kRingBytes = (kDf * kFwdSlot > kDb * kBwdSlot) ? kDf * kFwdSlot : kDb * kBwdSlot;   // per warp
 
 // One launch covers modes [m0, m0 + count) (order: the plan's class order, full plan only).
 // gsp: the per-warp global spill, GB blocks of [row][lane] float2 per warp slot.
 // TM: keep the last tmem_blocks blocks of every chain in Tensor Memory (tcols columns per CTA).
+// Shared memory: [16 B: TMEM address][rings: 4 x kRingBytes][y tier: smem_blocks x kRB x 128 float2].
 template <int PB, bool TM>
 __global__ void __launch_bounds__(kThreads, 1)
     df2_kernel(Plan p, const int *order, long m0, long count, const double *f, double *u, float2 *gsp,
                int tmem_blocks, int smem_blocks, int tcols) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *tm_slot = reinterpret_cast<uint32_t *>(smem_raw);
-    float2 *ysm = reinterpret_cast<float2 *>(smem_raw + 16);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *ring = smem_raw + 16 + warp * kRingBytes;
+    float2 *ysm = reinterpret_cast<float2 *>(smem_raw + 16 + (kThreads / 32) * kRingBytes);
     uint32_t tbase = 0;
     if (TM) {
         if (warp == 0) sw2::tmem_alloc(tm_slot, (uint32_t)tcols);
@@ -125,64 +131,59 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long nch = 2 * p.n_classes;
     const long ngroups = (count + 7) / 8;
     const F2 zero{0.f, 0.f};
+    // ring views
+    double *rf = reinterpret_cast<double *>(ring);                                  // [kDf][kRB][32]
+    float4 *rl = reinterpret_cast<float4 *>(ring + kDf * kRB * 32 * 8);            // [kDf][kRB][32]
+    float4 *rb0 = reinterpret_cast<float4 *>(ring);                                 // [kDb][kRB][32]
+    float4 *rb1 = rb0 + kDb * kRB * 32;
+    float2 *rb2 = reinterpret_cast<float2 *>(rb1 + kDb * kRB * 32);
+    float2 *ryg = rb2 + kDb * kRB * 32;
     for (long g = slot; g < ngroups; g += nslots) {
         const Lane L = lane_of(p, order, m0, count, g, lane, n);
         const double *fp = f + 2 * L.col * (long)N + L.ri;        // part of element k at fp[2 k]
         double *up = u + 2 * L.col * (long)N + L.ri;
-        // the warp's span of chains, for the L2 prefetch of factor rows
-        const int chmin = __reduce_min_sync(0xffffffffu, L.active ? (int)L.ch : 0x7fffffff);
-        const int chmax = __reduce_max_sync(0xffffffffu, L.active ? (int)L.ch : -1);
-        const int span = chmax - chmin + 1;
-        const bool pf_fac = span > 0 && span <= 64;
         F2 h = zero;                                               // Helmholtz: alpha pi / 2
         if (PB == 0) h = sw2::from_f64((p.d_class_z2[L.cls] + p.c) * (kPi / 2));
 
         // ---------------------------------------------------------------- forward sweep
-        F2 y1 = zero, y2 = zero;
-        auto fload = [&](FwdBuf<PB> &B, int b) {
-            if (b >= T.nb) return;
+        auto fissue = [&](int b) {
+            if (b < T.nb) {
+                const int s = b % kDf;
 #pragma unroll
-            for (int r = 0; r < kRB; r++) {
-                const int i = b * kRB + r;
-                const bool ok = L.active && i < L.rows;
-                const long k = 2L * i + L.par;
-                B.f[r] = ok ? fp[2 * k] : 0.0;
-                if (PB == 0) {
-                    const float2 l = ok ? p.df_hf[(long)i * nch + L.ch] : make_float2(0.f, 0.f);
-                    B.l[r] = make_float4(l.x, l.y, 0.f, 0.f);
-                } else {
-                    B.l[r] = ok ? p.df_bf[(long)i * nch + L.ch] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            const int bp = b + kPfBlocks;
-            if (bp < T.nb) {
-                const int ip = bp * kRB;
-                // 2 kRB complex rows of the column, inside it
-                if (L.active && L.par == 0 && L.ri == 0 && 2 * ip + 2 * kRB <= N)
-                    prefetch_l2(f + 2 * L.col * (long)N + 4L * ip, 2 * kRB * 16);
-                // factor rows before the last one (the rounded-up float2 span stays inside the stream)
-                if (pf_fac && lane < kRB && ip + lane < rows_max - 1) {
-                    const long row = (long)(ip + lane) * nch + chmin;
-                    if (PB == 0) {
-                        const long a0 = row & ~1L;                 // float2 entries: 16-byte aligned start
-                        prefetch_l2(p.df_hf + a0, (uint32_t)(((row - a0 + span + 1) / 2) * 16));
+                for (int r = 0; r < kRB; r++) {
+                    const int i = b * kRB + r;
+                    const int e = (s * kRB + r) * 32 + lane;
+                    if (L.active && i < L.rows) {
+                        cp_async8(rf + e, fp + 2 * (2L * i + L.par));
+                        if (PB == 0) cp_async8(rl + e, p.df_hf + (long)i * nch + L.ch);    // into .x .y
+                        else cp_async16(rl + e, p.df_bf + (long)i * nch + L.ch);
                     } else {
-                        prefetch_l2(p.df_bf + row, (uint32_t)span * 16);
+                        rf[e] = 0.0;
+                        rl[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
             }
+            cp_async_commit();
         };
-        auto frun = [&](const FwdBuf<PB> &B, int b) {
-            if (b >= T.nb) return;
+        F2 y1 = zero, y2 = zero;
+#pragma unroll 1
+        for (int b = 0; b < kDf - 1; b++) fissue(b);
+#pragma unroll 1
+        for (int b = 0; b < T.nb; b++) {
+            fissue(b + kDf - 1);
+            cp_async_wait<kDf - 1>();
+            const int s = b % kDf;
             float yv[2 * kRB];
 #pragma unroll
             for (int r = 0; r < kRB; r++) {
-                Acc a = sw2::acc_start(sw2::from_f64(B.f[r]));
+                const int e = (s * kRB + r) * 32 + lane;
+                const float4 l = rl[e];
+                Acc a = sw2::acc_start(sw2::from_f64(rf[e]));
                 if (PB == 0) {
-                    sw2::acc_sub_mul(a, F2{B.l[r].x, B.l[r].y}, y1);
+                    sw2::acc_sub_mul(a, F2{l.x, l.y}, y1);
                 } else {
-                    sw2::acc_sub_mul(a, F2{B.l[r].z, B.l[r].w}, y2);       // the y_{i-2} term first
-                    sw2::acc_sub_mul(a, F2{B.l[r].x, B.l[r].y}, y1);
+                    sw2::acc_sub_mul(a, F2{l.z, l.w}, y2);       // the y_{i-2} term first
+                    sw2::acc_sub_mul(a, F2{l.x, l.y}, y1);
                 }
                 const F2 y = sw2::acc_done(a);
                 y2 = y1;
@@ -201,74 +202,59 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncwarp();
                 sw2::tmem_st8(tbase + 8u * (uint32_t)(b - T.GB - T.SB), yv);
             }
-        };
-        {
-            FwdBuf<PB> A, B;
-            fload(A, 0);
-            for (int b = 0; b < T.nb; b += 2) {
-                fload(B, b + 1);
-                frun(A, b);
-                fload(A, b + 2);
-                frun(B, b + 1);
-            }
         }
+        cp_async_wait<0>();
         if (TM) sw2::tmem_wait_st();
 
         // ---------------------------------------------------------------- back substitution
         // biharmonic: u_i = (y_i - ta Sq - tb Ss - U2 u_{i+2} - U1 u_{i+1}) / U0,
         //             Sq = sum_{j >= i+3} q_j u_j, Ss = sum_{j >= i+3} s_j u_j;
-        // Helmholtz:  u_i = (y_i + h u_{i+1} - U2 S) / U0, S = sum_{j > i} u_j.
-        F2 u1 = zero, u2 = zero, u3 = zero, Sq = zero, Ss = zero;
-        float2 *gwb = gsp + slot * (long)T.GB * kRB * 32;         // warp base of the spill
-        auto bload = [&](BwdBuf &B, int b) {
-            if (b < 0) return;
+        // Helmholtz:  u_i = (y_i + h u_{i+1} - U2 S) / U0, S = sum_{j > i} u_j (kept in Sq).
+        auto bissue = [&](int b) {
+            if (b >= 0) {
+                const int s = b % kDb;
 #pragma unroll
-            for (int r = 0; r < kRB; r++) {
-                const int i = b * kRB + r;
-                const bool ok = L.active && i < L.rows;
-                const long o = (long)i * nch + L.ch;
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (PB == 0) {
-                    B.b0[r] = ok ? p.df_hb[o] : z4;
-                } else {
-                    B.b0[r] = ok ? p.df_bb0[o] : z4;
-                    B.b1[r] = ok ? p.df_bb1[o] : z4;
-                    B.b2[r] = ok ? p.df_bb2[o] : make_float2(0.f, 0.f);
-                }
-            }
-            if (b < T.GB) {
-#pragma unroll
-                for (int r = 0; r < kRB; r++) B.yg[r] = gw[(b * kRB + r) * 32 + lane];
-            } else if (TM && b >= T.GB + T.SB) {
-                __syncwarp();
-                sw2::tmem_ld8(tbase + 8u * (uint32_t)(b - T.GB - T.SB), B.yt);
-            }
-            const int bp = b - kPfBlocks;
-            if (bp >= 0) {
-                const int ip = bp * kRB;
-                if (pf_fac && lane < kRB && ip + lane < rows_max - 1) {
-                    const long row = (long)(ip + lane) * nch + chmin;
-                    if (PB == 0) {
-                        prefetch_l2(p.df_hb + row, (uint32_t)span * 16);
+                for (int r = 0; r < kRB; r++) {
+                    const int i = b * kRB + r;
+                    const int e = (s * kRB + r) * 32 + lane;
+                    if (L.active && i < L.rows) {
+                        const long o = (long)i * nch + L.ch;
+                        if (PB == 0) {
+                            cp_async16(rb0 + e, p.df_hb + o);
+                        } else {
+                            cp_async16(rb0 + e, p.df_bb0 + o);
+                            cp_async16(rb1 + e, p.df_bb1 + o);
+                            cp_async8(rb2 + e, p.df_bb2 + o);
+                        }
                     } else {
-                        prefetch_l2(p.df_bb0 + row, (uint32_t)span * 16);
-                        prefetch_l2(p.df_bb1 + row, (uint32_t)span * 16);
-                        const long a0 = row & ~1L;
-                        prefetch_l2(p.df_bb2 + a0, (uint32_t)(((row - a0 + span + 1) / 2) * 16));
+                        rb0[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        rb1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        rb2[e] = make_float2(0.f, 0.f);
                     }
+                    if (b < T.GB) cp_async8(ryg + e, gw + (b * kRB + r) * 32 + lane);
                 }
-                if (bp < T.GB && lane == kRB)                      // 4 rows x 32 lanes of the spill
-                    prefetch_l2(gwb + (long)bp * kRB * 32, kRB * 32 * 8);
+            }
+            cp_async_commit();
+        };
+        F2 u1 = zero, u2 = zero, u3 = zero, Sq = zero, Ss = zero;
+        auto yload = [&](uint32_t (&yt)[2 * kRB], int b) {
+            if (TM && b >= 0 && b >= T.GB + T.SB) {
+                __syncwarp();
+                sw2::tmem_ld8(tbase + 8u * (uint32_t)(b - T.GB - T.SB), yt);
             }
         };
-        auto brun = [&](BwdBuf &B, int b) {
+        auto brun = [&](uint32_t (&yt)[2 * kRB], int b) {
             if (b < 0) return;
+            bissue(b - kDb + 1);
+            cp_async_wait<kDb - 1>();
+            const int s = b % kDb;
             float yv[2 * kRB];
             if (b < T.GB) {
 #pragma unroll
                 for (int r = 0; r < kRB; r++) {
-                    yv[2 * r] = B.yg[r].x;
-                    yv[2 * r + 1] = B.yg[r].y;
+                    const float2 v = ryg[(s * kRB + r) * 32 + lane];
+                    yv[2 * r] = v.x;
+                    yv[2 * r + 1] = v.y;
                 }
             } else if (b < T.GB + T.SB) {
 #pragma unroll
@@ -279,20 +265,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             } else if (TM) {
                 __syncwarp();
-                sw2::tmem_wait_ld(B.yt);
+                sw2::tmem_wait_ld(yt);
 #pragma unroll
-                for (int q = 0; q < 2 * kRB; q++) yv[q] = __uint_as_float(B.yt[q]);
+                for (int q = 0; q < 2 * kRB; q++) yv[q] = __uint_as_float(yt[q]);
             }
 #pragma unroll
             for (int r = kRB - 1; r >= 0; r--) {
                 const int i = b * kRB + r;
+                const int e = (s * kRB + r) * 32 + lane;
                 const bool ok = L.active && i < L.rows;
                 const F2 yi{yv[2 * r], yv[2 * r + 1]};
+                const float4 b0 = rb0[e];
                 F2 ui;
                 if (PB == 0) {
-                    const F2 inv0{B.b0[r].x, B.b0[r].y}, U2{B.b0[r].z, B.b0[r].w};
+                    const F2 inv0{b0.x, b0.y}, U2{b0.z, b0.w};
                     Acc a = sw2::acc_start(yi);
-                    sw2::acc_sub_mul(a, U2, Sq);                     // Sq holds S = sum_{j > i} u_j
+                    sw2::acc_sub_mul(a, U2, Sq);
                     sw2::acc_add_mul(a, h, u1);
                     ui = sw2::mul_n(inv0, sw2::acc_done(a));
                     if (!ok) ui = zero;
@@ -303,8 +291,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         Sq = sw2::add_mul(Sq, F2{qv.x, qv.y}, u3);
                         Ss = sw2::add_mul(Ss, F2{qv.z, qv.w}, u3);
                     }
-                    const F2 inv0{B.b0[r].x, B.b0[r].y}, U1{B.b0[r].z, B.b0[r].w};
-                    const F2 U2{B.b1[r].x, B.b1[r].y}, ta{B.b1[r].z, B.b1[r].w}, tb{B.b2[r].x, B.b2[r].y};
+                    const float4 b1 = rb1[e];
+                    const float2 b2 = rb2[e];
+                    const F2 inv0{b0.x, b0.y}, U1{b0.z, b0.w};
+                    const F2 U2{b1.x, b1.y}, ta{b1.z, b1.w}, tb{b2.x, b2.y};
                     Acc a = sw2::acc_start(yi);
                     sw2::acc_sub_mul(a, ta, Sq);
                     sw2::acc_sub_mul(a, tb, Ss);
@@ -319,16 +309,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 u1 = ui;
             }
         };
+#pragma unroll 1
+        for (int j = 0; j < kDb - 1; j++) bissue(T.nb - 1 - j);
         {
-            BwdBuf A, B;
-            bload(A, T.nb - 1);
+            uint32_t ya[2 * kRB], yb[2 * kRB];
+            yload(ya, T.nb - 1);
+#pragma unroll 1
             for (int b = T.nb - 1; b >= 0; b -= 2) {
-                bload(B, b - 1);
-                brun(A, b);
-                bload(A, b - 2);
-                brun(B, b - 1);
+                yload(yb, b - 1);
+                brun(ya, b);
+                yload(ya, b - 2);
+                brun(yb, b - 1);
             }
         }
+        cp_async_wait<0>();
         // rows beyond the unknowns are written as 0
         if (L.active && L.par == 0)
             for (int k = n; k < N; k++) up[2L * k] = 0.0;
@@ -342,10 +336,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 constexpr int kSmemLimit = 232448;                                  // 227 KB per block
-constexpr int kSmemBlocks = (kSmemLimit - 16) / (kRB * kThreads * 8);   // 56 blocks of y rows per lane
+constexpr int kSmemBlocks = (kSmemLimit - 16 - (kThreads / 32) * kRingBytes) / (kRB * kThreads * 8);   // 26
 constexpr int kTmemCols = 512;
 
-inline size_t smem_bytes(int blocks) { return 16 + (size_t)blocks * kRB * kThreads * 8; }
+inline size_t smem_bytes(int blocks) {
+    return 16 + (size_t)(kThreads / 32) * kRingBytes + (size_t)blocks * kRB * kThreads * 8;
+}
 
 template <int PB, bool TM>
 const void *kern() {
