@@ -73,12 +73,9 @@ __device__ __forceinline__ Lane lane_of(const Plan &p, const int *order, long m0
     return L;
 }
 
-// cp.async (global -> shared, bypassing registers): 8-byte copies through L1, 16-byte ones
-// to L2 only; groups committed per block and waited for in order.
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
+// cp.async (global -> shared, bypassing registers), 16 bytes at a time through L2 only, so
+// the streams do not evict the small per-N tables from L1; groups committed per block and
+// waited for in order.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src)
@@ -91,13 +88,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Per-warp streaming ring in shared memory: the rows of the next blocks of every lane's
-// chain, copied ahead with cp.async.  Forward slot: f (8 B) and the forward factors (16 B)
-// per row and lane; backward slot: the three backward factor rows (16 + 16 + 8 B) and, for
-// spilled blocks, y (8 B) per row and lane.
-constexpr int kDf = 10;                                   // forward slots: 40 rows in flight
-constexpr int kDb = 5;                                    // backward slots: 20 rows in flight
-constexpr int kFwdSlot = kRB * 32 * (8 + 16);            // 3 KB
-constexpr int kBwdSlot = kRB * 32 * (16 + 16 + 8 + 8);   // 6 KB
+// chain, copied ahead with cp.async, 16 bytes per row, lane and stream.  Forward slot: the
+// complex element of f (the lane uses its part) and the forward factors; backward slot:
+// the three backward factor rows and, for spilled blocks, y.  8-byte values are copied as
+// the aligned 16-byte pair that holds them (the pair of parities of one class for the
+// float2 factor streams, the pair of lanes 2j, 2j+1 for the spill).
+constexpr int kDf = 8;                                    // forward slots: 32 rows in flight
+constexpr int kDb = 4;                                    // backward slots: 16 rows in flight
+constexpr int kFwdSlot = kRB * 32 * (16 + 16);           // 4 KB
+constexpr int kBwdSlot = kRB * 32 * (16 + 16 + 16 + 16); // 8 KB
 constexpr int kRingBytes = (kDf * kFwdSlot > kDb * kBwdSlot) ? kDf * kFwdSlot : kDb * kBwdSlot;   // per warp
 
 // One launch covers modes [m0, m0 + count) (order: the plan's class order, full plan only).
@@ -132,12 +131,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long ngroups = (count + 7) / 8;
     const F2 zero{0.f, 0.f};
     // ring views
-    double *rf = reinterpret_cast<double *>(ring);                                  // [kDf][kRB][32]
-    float4 *rl = reinterpret_cast<float4 *>(ring + kDf * kRB * 32 * 8);            // [kDf][kRB][32]
+    double2 *rf = reinterpret_cast<double2 *>(ring);                                // [kDf][kRB][32]
+    float4 *rl = reinterpret_cast<float4 *>(ring + kDf * kRB * 32 * 16);           // [kDf][kRB][32]
     float4 *rb0 = reinterpret_cast<float4 *>(ring);                                 // [kDb][kRB][32]
     float4 *rb1 = rb0 + kDb * kRB * 32;
-    float2 *rb2 = reinterpret_cast<float2 *>(rb1 + kDb * kRB * 32);
-    float2 *ryg = rb2 + kDb * kRB * 32;
+    float4 *rb2 = rb1 + kDb * kRB * 32;
+    float4 *ryg = rb2 + kDb * kRB * 32;
     for (long g = slot; g < ngroups; g += nslots) {
         const Lane L = lane_of(p, order, m0, count, g, lane, n);
         const double *fp = f + 2 * L.col * (long)N + L.ri;        // part of element k at fp[2 k]
@@ -154,11 +153,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int i = b * kRB + r;
                     const int e = (s * kRB + r) * 32 + lane;
                     if (L.active && i < L.rows) {
-                        cp_async8(rf + e, fp + 2 * (2L * i + L.par));
-                        if (PB == 0) cp_async8(rl + e, p.df_hf + (long)i * nch + L.ch);    // into .x .y
+                        cp_async16(rf + e, fp - L.ri + 2 * (2L * i + L.par));
+                        if (PB == 0) cp_async16(rl + e, p.df_hf + (((long)i * nch + L.ch) & ~1L));
                         else cp_async16(rl + e, p.df_bf + (long)i * nch + L.ch);
                     } else {
-                        rf[e] = 0.0;
+                        rf[e] = make_double2(0.0, 0.0);
                         rl[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
@@ -178,9 +177,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int r = 0; r < kRB; r++) {
                 const int e = (s * kRB + r) * 32 + lane;
                 const float4 l = rl[e];
-                Acc a = sw2::acc_start(sw2::from_f64(rf[e]));
+                const double2 fc = rf[e];
+                Acc a = sw2::acc_start(sw2::from_f64(L.ri ? fc.y : fc.x));
                 if (PB == 0) {
-                    sw2::acc_sub_mul(a, F2{l.x, l.y}, y1);
+                    const bool odd = (L.ch & 1) != 0;          // the chain's half of the float2 pair
+                    sw2::acc_sub_mul(a, odd ? F2{l.z, l.w} : F2{l.x, l.y}, y1);
                 } else {
                     sw2::acc_sub_mul(a, F2{l.z, l.w}, y2);       // the y_{i-2} term first
                     sw2::acc_sub_mul(a, F2{l.x, l.y}, y1);
@@ -224,14 +225,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         } else {
                             cp_async16(rb0 + e, p.df_bb0 + o);
                             cp_async16(rb1 + e, p.df_bb1 + o);
-                            cp_async8(rb2 + e, p.df_bb2 + o);
+                            cp_async16(rb2 + e, p.df_bb2 + (o & ~1L));
                         }
                     } else {
                         rb0[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                         rb1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        rb2[e] = make_float2(0.f, 0.f);
+                        rb2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    if (b < T.GB) cp_async8(ryg + e, gw + (b * kRB + r) * 32 + lane);
+                    if (b < T.GB) cp_async16(ryg + e, gw + (b * kRB + r) * 32 + (lane & ~1));
                 }
             }
             cp_async_commit();
@@ -252,9 +253,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (b < T.GB) {
 #pragma unroll
                 for (int r = 0; r < kRB; r++) {
-                    const float2 v = ryg[(s * kRB + r) * 32 + lane];
-                    yv[2 * r] = v.x;
-                    yv[2 * r + 1] = v.y;
+                    const float4 v = ryg[(s * kRB + r) * 32 + lane];
+                    yv[2 * r] = (lane & 1) ? v.z : v.x;
+                    yv[2 * r + 1] = (lane & 1) ? v.w : v.y;
                 }
             } else if (b < T.GB + T.SB) {
 #pragma unroll
@@ -286,15 +287,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) ui = zero;
                     Sq = df::add(Sq, ui);
                 } else {
-                    if (i + 3 < L.rows) {
+                    {
+                        // (q, s) of column k + 6 (in the table's range for every row: N + 8 entries)
                         const float4 qv = __ldg(p.df_qs + 2 * i + L.par + 6);
-                        Sq = sw2::add_mul(Sq, F2{qv.x, qv.y}, u3);
-                        Ss = sw2::add_mul(Ss, F2{qv.z, qv.w}, u3);
+                        const F2 nq = sw2::add_mul(Sq, F2{qv.x, qv.y}, u3);
+                        const F2 ns = sw2::add_mul(Ss, F2{qv.z, qv.w}, u3);
+                        if (i + 3 < L.rows) {
+                            Sq = nq;
+                            Ss = ns;
+                        }
                     }
                     const float4 b1 = rb1[e];
-                    const float2 b2 = rb2[e];
+                    const float4 b2 = rb2[e];
                     const F2 inv0{b0.x, b0.y}, U1{b0.z, b0.w};
-                    const F2 U2{b1.x, b1.y}, ta{b1.z, b1.w}, tb{b2.x, b2.y};
+                    const F2 U2{b1.x, b1.y}, ta{b1.z, b1.w};
+                    const F2 tb = (L.ch & 1) ? F2{b2.z, b2.w} : F2{b2.x, b2.y};
                     Acc a = sw2::acc_start(yi);
                     sw2::acc_sub_mul(a, ta, Sq);
                     sw2::acc_sub_mul(a, tb, Ss);
