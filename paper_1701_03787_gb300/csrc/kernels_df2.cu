@@ -279,11 +279,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float4 b0 = rb0[e];
                 F2 ui;
                 if (PB == 0) {
+                    // u_i = inv0 (y_i - U2 S) + (inv0 h) u_{i+1}: only the last product waits for u_{i+1}
                     const F2 inv0{b0.x, b0.y}, U2{b0.z, b0.w};
                     Acc a = sw2::acc_start(yi);
                     sw2::acc_sub_mul(a, U2, Sq);
-                    sw2::acc_add_mul(a, h, u1);
-                    ui = sw2::mul_n(inv0, sw2::acc_done(a));
+                    const F2 part = sw2::mul_n(inv0, sw2::acc_done(a));
+                    const F2 w = sw2::mul_n(inv0, h);
+                    ui = sw2::add_mul(part, w, u1);
                     if (!ok) ui = zero;
                     Sq = df::add(Sq, ui);
                 } else {
@@ -302,12 +304,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const F2 inv0{b0.x, b0.y}, U1{b0.z, b0.w};
                     const F2 U2{b1.x, b1.y}, ta{b1.z, b1.w};
                     const F2 tb = (L.ch & 1) ? F2{b2.z, b2.w} : F2{b2.x, b2.y};
+                    // u_i = inv0 (y_i - ta Sq - tb Ss - U2 u_{i+2}) - (inv0 U1) u_{i+1}: only the
+                    // last product waits for u_{i+1}
                     Acc a = sw2::acc_start(yi);
                     sw2::acc_sub_mul(a, ta, Sq);
                     sw2::acc_sub_mul(a, tb, Ss);
                     sw2::acc_sub_mul(a, U2, u2);
-                    sw2::acc_sub_mul(a, U1, u1);
-                    ui = sw2::mul_n(inv0, sw2::acc_done(a));
+                    const F2 part = sw2::mul_n(inv0, sw2::acc_done(a));
+                    const F2 w = sw2::mul_n(inv0, U1);
+                    Acc c = sw2::acc_start(part);
+                    sw2::acc_sub_mul(c, w, u1);
+                    ui = sw2::acc_done(c);
                     if (!ok) ui = zero;
                 }
                 if (ok) up[2 * (2L * i + L.par)] = sw2::to_f64(ui);
