@@ -74,11 +74,18 @@ typedef enum { SHEN_HELMHOLTZ = 0, SHEN_BIHARMONIC = 1 } shen_problem;
                                   tab:matrices); default Chebyshev-Gauss.  Single and batched plans. */
 #define SHEN_PLAN_WALL_FIRST 4u /* fields stored wall-index-first, the paper's uhat(l, m, n) order (Sec. 2):
                                   element (m, k) at complex index k * n_modes + m, so each Chebyshev
-                                  index k holds all modes contiguously.  Solves (SHEN_FP64, SHEN_DF,
-                                  SHEN_AUTO resolving to them, shen_solve_modes with f, u pointing at
-                                  element (mode_begin, 0) of the full field) support it; the other
-                                  entry points return SHEN_ERR_UNSUPPORTED on such a plan.  Single
-                                  plans (shen_plan_create / _z2) only. */
+                                  index k holds all modes contiguously.  Supported by the solves
+                                  (SHEN_FP64, SHEN_DF shapes 0 and 1, SHEN_AUTO resolving to them;
+                                  shen_solve_modes with f, u pointing at element (mode_begin, 0) of
+                                  the full field), the operators (shen_rhs_matvec, _ex,
+                                  shen_mass_matvec, shen_residual), shen_velocity, shen_linear_step
+                                  and the transforms (shen_transform, and shen_transform_modes with
+                                  in, out pointing at element (mode_begin, 0)): each gives the
+                                  transpose of the mode-major result bit for bit.  The transforms
+                                  go through a chunked transpose into 128 MB of plan-owned staging.
+                                  shen_solve_host, shen_solve_refine, SHEN_FP64_R1 and the
+                                  float32-sweep precisions return SHEN_ERR_UNSUPPORTED on such a
+                                  plan.  Single plans (shen_plan_create / _z2) only. */
 
 /* Arithmetic of a solve.  All variants read and write float64 (complex128) fields and
  * use the same float64 LU factors (built once per plan); they differ in how the

@@ -85,16 +85,17 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_fp64_kernel(Plan p, cons
     if (!work_item(p, nullptr, 0, p.n_modes, w)) return;
     const int N = p.N, n = N - 2, par = w.par;
     const int rows = (n - par + 1) / 2;
-    const long base = w.col * N;
+    // element k at complex index base + k rs (mode-major: rs = 1; wall-index-first: rs = n_modes)
+    const long base = p.wall_first ? w.col : w.col * N, rs = p.wall_first ? p.n_modes : 1L;
     const double g = p.c - p.d_class_z2[w.cls];
     const double off = -kPi / 2;
     double2 S = make_double2(0.0, 0.0);                 // sum_{j >= i+1} x_j
     double2 xn = make_double2(0.0, 0.0);                // x_{i+1}
-    double2 xc = rows > 0 ? ld2(x, base + (2 * (rows - 1) + par)) : xn;   // x_i
+    double2 xc = rows > 0 ? ld2(x, base + (2 * (rows - 1) + par) * rs) : xn;   // x_i
     for (int i = rows - 1; i >= 0; i--) {
         const int k = 2 * i + par;
         S.x += xn.x; S.y += xn.y;
-        const double2 xp = i > 0 ? ld2(x, base + k - 2) : make_double2(0.0, 0.0);
+        const double2 xp = i > 0 ? ld2(x, base + (k - 2) * rs) : make_double2(0.0, 0.0);
         const double b0 = p.tab.bd0[k], a0 = p.tab.ad0[k], at = p.tab.adt[k];
         double2 r;
         r.x = g * (off * (xp.x + xn.x) + b0 * xc.x) + a0 * xc.x + at * S.x;
@@ -102,17 +103,17 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_fp64_kernel(Plan p, cons
         r.x *= sign;
         r.y *= sign;
         if (y) {
-            const double2 yi = ld2(y, base + k);
+            const double2 yi = ld2(y, base + k * rs);
             r.x = fma(beta, yi.x, r.x);
             r.y = fma(beta, yi.y, r.y);
         }
-        st2(out, base + k, r);
+        st2(out, base + k * rs, r);
         xn = xc;
         xc = xp;
     }
     if (par == 0) {
-        st2(out, base + n, make_double2(0.0, 0.0));
-        st2(out, base + n + 1, make_double2(0.0, 0.0));
+        st2(out, base + n * rs, make_double2(0.0, 0.0));
+        st2(out, base + (n + 1) * rs, make_double2(0.0, 0.0));
     }
 }
 
@@ -126,12 +127,13 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_fp64_kernel(Plan p, con
     if (!work_item(p, nullptr, 0, p.n_modes, w)) return;
     const int N = p.N, n = N - 4, par = w.par;
     const int rows = (n - par + 1) / 2;
-    const long base = w.col * N;
+    // element k at complex index base + k rs (mode-major: rs = 1; wall-index-first: rs = n_modes)
+    const long base = p.wall_first ? w.col : w.col * N, rs = p.wall_first ? p.n_modes : 1L;
     const double z2 = p.d_class_z2[w.cls];
     const double ga = p.c - 2.0 * z2, gb = z2 * (z2 - p.c);
     const RowTables &T = p.tab;
     const double2 zero = make_double2(0.0, 0.0);
-    auto X = [&](int i) { return (i >= 0 && i < rows) ? ld2(x, base + 2 * i + par) : zero; };
+    auto X = [&](int i) { return (i >= 0 && i < rows) ? ld2(x, base + (2 * i + par) * rs) : zero; };
     double2 Sq = zero, Ss = zero;                      // sums over j >= i+1
     double2 xm2 = X(rows - 3), xm1 = X(rows - 2), xc = X(rows - 1), xp1 = zero, xp2 = zero;
     for (int i = rows - 1; i >= 0; i--) {
@@ -154,15 +156,15 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_fp64_kernel(Plan p, con
         r.x *= sign;
         r.y *= sign;
         if (y) {
-            const double2 yi = ld2(y, base + k);
+            const double2 yi = ld2(y, base + k * rs);
             r.x = fma(beta, yi.x, r.x);
             r.y = fma(beta, yi.y, r.y);
         }
-        st2(out, base + k, r);
+        st2(out, base + k * rs, r);
         xp2 = xp1; xp1 = xc; xc = xm1; xm1 = xm2; xm2 = X(i - 3);
     }
     if (par == 0)
-        for (int k = n; k < N; k++) st2(out, base + k, zero);
+        for (int k = n; k < N; k++) st2(out, base + k * rs, zero);
 }
 
 inline unsigned blocks_for(long threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }

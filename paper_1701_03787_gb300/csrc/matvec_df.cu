@@ -56,12 +56,12 @@ __device__ __forceinline__ F2 acc_done(Acc acc) { return df::fast_two_sum(acc.hi
 
 __device__ __forceinline__ F2 ff(float4 v, int half) { return half ? F2{v.z, v.w} : F2{v.x, v.y}; }
 
-__device__ __forceinline__ CF2 ld_cf2(const double *col, int k) {
+__device__ __forceinline__ CF2 ld_cf2(const double *col, long k) {
     const double2 v = reinterpret_cast<const double2 *>(col)[k];
     return CF2{df::from_f64(v.x), df::from_f64(v.y)};
 }
 
-__device__ __forceinline__ void st_out(double *out, const double *y, double beta, int k, CF2 r) {
+__device__ __forceinline__ void st_out(double *out, const double *y, double beta, long k, CF2 r) {
     double2 v = make_double2(df::to_f64(r.re), df::to_f64(r.im));
     if (y) {
         const double2 yi = reinterpret_cast<const double2 *>(y)[k];
@@ -72,7 +72,10 @@ __device__ __forceinline__ void st_out(double *out, const double *y, double beta
 }
 
 struct Chain {
-    long col;        // column offset (doubles)
+    long col;        // offset of element 0 of the mode's column (doubles)
+    long rs;         // complex elements between consecutive Chebyshev indices: 1 for
+                     // mode-major fields, n_modes for wall-index-first ones
+    long mode;
     int par;
     double z2;
 };
@@ -81,7 +84,9 @@ __device__ __forceinline__ bool chain_of(const Plan &p, long tid, Chain &c) {
     if (tid >= 2 * p.n_modes) return false;
     const long mode = tid >> 1;
     c.par = (int)(tid & 1);
-    c.col = 2 * mode * p.N;
+    c.col = p.wall_first ? 2 * mode : 2 * mode * p.N;
+    c.rs = p.wall_first ? p.n_modes : 1;
+    c.mode = mode;
     c.z2 = p.d_class_z2[p.d_mode_class[mode]];
     return true;
 }
@@ -90,7 +95,7 @@ __device__ __forceinline__ bool chain_of(const Plan &p, long tid, Chain &c) {
 // (float64); the two chains of a mode (adjacent lanes) are combined at the end.
 struct Res {
     double rr = 0.0, ff = 0.0;
-    __device__ __forceinline__ void add(const double *f, int k, CF2 hu) {
+    __device__ __forceinline__ void add(const double *f, long k, CF2 hu) {
         const double2 fk = reinterpret_cast<const double2 *>(f)[k];
         const double dr = fk.x - df::to_f64(hu.re), di = fk.y - df::to_f64(hu.im);
         rr = fma(dr, dr, fma(di, di, rr));
@@ -103,7 +108,7 @@ struct Res {
         const double f2 = ff + __shfl_xor_sync(pair, ff, 1);
         if (c.par == 0) {
             const double q = f2 > 0.0 ? sqrt(r2 / f2) : (r2 > 0.0 ? INFINITY : 0.0);
-            if (rel) rel[c.col / (2 * p.N)] = q;
+            if (rel) rel[c.mode] = q;
             // non-negative doubles order like their bit patterns
             atomicMax(p.d_resmax, (unsigned long long)__double_as_longlong(q));
         }
@@ -119,6 +124,7 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
     if (!chain_of(p, blockIdx.x * (long)blockDim.x + threadIdx.x, c)) return;
     const int N = p.N, n = N - 2, par = c.par;
     const int rows = (n - par + 1) / 2;
+    const long rs = c.rs;
     const double *xc_ = x + c.col;
     const double *yc_ = y ? y + c.col : nullptr;
     constexpr int OP = MODE == 3 ? 0 : MODE;                    // operator: R_h, H_h or B
@@ -130,12 +136,12 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
     const F2 zero{0.f, 0.f};
     CF2 S{zero, zero};                                           // sum_{j >= i+1} x_j (chain rows)
     CF2 xn{zero, zero};                                          // x_{i+1}
-    CF2 xc = rows > 0 ? ld_cf2(xc_, 2 * (rows - 1) + par) : xn;  // x_i
+    CF2 xc = rows > 0 ? ld_cf2(xc_, (2 * (rows - 1) + par) * rs) : xn;  // x_i
     for (int i = rows - 1; i >= 0; i--) {
         const int k = 2 * i + par;
         S.re = df::add(S.re, xn.re);
         S.im = df::add(S.im, xn.im);
-        const CF2 xp = i > 0 ? ld_cf2(xc_, k - 2) : CF2{zero, zero};
+        const CF2 xp = i > 0 ? ld_cf2(xc_, (k - 2) * rs) : CF2{zero, zero};
         const float4 t0 = T[2 * k], t1 = T[2 * k + 1];
         // coefficient of x_k: g B_kk +- A_kk (+ for R_h, - for H_h, none for B)
         const F2 zero2{0.f, 0.f};
@@ -156,16 +162,16 @@ __global__ void __launch_bounds__(128) matvec_helmholtz_df_kernel(Plan p, const 
         r.re = acc_done(ar);
         r.im = acc_done(ai);
         if (MODE == 3) r = CF2{chains::neg(r.re), chains::neg(r.im)};
-        if (MODE != 1) st_out(oc, yc_, beta, k, r);
-        else res.add(yc_, k, r);
+        if (MODE != 1) st_out(oc, yc_, beta, k * rs, r);
+        else res.add(yc_, k * rs, r);
         xn = xc;
         xc = xp;
     }
     if (MODE == 1) {
         res.finish(p, c, rel);
     } else if (par == 0) {
-        reinterpret_cast<double2 *>(oc)[n] = make_double2(0.0, 0.0);
-        reinterpret_cast<double2 *>(oc)[n + 1] = make_double2(0.0, 0.0);
+        reinterpret_cast<double2 *>(oc)[n * rs] = make_double2(0.0, 0.0);
+        reinterpret_cast<double2 *>(oc)[(n + 1) * rs] = make_double2(0.0, 0.0);
     }
 }
 
@@ -179,6 +185,7 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
     if (!chain_of(p, blockIdx.x * (long)blockDim.x + threadIdx.x, c)) return;
     const int N = p.N, n = N - 4, par = c.par;
     const int rows = (n - par + 1) / 2;
+    const long rs = c.rs;
     const double *xc_ = x + c.col;
     const double *yc_ = y ? y + c.col : nullptr;
     constexpr int OP = MODE == 3 ? 0 : MODE;                    // operator: R_b, H_b or B
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
     Res res;
     const F2 zero{0.f, 0.f};
     const CF2 z{zero, zero};
-    auto X = [&](int i) { return (i >= 0 && i < rows) ? ld_cf2(xc_, 2 * i + par) : z; };
+    auto X = [&](int i) { return (i >= 0 && i < rows) ? ld_cf2(xc_, (2 * i + par) * rs) : z; };
     CF2 Sq = z, Ss = z;                                          // sums over chain rows >= i+1
     CF2 xm2 = X(rows - 3), xm1 = X(rows - 2), xc = X(rows - 1), xp1 = z, xp2 = z;
     for (int i = rows - 1; i >= 0; i--) {
@@ -254,8 +261,8 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
         r.re = acc_done(ar);
         r.im = acc_done(ai);
         if (MODE == 3) r = CF2{chains::neg(r.re), chains::neg(r.im)};
-        if (MODE != 1) st_out(oc, yc_, beta, k, r);
-        else res.add(yc_, k, r);
+        if (MODE != 1) st_out(oc, yc_, beta, k * rs, r);
+        else res.add(yc_, k * rs, r);
         xp2 = xp1;
         xp1 = xc;
         xc = xm1;
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(128) matvec_biharmonic_df_kernel(Plan p, const
     if (MODE == 1) {
         res.finish(p, c, rel);
     } else if (par == 0) {
-        for (int k = n; k < N; k++) reinterpret_cast<double2 *>(oc)[k] = make_double2(0.0, 0.0);
+        for (int k = n; k < N; k++) reinterpret_cast<double2 *>(oc)[k * rs] = make_double2(0.0, 0.0);
     }
 }
 

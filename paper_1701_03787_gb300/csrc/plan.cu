@@ -95,6 +95,7 @@ void free_plan(Plan &p) {
     cudaFree((void *)p.d_dd);
     cudaFree(p.d_gsp[0]);
     cudaFree(p.d_gsp[1]);
+    cudaFree(p.d_wf_stage);
     p = Plan{};
 }
 
@@ -232,6 +233,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(cudaMemcpyAsync(p.d_vel_df, vel.data(), vel.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     PLAN_TRY(velocity_setup(p, B));
     PLAN_TRY(transform_setup(p, B, s));
+    PLAN_TRY(wall_first_setup(p, B));
     {
         std::vector<double2> dd;
         build_dd_tables(N, gl, dd);
@@ -379,7 +381,6 @@ shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, c
         return precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2 ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
     if (precision == SHEN_FP64) return shen_rhs_matvec(plan, problem, x, y, beta, out, stream);
     if (!plan || !x || !out) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
@@ -394,7 +395,6 @@ shen_status shen_rhs_matvec_ex(shen_plan_t plan, int problem, const double *x, c
 shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, double *v, double *w, double *f,
                           int precision, void *stream) {
     if (!plan || !u || !g || !v || !w) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (precision == SHEN_AUTO) precision = SHEN_DF;
     if (precision != SHEN_DF)
         return precision >= SHEN_FP64 && precision <= SHEN_DF ? SHEN_ERR_UNSUPPORTED : SHEN_ERR_ARG;
@@ -420,7 +420,6 @@ shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double
                              const double *load_g, double *u_new, double *g_new, double *v, double *w,
                              int precision, void *stream) {
     if (!plan || !u_old || !g_old || !u_new || !g_new || !v || !w) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     Plan &p = plan->p;
     if (p.grid_Nz <= 0) return SHEN_ERR_UNSUPPORTED;            // the velocity step needs (m, n)
     const long nd = 2 * p.n_modes * (long)p.N;
@@ -464,7 +463,6 @@ shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double
 shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
                              double *out, void *stream) {
     if (!plan || !x || !out) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;
@@ -478,21 +476,22 @@ shen_status shen_mass_matvec(shen_plan_t plan, int problem, const double *x, con
 
 shen_status shen_transform(shen_plan_t plan, int kind, int space, const double *in, double *out, void *stream) {
     if (!plan || !in || !out) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (kind < SHEN_TRANSFORM_INVERSE || kind > SHEN_TRANSFORM_FORWARD) return SHEN_ERR_ARG;
     if (space < SHEN_SPACE_CHEBYSHEV || space > SHEN_SPACE_BIHARMONIC) return SHEN_ERR_ARG;
     const Plan &p = plan->p;
     if (!aligned16(in) || !aligned16(out)) return SHEN_ERR_ARG;
     if (!overlap_ok(in, out, 2 * p.n_modes * (long)p.N)) return SHEN_ERR_ARG;
     if (!transform_supported(p) || !transform_shape_ok(p, kind, space)) return SHEN_ERR_UNSUPPORTED;
-    SHEN_CUDA_TRY(launch_transform(p, kind, space, p.n_modes, in, out, as_stream(stream)));
+    if (p.wall_first)
+        SHEN_CUDA_TRY(launch_transform_wall_first(p, kind, space, p.n_modes, in, out, as_stream(stream)));
+    else
+        SHEN_CUDA_TRY(launch_transform(p, kind, space, p.n_modes, in, out, as_stream(stream)));
     return SHEN_OK;
 }
 
 shen_status shen_transform_modes(shen_plan_t plan, int kind, int space, long mode_begin, long mode_count,
                                  const double *in, double *out, void *stream) {
     if (!plan) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (kind < SHEN_TRANSFORM_INVERSE || kind > SHEN_TRANSFORM_FORWARD) return SHEN_ERR_ARG;
     if (space < SHEN_SPACE_CHEBYSHEV || space > SHEN_SPACE_BIHARMONIC) return SHEN_ERR_ARG;
     const Plan &p = plan->p;
@@ -501,15 +500,20 @@ shen_status shen_transform_modes(shen_plan_t plan, int kind, int space, long mod
     if (mode_count == 0) return SHEN_OK;                     // an empty range: in, out are not read
     if (!in || !out) return SHEN_ERR_ARG;
     if (!aligned16(in) || !aligned16(out)) return SHEN_ERR_ARG;
-    if (!overlap_ok(in, out, 2 * mode_count * (long)p.N)) return SHEN_ERR_ARG;
-    SHEN_CUDA_TRY(launch_transform(p, kind, space, mode_count, in, out, as_stream(stream)));
+    // the range's elements span (N - 1) n_modes + mode_count complex values on a wall-first
+    // plan (in, out point at element (mode_begin, 0)), mode_count N on a mode-major one
+    const long span = p.wall_first ? (long)(p.N - 1) * p.n_modes + mode_count : mode_count * (long)p.N;
+    if (!overlap_ok(in, out, 2 * span)) return SHEN_ERR_ARG;
+    if (p.wall_first)
+        SHEN_CUDA_TRY(launch_transform_wall_first(p, kind, space, mode_count, in, out, as_stream(stream)));
+    else
+        SHEN_CUDA_TRY(launch_transform(p, kind, space, mode_count, in, out, as_stream(stream)));
     return SHEN_OK;
 }
 
 shen_status shen_residual(shen_plan_t plan, int problem, const double *f, const double *u, double *rel,
                           void *stream) {
     if (!plan || !f || !u) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(f) || !aligned16(u) || (rel && (reinterpret_cast<uintptr_t>(rel) & 7u))) return SHEN_ERR_ARG;
     SHEN_CUDA_TRY(launch_residual_df(plan->p, problem, f, u, rel, as_stream(stream)));
@@ -534,7 +538,6 @@ shen_status shen_last_error_detail(shen_plan_t plan, double *max_rel_residual, l
 shen_status shen_rhs_matvec(shen_plan_t plan, int problem, const double *x, const double *y, double beta,
                             double *out, void *stream) {
     if (!plan || !x || !out) return SHEN_ERR_ARG;
-    if (plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
     const Plan &p = plan->p;
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (!aligned16(x) || !aligned16(out) || (y && !aligned16(y))) return SHEN_ERR_ARG;

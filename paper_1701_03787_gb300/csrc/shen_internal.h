@@ -102,6 +102,7 @@ struct Plan {
     int df2_grid = 0;
     int df2_gb[2] = {0, 0};
     float2 *d_gsp[2] = {nullptr, nullptr};
+    double2 *d_wf_stage = nullptr;        // wall-first plans: staging of the transforms (wallfirst.cu)
 
     long long device_bytes = 0;
 };
@@ -151,6 +152,12 @@ bool transform_shape_ok(const Plan &p, int kind, int space);   // the launch fit
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s);   // tables and launch shape
 cudaError_t launch_transform(const Plan &p, int kind, int space, long count, const double *in, double *out,
                              cudaStream_t s);   // count columns from in / out
+
+// wallfirst.cu
+long wall_first_chunk(const Plan &p);
+cudaError_t wall_first_setup(Plan &p, long long &bytes);
+cudaError_t launch_transform_wall_first(const Plan &p, int kind, int space, long count, const double *in,
+                                        double *out, cudaStream_t s);
 
 // matvec_df.cu
 size_t matvec_df_floats(const Plan &p);

@@ -141,12 +141,22 @@ __device__ __forceinline__ uint32_t rev4(uint32_t x, int nd) {   // reverse nd b
     uint32_t r = __brev(x) >> (32 - 2 * nd);
     return ((r & 0x55555555u) << 1) | ((r >> 1) & 0x55555555u);
 }
-__device__ __forceinline__ int dpos(int k, int lg) {
+__device__ __forceinline__ int dpos2(int k, int lg) {
     const int nd = lg >> 1;
     if ((lg & 1) == 0) return (int)rev4((uint32_t)k, nd);
     const uint32_t low = (uint32_t)k & ((1u << (lg - 1)) - 1u);
     return (int)(2u * rev4(low, nd) + ((uint32_t)k >> (lg - 1)));
 }
+// FFT length f3 2^lg (f3 = 1 or 3): with a leading radix-3 pass frequency k = 3 k' + m sits
+// in third m of the array, at the power-of-two position of k' there.
+__device__ __forceinline__ int dpos(int k, int lg, int f3) {
+    if (f3 == 1) return dpos2(k, lg);
+    const int m = k % 3;
+    return (m << lg) + dpos2(k / 3, lg);
+}
+
+__device__ __forceinline__ F2 lo2(float4 v) { return F2{v.x, v.y}; }
+__device__ __forceinline__ F2 hi2(float4 v) { return F2{v.z, v.w}; }
 
 // Thread group of one mode column: G warps (32 G threads) synchronised by the named
 // barrier `id` (ids 1 .. 15; 0 is __syncthreads).
@@ -171,15 +181,44 @@ struct Group {
     }
 };
 
-// In-place FFT of the group's column A[0 .. N): forward e^{-2 pi i jk/N}, or (INV) e^{+...},
-// unnormalised, output in dpos() order.  tw: per radix-4 pass p (span L = N / 4^p,
-// Q = L/4), entries [3 j + m - 1] = e^{-2 pi i m j 4^p / N}, j < Q, m = 1, 2, 3, passes
-// stored one after the other, so a pass reads its twiddles contiguously.
+// In-place FFT of the group's column A[0 .. NF), NF = f3 2^lg (f3 = 1 or 3): forward
+// e^{-2 pi i jk/NF}, or (INV) e^{+...}, unnormalised, output in dpos() order.
+// f3 = 3: a radix-3 decimation-in-frequency pass first (tw[0] = e^{-2 pi i/3}; tw[1 + 2 n],
+// tw[2 + 2 n] = e^{-2 pi i n/NF}, e^{-2 pi i 2n/NF}, n < Q = NF/3) splits the column into
+// three transforms of length 2^lg, which the radix-4 passes then run side by side.
+// tw (after the radix-3 part): per radix-4 pass p (span L = 2^lg / 4^p, Q = L/4), entries
+// [3 j + m - 1] = e^{-2 pi i m j 4^p / 2^lg}, j < Q, m = 1, 2, 3, passes stored one after the
+// other, so a pass reads its twiddles contiguously.
 template <bool INV, bool RAW>
-__device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
-    const int N = 1 << lg, half = N >> 1;
+__device__ void fft_dif(float4 *A, int lg, int f3, const float4 *tw, const Group &g) {
+    const int N = f3 << lg, half = N >> 1;
     int lgL = lg;
     const float4 *twp = tw;
+    if (f3 == 3) {
+        const int Q = 1 << lg;
+        const float4 om = tw[0];
+        const F2 c = lo2(om), sn = INV ? dneg(hi2(om)) : hi2(om);    // cos, sin of -+2 pi/3
+        for (int b = g.t; b < Q; b += g.nt) {
+            const Z a0 = ldz(A, b), a1 = ldz(A, b + Q), a2 = ldz(A, b + 2 * Q);
+            const Z t1 = zadd(a1, a2), t2 = zsub(a1, a2);
+            // a0 + w a1 + w^2 a2 and a0 + w^2 a1 + w a2 (w = c + i sn, w^2 = conj(w)):
+            // m + i sn t2 and m - i sn t2, m = a0 + c t1
+            const Z m = zfma(c, t1, a0);
+            const Z s = zi(Z{df::mul(t2.re, sn), df::mul(t2.im, sn)});
+            Z y1 = zadd(m, s), y2 = zsub(m, s);
+            const Z y0 = zadd(a0, t1);
+            if (b != 0) {
+                const Z w1 = ldz(tw, 1 + 2 * b), w2 = ldz(tw, 2 + 2 * b);
+                y1 = INV ? zmulc(y1, w1) : zmul(y1, w1);
+                y2 = INV ? zmulc(y2, w2) : zmul(y2, w2);
+            }
+            stz(A, b, y0);
+            stz(A, b + Q, y1);
+            stz(A, b + 2 * Q, y2);
+        }
+        twp += 1 + 2 * Q;
+        g.sync();
+    }
     for (; lgL >= 2; lgL -= 2) {
         const int lgQ = lgL - 2, Q = 1 << lgQ;
 #pragma unroll 2
@@ -222,8 +261,6 @@ __device__ void fft_dif(float4 *A, int lg, const float4 *tw, const Group &g) {
     }
 }
 
-__device__ __forceinline__ F2 lo2(float4 v) { return F2{v.x, v.y}; }
-__device__ __forceinline__ F2 hi2(float4 v) { return F2{v.z, v.w}; }
 
 // ------------------------------------------------------------------ kernel
 
@@ -261,7 +298,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 struct TrArgs {
-    int N, lg;               // Chebyshev modes; log2 of the FFT length (N, or 2 (N - 1) on Gauss-Lobatto points)
+    int N, lg, f3;           // Chebyshev modes; FFT length (N, or 2 (N - 1) on Gauss-Lobatto points) = f3 2^lg
     int G, n_groups;         // warps per mode group, groups per block
     long n_modes;
     int stride;              // float4 per buffer
@@ -284,7 +321,7 @@ constexpr int kBuffers = 2;
 template <int KIND, int SPACE, bool GL>
 __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *in, double *out) {
     extern __shared__ float4 sm[];
-    const int N = a.N, lg = a.lg, half = N >> 1, M = N - 1;
+    const int N = a.N, lg = a.lg, f3 = a.f3, half = N >> 1, M = N - 1;
     const float4 *tw = sm;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + a.n_tw);
     for (int t = threadIdx.x; t < a.n_tw; t += blockDim.x) sm[t] = __ldg(a.tw + t);
@@ -354,10 +391,10 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     if (k >= 1 && k < M) stz(A, 2 * M - k, t);
                 }
                 prefetch_next(next);
-                fft_dif<false, kRawForward>(A, lg, tw, g);
+                fft_dif<false, kRawForward>(A, lg, f3, tw, g);
                 for (int i = g.t; i < N; i += g.nt) {
                     const Z e = zadd(t0, (i & 1) ? Z{dneg(tM.re), dneg(tM.im)} : tM);
-                    y[i] = ztof64(zhalf(zadd(ldz(A, dpos(i, lg)), e)));
+                    y[i] = ztof64(zhalf(zadd(ldz(A, dpos(i, lg, f3)), e)));
                 }
                 g.sync();
                 continue;
@@ -375,10 +412,10 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 if (k != half) stz(A, N - k, zhalf(zi(zmul_raw(zadd_raw(t2, zmi(t1)), w))));
             }
             prefetch_next(next);
-            fft_dif<true, true>(A, lg, tw, g);
+            fft_dif<true, true>(A, lg, f3, tw, g);
             for (int m = g.t; m < N; m += g.nt) {
                 const int src = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
-                y[m] = ztof64(ldz(A, dpos(src, lg)));
+                y[m] = ztof64(ldz(A, dpos(src, lg, f3)));
             }
         } else {
             if (GL) {
@@ -391,7 +428,7 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     if (m >= 1 && m < M) stz(A, 2 * M - m, v);
                 }
                 prefetch_next(next);
-                fft_dif<false, kRawForward>(A, lg, tw, g);
+                fft_dif<false, kRawForward>(A, lg, f3, tw, g);
             } else {
             // values -> Makhoul order in A; R free for the next column
             for (int m = g.t; m < N; m += g.nt) {
@@ -399,12 +436,12 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 stz(A, dst, zfromf64(xs[m]));
             }
             prefetch_next(next);
-            fft_dif<false, kRawForward>(A, lg, tw, g);
+            fft_dif<false, kRawForward>(A, lg, f3, tw, g);
             // C_k (DCT-II) in place: the pair (k, N-k) is read and written by one thread at
             // positions dpos(k), dpos(N-k)
             for (int k = g.t; k <= half; k += g.nt) {
                 if (k == 0) continue;                                  // C_0 = V_0
-                const int pk = dpos(k, lg), pn = dpos(N - k, lg);
+                const int pk = dpos(k, lg, f3), pn = dpos(N - k, lg, f3);
                 const Z w = mkz(k);
                 const Z P = zmul(ldz(A, pk), w);
                 const Z Q = zmulc(ldz(A, pn), w);
@@ -413,17 +450,26 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
             }
             }
             g.sync();
-            auto C = [&](int k) { return ldz(A, dpos(k, lg)); };
+            auto C = [&](int k) { return ldz(A, dpos(k, lg, f3)); };
             if (KIND == 2 && SPACE == 0) {
                 // uhat_k = S_k / (pi c_k / 2): Gauss: C_k 2 / (N c_k) (c_0 = 2);
                 // Gauss-Lobatto: Y_k / (M c_k) (c_0 = c_M = 2); N, M powers of two
+                // (1 / M or 2 / N is a power of two for power-of-two lengths; with a factor 3
+                // it is applied as a float-float quotient)
                 if (GL) {
                     const float sc = 1.0f / (float)M;
-                    for (int k = g.t; k < N; k += g.nt)
-                        y[k] = ztof64(zpow2(C(k), (k == 0 || k == M) ? 0.5f * sc : sc));
+                    const F2 scd = ratio(1.0f, (float)M);
+                    for (int k = g.t; k < N; k += g.nt) {
+                        const float h = (k == 0 || k == M) ? 0.5f : 1.0f;
+                        y[k] = ztof64(f3 == 1 ? zpow2(C(k), h * sc) : zpow2(zscale(C(k), scd), h));
+                    }
                 } else {
                     const float sc = 2.0f / (float)N;
-                    for (int k = g.t; k < N; k += g.nt) y[k] = ztof64(zpow2(C(k), k == 0 ? 0.5f * sc : sc));
+                    const F2 scd = ratio(2.0f, (float)N);
+                    for (int k = g.t; k < N; k += g.nt) {
+                        const float h = k == 0 ? 0.5f : 1.0f;
+                        y[k] = ztof64(f3 == 1 ? zpow2(C(k), h * sc) : zpow2(zscale(C(k), scd), h));
+                    }
                 }
             } else {
                 // scalar products S_l (Algorithm fst, forwardScalar)
@@ -603,21 +649,28 @@ void mass_rows(int N, int space, int RM, std::vector<float4> &T, bool gl) {
 
 }  // namespace
 
-// Gauss points: N a power of two (FFT length N); Gauss-Lobatto points: N - 1 a power of two
-// (FFT length 2 (N - 1)).
+namespace {
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+}  // namespace
+
+// Gauss points: N a power of two or three times one (FFT length N); Gauss-Lobatto points:
+// N - 1 such a number (FFT length 2 (N - 1)).
 bool transform_supported(const Plan &p) {
     const int L = p.gl ? p.N - 1 : p.N;
-    return p.N >= 8 && L >= 8 && (L & (L - 1)) == 0;
+    return p.N >= 8 && L >= 8 && (pow2(L) || (L % 3 == 0 && pow2(L / 3)));
 }
 
 namespace {
 int fft_length(const Plan &p) { return p.gl ? 2 * (p.N - 1) : p.N; }
+int fft_f3(int NF) { return pow2(NF) ? 1 : 3; }
 }  // namespace
 
-// Number of float4 of the per-pass twiddle table: 3 Q per radix-4 pass.
-int twiddle_count(int N) {
-    int c = 0;
-    for (int lgL = ilog2(N); lgL >= 2; lgL -= 2) c += 3 * (1 << (lgL - 2));
+// Number of float4 of the per-pass twiddle table: 1 + 2 Q for a radix-3 pass (NF = 3 Q),
+// then 3 Q per radix-4 pass.
+int twiddle_count(int NF) {
+    const int f3 = fft_f3(NF);
+    int c = f3 == 3 ? 1 + 2 * (NF / 3) : 0;
+    for (int lgL = ilog2(NF / f3); lgL >= 2; lgL -= 2) c += 3 * (1 << (lgL - 2));
     return c;
 }
 
@@ -627,18 +680,26 @@ int twiddle_count(int N) {
 //   then the mass-solve rows of phi (2 RMd 3) and of psi (2 RMb 3).
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
-    const int N = p.N, NF = fft_length(p), lg = ilog2(NF);
+    const int N = p.N, NF = fft_length(p), f3 = fft_f3(NF), L2 = NF / f3, lg = ilog2(L2);
     const long double pi = 3.141592653589793238462643383279502884L;
     const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
     const int ntw = twiddle_count(NF), nmk = N / 2 + 1;
     std::vector<float4> tab;
     tab.reserve((size_t)ntw + nmk);
-    for (int lgL = lg, sh = 0; lgL >= 2; lgL -= 2, sh += 2) {
+    if (f3 == 3) {                                                     // radix-3 pass
+        tab.push_back(pair4(cosl(-2 * pi / 3), sinl(-2 * pi / 3)));
+        for (int n = 0; n < L2; n++)
+            for (int m = 1; m <= 2; m++) {
+                const long double ang = -2 * pi * (long double)(m * n) / NF;
+                tab.push_back(pair4(cosl(ang), sinl(ang)));
+            }
+    }
+    for (int lgL = lg, sh = 0; lgL >= 2; lgL -= 2, sh += 2) {           // radix-4 passes on 2^lg
         const int Q = 1 << (lgL - 2);
         for (int j = 0; j < Q; j++)
             for (int m = 1; m <= 3; m++) {
-                const long t = ((long)m * j) << sh;                    // < 3N/4
-                const long double ang = -2 * pi * (long double)t / NF;
+                const long t = ((long)m * j) << sh;                    // < 3 L2 / 4
+                const long double ang = -2 * pi * (long double)t / L2;
                 tab.push_back(pair4(cosl(ang), sinl(ang)));
             }
     }
@@ -713,7 +774,8 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, long count, con
     const int k = mass ? SHEN_TRANSFORM_SCALAR : kind;
     TrArgs a;
     a.N = N;
-    a.lg = ilog2(fft_length(p));
+    a.f3 = fft_f3(fft_length(p));
+    a.lg = ilog2(fft_length(p) / a.f3);
     a.G = p.tr_G;
     a.n_groups = p.tr_groups[k][space];
     a.n_modes = count;

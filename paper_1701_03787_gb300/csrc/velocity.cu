@@ -28,7 +28,7 @@ namespace {
 using chains::CF2;
 using df::F2;
 
-__device__ __forceinline__ CF2 ld_cf2(const double *col, int k) {
+__device__ __forceinline__ CF2 ld_cf2(const double *col, long k) {
     const double2 v = reinterpret_cast<const double2 *>(col)[k];
     return CF2{df::from_f64(v.x), df::from_f64(v.y)};
 }
@@ -55,13 +55,16 @@ __device__ void velocity_chain(const Plan &p, const float4 *T, const double *u, 
     const double z2 = m * m + nn * nn;
     if (!(z2 > 0.0)) return;                      // m = n = 0: mean flow (Eqs. v00, w00), not here
     const F2 a = df::from_f64(nn / z2), b = df::from_f64(m / z2);
-    const long col = 2 * mode * N;
+    // element k of the mode's columns at complex index k rs from col (mode-major: rs = 1;
+    // wall-index-first: rs = n_modes)
+    const long col = p.wall_first ? 2 * mode : 2 * mode * N;
+    const long rs = p.wall_first ? p.n_modes : 1L;
     const double *uc = u + col, *gc = g + col;
     double *vc = v + col, *wc = w + col;
     double *fc = fo ? fo + col : nullptr;
     const F2 zero{0.f, 0.f};
     const CF2 z{zero, zero};
-    auto U = [&](int j) { return (j >= 0 && j < nu_) ? ld_cf2(uc, j) : z; };
+    auto U = [&](int j) { return (j >= 0 && j < nu_) ? ld_cf2(uc, j * rs) : z; };
     // forward: y_i = r_i - l_i y_{i-1}, r_i = -(C u)_k, k = 2 i + par.  (Register prefetch of
     // the rows, as in the solves, made this kernel slower: its long float-float body runs
     // best in these plain rolled loops.)
@@ -91,20 +94,20 @@ __device__ void velocity_chain(const Plan &p, const float4 *T, const double *u, 
         CF2 f;
         f.re = nrm(df::mul(inv, df::add(F2{yv.x, yv.y}, df::mul(half_pi, fn.re))));
         f.im = nrm(df::mul(inv, df::add(F2{yv.z, yv.w}, df::mul(half_pi, fn.im))));
-        const CF2 gk = ld_cf2(gc, k);
+        const CF2 gk = ld_cf2(gc, k * rs);
         // v = i (a g - b f), w = -i (a f + b g);  i (x + i y) = -y + i x
         const CF2 t = lin2(a, gk, chains::neg(b), f);
         const CF2 sm = lin2(a, f, b, gk);
-        reinterpret_cast<double2 *>(vc)[k] = make_double2(-df::to_f64(t.im), df::to_f64(t.re));
-        reinterpret_cast<double2 *>(wc)[k] = make_double2(df::to_f64(sm.im), -df::to_f64(sm.re));
-        if (fc) reinterpret_cast<double2 *>(fc)[k] = make_double2(df::to_f64(f.re), df::to_f64(f.im));
+        reinterpret_cast<double2 *>(vc)[k * rs] = make_double2(-df::to_f64(t.im), df::to_f64(t.re));
+        reinterpret_cast<double2 *>(wc)[k * rs] = make_double2(df::to_f64(sm.im), -df::to_f64(sm.re));
+        if (fc) reinterpret_cast<double2 *>(fc)[k * rs] = make_double2(df::to_f64(f.re), df::to_f64(f.im));
         fn = f;
     }
     if (par == 0)
         for (int k = n; k < N; k++) {
-            reinterpret_cast<double2 *>(vc)[k] = make_double2(0.0, 0.0);
-            reinterpret_cast<double2 *>(wc)[k] = make_double2(0.0, 0.0);
-            if (fc) reinterpret_cast<double2 *>(fc)[k] = make_double2(0.0, 0.0);
+            reinterpret_cast<double2 *>(vc)[k * rs] = make_double2(0.0, 0.0);
+            reinterpret_cast<double2 *>(wc)[k * rs] = make_double2(0.0, 0.0);
+            if (fc) reinterpret_cast<double2 *>(fc)[k * rs] = make_double2(0.0, 0.0);
         }
 }
 

@@ -12,6 +12,9 @@ transform's mass solve multiplies that by the conditioning of B: it is checked t
 its defining property (B uhat reproduces the scalar products to the same bound, scaled
 by ||B||), and against the refined projection within 64 (= 2^-47 / 2^-53) times the error
 of the plain float64 dense solve of the same system.
+
+Sizes: N a power of two, and N = 3 2^p (24, 96, 1536: the FFT adds one radix-3 pass), on
+Gauss points; on Gauss-Lobatto points N - 1 of either form.
 """
 import numpy as np
 import pytest
@@ -26,7 +29,7 @@ C_BOUND = 16
 
 
 def _bound(N, in_row, scale=1.0, weight=1.0):
-    lg = int(np.log2(N))
+    lg = int(np.ceil(np.log2(N)))              # passes of the FFT (one radix-3 pass counts as one)
     return C_BOUND * (lg + 2) * U_DF * weight * scale * np.abs(in_row).sum()
 
 
@@ -46,7 +49,7 @@ def _run(plan, kind, space, X):
 WEIGHT = {"chebyshev": 1.0, "dirichlet": 2.0, "biharmonic": 4.0}
 
 
-@pytest.mark.parametrize("N", [8, 16, 32, 128, 1024])
+@pytest.mark.parametrize("N", [8, 16, 24, 32, 96, 128, 1024, 1536])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_inverse_matches_oracle(N, space):
     with Plan(N, 4, 4, 1 / 180, 1e-3) as plan:
@@ -60,7 +63,7 @@ def test_inverse_matches_oracle(N, space):
         assert err <= _bound(N, Cs[m], weight=WEIGHT[space]), (m, err)
 
 
-@pytest.mark.parametrize("N", [8, 16, 32, 128, 1024])
+@pytest.mark.parametrize("N", [8, 16, 24, 32, 96, 128, 1024, 1536])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_scalar_matches_oracle(N, space):
     with Plan(N, 4, 4, 1 / 180, 1e-3) as plan:
@@ -78,7 +81,7 @@ def _forward_cases():
     # (biharmonic, 1024) is left to the error test below: its L^-1 has a double
     # characteristic root at 1, so the chunk-local homogeneous solutions grow like the
     # chunk length and the residual is no longer bounded by u |B| |uhat|
-    return [(N, s) for N in (8, 16, 64, 128, 1024) for s in tr.SPACES if not (s == "biharmonic" and N > 128)]
+    return [(N, s) for N in (8, 16, 24, 64, 96, 128, 1024) for s in tr.SPACES if not (s == "biharmonic" and N > 128)]
 
 
 @pytest.mark.parametrize("N,space", _forward_cases())
@@ -109,7 +112,7 @@ def _f64_factor_bound(N, got, ref, f64):
     return e_got, 64 * e_64.max() + floor
 
 
-@pytest.mark.parametrize("N", [8, 64, 256, 1024])
+@pytest.mark.parametrize("N", [8, 64, 96, 192, 256, 1024])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_forward_matches_refined_projection(N, space):
     """Random values (not in the space) against the refined projection: the conditioning
@@ -121,7 +124,7 @@ def test_forward_matches_refined_projection(N, space):
     assert np.all(e <= tol), (e.max(), tol.min())
 
 
-@pytest.mark.parametrize("N", [8, 64, 1024])
+@pytest.mark.parametrize("N", [8, 64, 96, 1024, 1536])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_forward_inverts_inverse(N, space):
     """Coefficients of the workload's spectrum -> values (longdouble oracle, rounded to
@@ -188,8 +191,8 @@ def test_full_size_sampled():
 
 def test_unsupported_plans():
     import torch
-    with Plan(96, 4, 4, 1 / 180, 1e-3) as plan:             # N not a power of two
-        x = torch.zeros((plan.n_modes, 96), dtype=torch.complex128, device="cuda")
+    with Plan(80, 4, 4, 1 / 180, 1e-3) as plan:             # N neither 2^p nor 3 2^p
+        x = torch.zeros((plan.n_modes, 80), dtype=torch.complex128, device="cuda")
         with pytest.raises(ShenError) as e:
             plan.transform("inverse", "dirichlet", x)
         assert e.value.status == 5
@@ -204,7 +207,7 @@ def test_unsupported_plans():
 # Gauss-Lobatto points (N - 1 a power of two): DCT-I through the even extension
 # ---------------------------------------------------------------------------
 
-GL_N = [9, 17, 65, 129, 1025]
+GL_N = [9, 17, 25, 65, 97, 129, 1025]
 
 
 @pytest.mark.parametrize("N", GL_N)

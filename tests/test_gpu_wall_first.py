@@ -47,10 +47,64 @@ def test_wall_first_auto_and_unsupported_entry_points():
         name, ms = pw.autotune("biharmonic", f)
         assert name in ("fp64", "df")
         pw.solve("biharmonic", f, precision="auto")
-        for call in (lambda: pw.rhs_matvec("helmholtz", f), lambda: pw.transform("inverse", "dirichlet", f),
-                     lambda: pw.velocity(f, f), lambda: pw.residual("helmholtz", f, f),
-                     lambda: pw.solve("helmholtz", f, precision="df_r1")):
+        for call in (lambda: pw.solve("helmholtz", f, precision="df_r1"),
+                     lambda: pw.solve("helmholtz", f, precision="fp64_r1"),
+                     lambda: pw.solve_refine("helmholtz", f)):
             with pytest.raises(ShenError) as e:
                 call()
             assert e.value.status == 5
         torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("N,Nx,Nz", [(16, 4, 6), (128, 16, 12), (1024, 32, 32)])
+def test_wall_first_operators_velocity_transforms(N, Nx, Nz):
+    """Every other entry point on a wall-first plan gives the transpose of the mode-major
+    result bit for bit: the operators (float64 and float-float), the mass operator, the
+    residual, the velocity recovery, the linear step and every transform (whole field and a
+    mode range)."""
+    import ctypes
+    import torch
+    from paper_1701_03787_gb300 import binding
+    nu, dt = 1 / 2000, 1e-4
+    T = lambda t: t.t().contiguous()
+    with Plan(N, Nx, Nz, nu, dt) as pm, Plan(N, Nx, Nz, nu, dt, wall_first=True) as pw:
+        x = inputs.rhs_torch(pm.n_modes, N, seed=N + 11)
+        y = inputs.rhs_torch(pm.n_modes, N, seed=N + 12)
+        for problem in ("helmholtz", "biharmonic"):
+            for prec in ("fp64", "df"):
+                a = pm.rhs_matvec(problem, x, y, beta=0.5, precision=prec)
+                b = pw.rhs_matvec(problem, T(x), T(y), beta=0.5, precision=prec)
+                assert torch.equal(T(b), a), (problem, prec)
+            assert torch.equal(T(pw.mass_matvec(problem, T(x), T(y), 0.25)), pm.mass_matvec(problem, x, y, 0.25))
+            u = pm.solve(problem, x, precision="df")
+            assert torch.equal(pw.residual(problem, T(x), T(u)), pm.residual(problem, x, u))
+        um, gm = pm.solve("biharmonic", x, precision="df"), pm.solve("helmholtz", y, precision="df")
+        fm = torch.zeros_like(x)
+        vm, wm = pm.velocity(um, gm, f=fm)
+        fw = torch.zeros_like(x)
+        vw, ww = pw.velocity(T(um), T(gm), f=fw)
+        assert torch.equal(T(vw), vm) and torch.equal(T(ww), wm) and torch.equal(T(fw), fm)
+        sm = pm.linear_step(x, y, um, gm, precision="df")
+        sw = pw.linear_step(T(x), T(y), T(um), T(gm), precision="df")
+        for a, b in zip(sm, sw):
+            assert torch.equal(T(b), a)
+        L = binding.lib()
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        for kind in ("inverse", "scalar", "forward"):
+            for space in ("chebyshev", "dirichlet", "biharmonic"):
+                src = x if kind == "inverse" else pm.transform("inverse", "chebyshev", x)
+                a = pm.transform(kind, space, src)
+                b = pw.transform(kind, space, T(src))
+                assert torch.equal(T(b), a), (kind, space)
+                g = T(src)
+                pw.transform(kind, space, g, out=g)                       # in place
+                assert torch.equal(T(g), a), (kind, space)
+                # a mode range: pointers at element (mode_begin, 0) of the full wall-first field
+                m0, cnt = 3, pm.n_modes - 5
+                wsrc, wout = T(src), torch.zeros_like(T(src))
+                st = L.shen_transform_modes(pw._h, binding.TRANSFORMS[kind], binding.SPACES[space], m0, cnt,
+                                            ctypes.c_void_p(wsrc.data_ptr() + 16 * m0),
+                                            ctypes.c_void_p(wout.data_ptr() + 16 * m0), stream)
+                assert st == 0, binding.status_string(st)
+                torch.cuda.synchronize()
+                assert torch.equal(T(wout)[m0:m0 + cnt], a[m0:m0 + cnt]), (kind, space)
