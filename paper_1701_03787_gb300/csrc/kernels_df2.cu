@@ -364,8 +364,10 @@ const void *kern() {
 
 }  // namespace
 
-// Grid (one CTA per SM) and the per-problem spill of the on-chip float-float sweeps.
-cudaError_t df2_setup(Plan &p, long long &bytes) {
+// Grid of the on-chip float-float sweeps: one CTA per SM, at most one warp slot per group of
+// 8 modes.  Their global spill is allocated by df2_alloc, when a plan first selects shape 2
+// or 3 (shen_plan_set_shape, shen_plan_autotune), so plans that never use them do not hold it.
+cudaError_t df2_setup(Plan &p, long long &) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -375,17 +377,22 @@ cudaError_t df2_setup(Plan &p, long long &bytes) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(kSmemBlocks));
         if (e != cudaSuccess) return e;
     }
-    p.df2_grid = sms;
+    const long groups = (p.n_modes + 7) / 8;
+    p.df2_grid = (int)std::max(1L, std::min<long>(sms, (groups + 3) / 4));
+    return cudaSuccess;
+}
+
+cudaError_t df2_alloc(Plan &p) {
     for (int pb = 0; pb < 2; pb++) {
+        if (p.d_gsp[pb]) continue;
         const int n = pb == 0 ? p.N - 2 : p.N - 4;
         const int nb = ((n + 1) / 2 + kRB - 1) / kRB;
         const int GB = std::max(0, nb - kSmemBlocks);             // the larger spill: no Tensor Memory tier
-        const size_t cnt = (size_t)sms * (kThreads / 32) * GB * kRB * 32;
-        p.df2_gb[pb] = GB;
+        const size_t cnt = (size_t)p.df2_grid * (kThreads / 32) * GB * kRB * 32;
         if (cnt == 0) continue;
-        bytes += (long long)(cnt * sizeof(float2));
-        e = cudaMalloc((void **)&p.d_gsp[pb], cnt * sizeof(float2));
+        const cudaError_t e = cudaMalloc((void **)&p.d_gsp[pb], cnt * sizeof(float2));
         if (e != cudaSuccess) return e;
+        p.device_bytes += (long long)(cnt * sizeof(float2));
     }
     return cudaSuccess;
 }

@@ -599,6 +599,7 @@ shen_status shen_plan_autotune(shen_plan_t plan, int problem, const double *f, d
         int prec, variant;
     };
     std::vector<Cand> cands;
+    if (!p.wall_first) SHEN_CUDA_TRY(df2_alloc(p));           // shapes 2, 3 are candidates
     for (Cand c : {Cand{SHEN_FP64, 0}, Cand{SHEN_DF, 0}, Cand{SHEN_DF, 1}, Cand{SHEN_DF, 2}, Cand{SHEN_DF, 3},
                    Cand{SHEN_DF_R1, 0}, Cand{SHEN_FP32_R1, 0}})
         if (check_precision(p, problem, c.prec) == SHEN_OK && !(c.variant >= 2 && p.wall_first))
@@ -691,6 +692,7 @@ shen_status shen_plan_set_shape(shen_plan_t plan, int problem, int shape) {
     if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
     if (shape < 0 || shape >= kDfShapes) return SHEN_ERR_ARG;
     if (shape >= 2 && plan->p.wall_first) return SHEN_ERR_UNSUPPORTED;   // mode-major fields only
+    if (shape >= 2) SHEN_CUDA_TRY(df2_alloc(plan->p));
     plan->p.df_variant[problem] = shape;
     return SHEN_OK;
 }

@@ -100,7 +100,6 @@ struct Plan {
     // on-chip float-float sweeps (shapes 2 and 3): one CTA per SM, per-problem global spill of
     // the forward results that do not fit on chip ([warp slot][block][row][lane] float2)
     int df2_grid = 0;
-    int df2_gb[2] = {0, 0};
     float2 *d_gsp[2] = {nullptr, nullptr};
     double2 *d_wf_stage = nullptr;        // wall-first plans: staging of the transforms (wallfirst.cu)
 
@@ -122,6 +121,7 @@ cudaError_t launch_solve_fp64r(const Plan &p, int problem, long m0, long count, 
 
 // kernels_df2.cu
 cudaError_t df2_setup(Plan &p, long long &bytes);
+cudaError_t df2_alloc(Plan &p);                 // the spill of shapes 2 and 3 (on first use)
 cudaError_t launch_solve_df2(const Plan &p, int problem, bool tmem, long m0, long count, const double *f,
                              double *u, cudaStream_t s);
 

@@ -81,7 +81,7 @@ def test_wall_first_operators_velocity_transforms(N, Nx, Nz):
         um, gm = pm.solve("biharmonic", x, precision="df"), pm.solve("helmholtz", y, precision="df")
         fm = torch.zeros_like(x)
         vm, wm = pm.velocity(um, gm, f=fm)
-        fw = torch.zeros_like(x)
+        fw = torch.zeros_like(T(x))
         vw, ww = pw.velocity(T(um), T(gm), f=fw)
         assert torch.equal(T(vw), vm) and torch.equal(T(ww), wm) and torch.equal(T(fw), fm)
         sm = pm.linear_step(x, y, um, gm, precision="df")
