@@ -57,3 +57,37 @@ def test_linear_step_rejects_aliasing():
             plan.linear_step(a, b, out=(a,) + outs[1:])
         with pytest.raises(ShenError):
             plan.linear_step(a, b, out=(outs[0], outs[0]) + outs[2:])
+
+
+@pytest.mark.parametrize("with_loads", [True, False])
+def test_fused_step_at_n1024(with_loads):
+    """The float-float step (each right-hand-side operator fused into its solve: g_new = -g_old
+    + H_h^-1 (2 c B g_old + s load_g), u_new = -u_old + H_b^-1 (-2 c (A - z2 B) u_old - s load_u))
+    against the float64 composition (operators, then solves) on N = 1024, 64 x 64 modes
+    (z up to ~72), and the unscaled paper equations on a few modes."""
+    import torch
+    N, Nx, Nz, nu, dt = 1024, 64, 64, 1 / 2000, 1e-4
+    z2s = so.mode_z2(Nx, Nz)
+    with Plan(N, Nx, Nz, nu, dt) as plan:
+        dev = [inputs.rhs_torch(plan.n_modes, N, seed=s) for s in (141, 142, 143, 144)]
+        if not with_loads:
+            dev[2] = dev[3] = None
+        fused = [t.cpu().numpy() for t in plan.linear_step(*dev, precision="df")]
+        ref = [t.cpu().numpy() for t in plan.linear_step(*dev, precision="fp64")]
+        Uo, Go = dev[0].cpu().numpy(), dev[1].cpu().numpy()
+        Lu = dev[2].cpu().numpy() if with_loads else np.zeros_like(Uo)
+        Lg = dev[3].cpu().numpy() if with_loads else np.zeros_like(Go)
+    nb, nd = N - 4, N - 2
+    for a, b, n in zip(fused, ref, (nb, nd, nd, nd)):
+        assert np.all(a[:, n:] == 0)
+        for k in range(plan.n_modes):
+            if np.any(b[k]):
+                assert so.rel_l2(a[k, :n], b[k, :n]) <= 1e-10, k
+    for k in (1, plan.n_modes // 2, int(z2s.argmax())):
+        z2 = z2s[k]
+        rhs_u = mat.paper_biharmonic_rhs(N, z2, nu, dt) @ Uo[k, :nb] + dt * Lu[k, :nb]
+        u_ref = so.solve_dense(mat.paper_biharmonic(N, z2, nu, dt), rhs_u)
+        rhs_g = mat.paper_helmholtz_rhs(N, z2, nu, dt) @ Go[k, :nd] + dt * Lg[k, :nd]
+        g_ref = so.solve_dense(mat.paper_helmholtz(N, z2, nu, dt), rhs_g)
+        assert so.rel_l2(fused[0][k, :nb], u_ref) <= 1e-10, k
+        assert so.rel_l2(fused[1][k, :nd], g_ref) <= 1e-10, k
