@@ -225,7 +225,6 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
     PLAN_TRY(pack_df(p, s));
     PLAN_TRY(df_setup(p, B));
     PLAN_TRY(df2_setup(p, B));
-    PLAN_TRY(step_setup(p));
     PLAN_TRY(dalloc(&p.d_mv_df, matvec_df_floats(p), B));
     PLAN_TRY(pack_matvec_df(p, p.d_mv_df, s));
     std::vector<float4> vel;
@@ -445,13 +444,6 @@ shen_status shen_linear_step(shen_plan_t plan, const double *u_old, const double
     //   H_h g_new = R_h g_old + (2/nu) load_g,   H_b u_new = -R_b u_old - (2/nu) load_u
     const double load_scale = 2.0 / p.nu;
     cudaStream_t s = as_stream(stream);
-    if (ph == SHEN_DF && pb == SHEN_DF && !p.wall_first) {
-        // float-float: each right-hand-side operator fused into its solve (step_df.cu), then v, w
-        SHEN_CUDA_TRY(launch_step_df(p, SHEN_BIHARMONIC, u_old, load_u, u_new, s));
-        SHEN_CUDA_TRY(launch_step_df(p, SHEN_HELMHOLTZ, g_old, load_g, g_new, s));
-        SHEN_CUDA_TRY(launch_velocity_df(p, u_new, g_new, v, w, nullptr, s));
-        return SHEN_OK;
-    }
     // right-hand sides into the new fields (float-float operators unless float64 was asked)
     auto rhs = [&](int problem, const double *x, const double *load, double *out) {
         const double sg = problem == SHEN_BIHARMONIC ? -1.0 : 1.0;

@@ -100,7 +100,6 @@ struct Plan {
     // on-chip float-float sweeps (shapes 2 and 3): one CTA per SM, per-problem global spill of
     // the forward results that do not fit on chip ([warp slot][block][row][lane] float2)
     int df2_grid = 0;
-    int step_grid[2] = {0, 0};            // fused Crank-Nicolson step kernels (step_df.cu)
     float2 *d_gsp[2] = {nullptr, nullptr};
     double2 *d_wf_stage = nullptr;        // wall-first plans: staging of the transforms (wallfirst.cu)
 
@@ -153,11 +152,6 @@ bool transform_shape_ok(const Plan &p, int kind, int space);   // the launch fit
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s);   // tables and launch shape
 cudaError_t launch_transform(const Plan &p, int kind, int space, long count, const double *in, double *out,
                              cudaStream_t s);   // count columns from in / out
-
-// step_df.cu
-cudaError_t step_setup(Plan &p);   // after df_setup
-cudaError_t launch_step_df(const Plan &p, int problem, const double *x, const double *load, double *u,
-                           cudaStream_t s);   // one Crank-Nicolson step, operator fused into the solve
 
 // wallfirst.cu
 long wall_first_chunk(const Plan &p);

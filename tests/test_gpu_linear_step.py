@@ -60,11 +60,10 @@ def test_linear_step_rejects_aliasing():
 
 
 @pytest.mark.parametrize("with_loads", [True, False])
-def test_fused_step_at_n1024(with_loads):
-    """The float-float step (each right-hand-side operator fused into its solve: g_new = -g_old
-    + H_h^-1 (2 c B g_old + s load_g), u_new = -u_old + H_b^-1 (-2 c (A - z2 B) u_old - s load_u))
-    against the float64 composition (operators, then solves) on N = 1024, 64 x 64 modes
-    (z up to ~72), and the unscaled paper equations on a few modes."""
+def test_step_at_n1024(with_loads):
+    """The float-float step (float-float operators and solves) against the float64 one on
+    N = 1024, 64 x 64 modes (z up to ~72), with and without loads, and the unscaled paper
+    equations on a few modes."""
     import torch
     N, Nx, Nz, nu, dt = 1024, 64, 64, 1 / 2000, 1e-4
     z2s = so.mode_z2(Nx, Nz)
