@@ -11,68 +11,6 @@
 namespace shen {
 namespace chains {
 
-// L2 cache policies of the float-float sweeps' streams (SHEN_DF_HINTS = 1): the forward
-// result y, written and read back by the same thread, stays in L2 preferentially
-// (evict_last) and each of its 128-byte lines is discarded once the back substitution has
-// read it, so a line still in L2 then is never written to DRAM; the columns f and u, each
-// touched once, go first (evict_first).
-#ifndef SHEN_DF_HINTS
-#define SHEN_DF_HINTS 1
-#endif
-__device__ __forceinline__ uint64_t l2_last() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_first() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ void st4_hint(float4 *p, float4 v, uint64_t pol) {
-#if SHEN_DF_HINTS
-    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w), "l"(pol)
-                 : "memory");
-#else
-    *p = v;
-#endif
-}
-__device__ __forceinline__ float4 ld4_hint(const float4 *p, uint64_t pol) {
-#if SHEN_DF_HINTS
-    float4 v;
-    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-#else
-    return *p;
-#endif
-}
-__device__ __forceinline__ double2 ld2_hint(const double2 *p, uint64_t pol) {
-#if SHEN_DF_HINTS
-    double2 v;
-    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
-    return v;
-#else
-    return *p;
-#endif
-}
-__device__ __forceinline__ void st2_hint(double2 *p, double2 v, uint64_t pol) {
-#if SHEN_DF_HINTS
-    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
-                 : "memory");
-#else
-    *p = v;
-#endif
-}
-// drop the 128-byte line at p from L2 without writing it back (its contents become undefined)
-__device__ __forceinline__ void discard_l2(const void *p) {
-#if SHEN_DF_HINTS
-    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
-#endif
-}
-
 // err[0]: any bad pivot; err[1]: smallest class with one; err[2]: number of chains with one
 __device__ __forceinline__ void flag_error(int *err, long cls) {
     atomicExch(err, 1);
@@ -357,13 +295,9 @@ struct BihDF {
 
 template <int PB>
 __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
-                                             float4 *ys, int ystride, long rs, bool lockstep = false) {
+                                             float4 *ys, int ystride, long rs) {
     const int n = N - 2;
     const int rows = (n - par + 1) / 2;
-    // the 8 lanes sharing a 128-byte line of the y scratch reach each row together when the
-    // caller says so (one plan, both parity chains of equal length)
-    const bool disc = lockstep && (n & 1) == 0 && (threadIdx.x & 7) == 0;
-    const uint64_t pl = l2_last(), pf = l2_first();
     // Forward elimination y_i = f_i - l_i y_{i-1}.  Rows are fetched PB at a time into two
     // register buffers: the next block's loads are issued before the current block is
     // computed (software pipelining), and all loads of a block precede its stores (which
@@ -376,7 +310,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = min(i0 + q, rows - 1);
-                fx[q] = ld2_hint(reinterpret_cast<const double2 *>(fcol) + (2 * i + par) * rs, pf);
+                fx[q] = reinterpret_cast<const double2 *>(fcol)[(2 * i + par) * rs];
                 lx[q] = F.f[(long)i * F.s];
             }
         };
@@ -387,7 +321,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
                     const F2 l{lx[q].x, lx[q].y};
                     y.re = fnma(l, y.re, df::from_f64(fx[q].x));
                     y.im = fnma(l, y.im, df::from_f64(fx[q].y));
-                    st4_hint(ys + (long)(i0 + q) * ystride, make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo), pl);
+                    ys[(long)(i0 + q) * ystride] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
                 }
             }
         };
@@ -407,7 +341,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = max(i0 - q, 0);
-                yx[q] = ld4_hint(ys + (long)i * ystride, pl);
+                yx[q] = ys[(long)i * ystride];
                 ax[q] = F.b[(long)i * F.s];
             }
         };
@@ -426,9 +360,7 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
                     un.im = df::fast_two_sum(un.im.hi, un.im.lo);
                     S.re = df::add(S.re, un.re);
                     S.im = df::add(S.im, un.im);
-                    st2_hint(reinterpret_cast<double2 *>(ucol) + (2 * (i0 - q) + par) * rs,
-                             make_double2(df::to_f64(un.re), df::to_f64(un.im)), pf);
-                    if (disc) discard_l2(ys + (long)(i0 - q) * ystride);
+                    store_f64(ucol, (2 * (i0 - q) + par) * rs, un);
                 }
             }
         };
@@ -467,12 +399,9 @@ __device__ inline void solve_helm_df_chain_t(int N, int par, const double *fcol,
 // when u == f).
 template <int PBF, int PBB, bool QSD>
 __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, double *ucol, BihDF F,
-                                            const float4 *qs, float4 *ys, int ystride, long rs,
-                                            bool lockstep = false) {
+                                            const float4 *qs, float4 *ys, int ystride, long rs) {
     const int n = N - 4;
     const int rows = (n - par + 1) / 2;
-    const bool disc = lockstep && (n & 1) == 0 && (threadIdx.x & 7) == 0;   // as in the Helmholtz chain
-    const uint64_t pl = l2_last(), pf = l2_first();
     const F2 zero{0.f, 0.f};
     // forward elimination y_i = f_i - L1_i y_{i-1} - L2_i y_{i-2}
     CF2 y1{zero, zero}, y2 = y1;
@@ -484,7 +413,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
 #pragma unroll
             for (int q = 0; q < PB; q++) {
                 const int i = min(i0 + q, rows - 1);
-                fx[q] = ld2_hint(reinterpret_cast<const double2 *>(fcol) + (2 * i + par) * rs, pf);
+                fx[q] = reinterpret_cast<const double2 *>(fcol)[(2 * i + par) * rs];
                 lx[q] = F.f[(long)i * F.s];
             }
         };
@@ -497,7 +426,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
                     // the y_{i-2} term first: only the last step waits for y_{i-1}
                     y.re = fnma(L1, y1.re, fnma(L2, y2.re, df::from_f64(fx[q].x)));
                     y.im = fnma(L1, y1.im, fnma(L2, y2.im, df::from_f64(fx[q].y)));
-                    st4_hint(ys + (long)(i0 + q) * ystride, make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo), pl);
+                    ys[(long)(i0 + q) * ystride] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
                     y2 = y1;
                     y1 = y;
                 }
@@ -525,7 +454,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
             for (int q = 0; q < PB; q++) {
                 const int i = max(i0 - q, 0);
                 const long r = (long)i * F.s;
-                yx[q] = ld4_hint(ys + (long)i * ystride, pl);
+                yx[q] = ys[(long)i * ystride];
                 bx[q] = F.b0[r];
                 cx[q] = F.b1[r];
                 dx[q] = F.b2[r];
@@ -558,9 +487,7 @@ __device__ inline void solve_bih_df_chain_t(int N, int par, const double *fcol, 
                     ui.im = df::mul(inv0, t.im);
                     ui.re = df::fast_two_sum(ui.re.hi, ui.re.lo);
                     ui.im = df::fast_two_sum(ui.im.hi, ui.im.lo);
-                    st2_hint(reinterpret_cast<double2 *>(ucol) + (2 * i + par) * rs,
-                             make_double2(df::to_f64(ui.re), df::to_f64(ui.im)), pf);
-                    if (disc) discard_l2(ys + (long)i * ystride);
+                    store_f64(ucol, (2 * i + par) * rs, ui);
                     u3 = u2;
                     u2 = u1;
                     u1 = ui;
@@ -725,24 +652,20 @@ __device__ inline void solve_bih_f32_chain(int N, int par, const double *fcol, d
 // for chain row i: either the chain's own rows of the output column (ys = column + par,
 // ystride = 2; no scratch memory) or a scratch laid out [row][lane] per warp (ystride =
 // 32), where each warp's spill of a row is 512 contiguous bytes.
-// lockstep: the caller runs the two parity chains of one plan's modes side by side and ys is
-// the [row][lane] scratch (ystride 32), so the lines of y read back may be discarded from L2.
 template <int V>
 __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
-                                           float4 *ys, int ystride, long rs = 1, bool lockstep = false) {
-    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride, rs, lockstep && ystride == 32);
+                                           float4 *ys, int ystride, long rs = 1) {
+    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride, rs);
 }
 
 template <int V>
 __device__ inline void solve_bih_df_chain(int N, int par, const double *fcol, double *ucol, BihDF F,
-                                          const float4 *qs, float4 *ys, int ystride, long rs = 1,
-                                          bool lockstep = false) {
+                                          const float4 *qs, float4 *ys, int ystride, long rs = 1) {
     if (V == 0)
         solve_bih_df_chain_t<SHEN_BIH_DF_PBF, SHEN_BIH_DF_PBB, SHEN_BIH_DF_QSD != 0>(N, par, fcol, ucol, F, qs, ys,
-                                                                                    ystride, rs,
-                                                                                    lockstep && ystride == 32);
+                                                                                    ystride, rs);
     else
-        solve_bih_df_chain_t<4, 4, false>(N, par, fcol, ucol, F, qs, ys, ystride, rs, lockstep && ystride == 32);
+        solve_bih_df_chain_t<4, 4, false>(N, par, fcol, ucol, F, qs, ys, ystride, rs);
 }
 
 // The output column's own rows of chain `par`, as a spill target (ystride 2).

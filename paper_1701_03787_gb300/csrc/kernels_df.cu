@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128) helm_df_kernel(Plan p, const int *order, 
         const F2 h = df::from_f64((p.d_class_z2[w.cls] + p.c) * (kPi / 2));
         const long ch = 2L * w.cls + w.par, nch = 2 * p.n_classes;
         chains::solve_helm_df_chain<V>(p.N, w.par, f + off, u + off, chains::HelmDF{p.df_hb + ch, p.df_hf + ch, nch},
-                                       h, ys, 32, rs, true);
+                                       h, ys, 32, rs);
     }
 }
 
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128) bih_df_kernel(Plan p, const int *order, l
         const long ch = 2L * w.cls + w.par, nch = 2 * p.n_classes;
         chains::solve_bih_df_chain<V>(p.N, w.par, f + off, u + off,
                                       chains::BihDF{p.df_bf + ch, p.df_bb0 + ch, p.df_bb1 + ch, p.df_bb2 + ch, nch},
-                                      p.df_qs, ys, 32, rs, true);
+                                      p.df_qs, ys, 32, rs);
     }
 }
 
