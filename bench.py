@@ -130,24 +130,30 @@ TRAFFIC_KERNELS = (
 )
 
 
-def write_traffic(csv_path, w):
-    """Rewrite profiles/traffic.json from an ncu CSV launch list with dram__bytes_read.sum and
-    dram__bytes_write.sum of the kernels above, taken on workload `w`: bytes per complex row
-    (averaged over the captured launches of each kernel), stamped with the current hashes
-    of each group's sources."""
+def write_traffic(csv_paths, w):
+    """Rewrite profiles/traffic.json from ncu CSV launch lists with dram__bytes_read.sum and
+    dram__bytes_write.sum of the kernels above (one CSV per capture, e.g. one per kernel),
+    taken on workload `w`: bytes per complex row (averaged over the captured launches of each
+    kernel), stamped with the current hashes of each group's sources."""
     import csv
     import re
-    with open(csv_path) as fh:
-        lines = [ln for ln in fh if ln.startswith('"')]
-    rows = list(csv.reader(lines))
-    hdr = rows[0]
-    c_id, c_name = hdr.index("ID"), hdr.index("Kernel Name")
-    c_metric, c_val = hdr.index("Metric Name"), hdr.index("Metric Value")
+    if isinstance(csv_paths, str):
+        csv_paths = [csv_paths]
     per_launch = {}
-    for r in rows[1:]:
-        if r[c_metric] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            name, b = per_launch.get(r[c_id], (r[c_name], 0.0))
-            per_launch[r[c_id]] = (name, b + float(r[c_val].replace(",", "")))
+    for f_i, csv_path in enumerate(csv_paths):
+        with open(csv_path) as fh:
+            lines = [ln for ln in fh if ln.startswith('"')]
+        rows = list(csv.reader(lines))
+        if not rows:
+            continue
+        hdr = rows[0]
+        c_id, c_name = hdr.index("ID"), hdr.index("Kernel Name")
+        c_metric, c_val = hdr.index("Metric Name"), hdr.index("Metric Value")
+        for r in rows[1:]:
+            if r[c_metric] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                key = (f_i, r[c_id])                      # launch IDs restart in every capture
+                name, b = per_launch.get(key, (r[c_name], 0.0))
+                per_launch[key] = (name, b + float(r[c_val].replace(",", "")))
     n_rows = n_modes_of(w) * w["N"]
     counts, per_kind = {}, {}
     for pat, kinds in TRAFFIC_KERNELS:
@@ -537,8 +543,9 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="split the one field's modes into contiguous ranges, one per rank (shen_solve_modes); "
                          "strong scaling.  Default: one whole replica of the workload per rank (weak scaling)")
-    ap.add_argument("--write-traffic", metavar="CSV",
-                    help="rewrite profiles/traffic.json from an ncu DRAM-bytes capture on --workload, then exit")
+    ap.add_argument("--write-traffic", metavar="CSV", nargs="+",
+                    help="rewrite profiles/traffic.json from ncu DRAM-bytes captures (one CSV per capture) on "
+                         "--workload, then exit")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.write_traffic:

@@ -94,3 +94,18 @@ def test_reference_arm_times_whole_sampled_steps():
     assert line["full_step_ms_extrapolated"] >= line["ms_per_step"] * 0.999
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_traffic_from_one_capture_per_kernel(tmp_path, monkeypatch):
+    """Captures taken one kernel at a time restart their launch IDs: each file's launches
+    stay apart."""
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(tmp_path / "traffic.json"))
+    a = tmp_path / "a"
+    b = tmp_path / "b"
+    a.mkdir()
+    b.mkdir()
+    pa = _csv(a, [("void unnamed>::bih_df_kernel<0>(Plan)", 768 * 40, 768 * 40)])
+    pb = _csv(b, [("void unnamed>::helm_df_kernel<0>(Plan)", 768 * 30, 768 * 30)])
+    bpr = bench.write_traffic([pa, pb], W)["bytes_per_row"]
+    assert bpr["biharmonic:df"] == pytest.approx(80.0)
+    assert bpr["helmholtz:df"] == pytest.approx(60.0)
