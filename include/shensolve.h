@@ -457,6 +457,24 @@ shen_status shen_batch_solve(shen_batch_t batch, int problem, const double *f, d
 shen_status shen_batch_autotune(shen_batch_t batch, int problem, const double *f, double *u, int *chosen,
                                 float *ms, void *stream);
 
+/* Solve every mode of every instance for batched fields in HOST memory, as
+ * shen_solve_host does for single plans: f_host and u_host hold the batched field
+ * (field_elems complex values, u_host == f_host allowed); page-locked (pinned) host
+ * memory gives full copy bandwidth.  The field is cut into chunks of whole modes (at
+ * most 256 MB each, contiguous in the field); each chunk is copied into one of three
+ * device staging slots, solved there by one persistent launch over its modes (in the
+ * batch's decreasing-N order) and copied back, with the copies of neighbouring chunks
+ * overlapping the solve on internal streams.  The first call sets up the slots, the
+ * chunks' work lists (4 bytes per mode) and the streams, blocking while it copies the
+ * work lists; shen_batch_info counts them from then on.  The work starts after what is
+ * queued on `stream`, and `stream` waits for the last copy-out: synchronise it before
+ * reading u_host.  Calls on one plan share the pipeline (they follow each other chunk by
+ * chunk) and must come from one host thread at a time; like shen_batch_solve, a call
+ * must not overlap a device solve of the same problem on the same plan.  problem and
+ * precision as shen_batch_solve; results equal shen_batch_solve's bit for bit. */
+shen_status shen_batch_solve_host(shen_batch_t batch, int problem, const double *f_host, double *u_host,
+                                  int precision, void *stream);
+
 /* Device-side error state of the batched plan (SHEN_OK or SHEN_ERR_SINGULAR). */
 shen_status shen_batch_check(shen_batch_t batch);
 

@@ -68,6 +68,7 @@ def lib():
         "shen_batch_solve": ([P, I, P, P, I, P], I),
         "shen_batch_check": ([P], I),
         "shen_batch_solve_noalloc": ([P, I, P, P, I, P], I),
+        "shen_batch_solve_host": ([P, I, P, P, I, P], I),
         "shen_batch_autotune": ([P, I, P, P, P, P, P], I),
         "shen_plan_autotune": ([P, I, P, P, P, P, P], I),
         "shen_batch_destroy": ([P], None),
@@ -416,16 +417,23 @@ class BatchPlan:
         self._h = ctypes.c_void_p()
         check(lib().shen_batch_plan_create(ctypes.byref(self._h), len(instances), ctypes.cast(descs, ctypes.c_void_p),
                                            SHEN_PLAN_GL if gl else 0, _stream(stream)), "shen_batch_plan_create")
+        self.n_instances = len(instances)
+        i = self.info()
+        self.n_modes, self.field_elems, self.n_classes, self.device_bytes = (
+            i["n_modes"], i["field_elems"], i["n_classes"], i["device_bytes"])
+        offs = (ctypes.c_long * (len(instances) + 1))()
+        check(lib().shen_batch_offsets(self._h, ctypes.cast(offs, ctypes.c_void_p)), "shen_batch_offsets")
+        self.offsets = list(offs)
+
+    def info(self):
+        """dict of n_modes, field_elems, n_classes and device_bytes (the latter includes the
+        host-solve staging once solve_host has run)."""
         n_modes, elems, ncls = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
         nbytes = ctypes.c_longlong()
         check(lib().shen_batch_info(self._h, ctypes.byref(n_modes), ctypes.byref(elems), ctypes.byref(ncls),
                                     ctypes.byref(nbytes)), "shen_batch_info")
-        self.n_instances = len(instances)
-        self.n_modes, self.field_elems, self.n_classes, self.device_bytes = (
-            n_modes.value, elems.value, ncls.value, nbytes.value)
-        offs = (ctypes.c_long * (len(instances) + 1))()
-        check(lib().shen_batch_offsets(self._h, ctypes.cast(offs, ctypes.c_void_p)), "shen_batch_offsets")
-        self.offsets = list(offs)
+        return {"n_modes": n_modes.value, "field_elems": elems.value, "n_classes": ncls.value,
+                "device_bytes": nbytes.value}
 
     def close(self):
         if self._h:
@@ -452,6 +460,21 @@ class BatchPlan:
             u = torch.empty_like(f)
         check(lib().shen_batch_solve(self._h, _problem(problem), _ptr(f), _ptr(u), _prec(precision),
                                      _stream(stream)), "shen_batch_solve")
+        return u
+
+    def solve_host(self, problem, f, u=None, precision="fp64", stream=None):
+        """Solve a batched field held in (preferably pinned) host memory; returns u (host).
+        Asynchronous on `stream` (default: the current stream); synchronise the stream
+        before reading u."""
+        import torch
+        if f.dtype != torch.complex128 or f.is_cuda or not f.is_contiguous() or f.numel() != self.field_elems:
+            raise ValueError(f"f must be a contiguous complex128 host tensor of {self.field_elems} entries")
+        if u is None:
+            u = torch.empty_like(f, pin_memory=f.is_pinned())
+        if u.dtype != torch.complex128 or u.is_cuda or not u.is_contiguous() or u.numel() != f.numel():
+            raise ValueError("u must be a contiguous complex128 host tensor shaped like f")
+        check(lib().shen_batch_solve_host(self._h, _problem(problem), _ptr(f), _ptr(u), _prec(precision),
+                                          _stream(stream)), "shen_batch_solve_host")
         return u
 
     def autotune(self, problem, f, u=None, stream=None):

@@ -49,6 +49,9 @@ struct BatchDev {
     float2 *df_hf, *df_bb2;
     int *queue;
     int *err;
+    // complex-element offset subtracted from every column offset: 0 for whole batched
+    // fields; the first column of the chunk for a staging slot of the host pipeline
+    long col_shift;
     // float-float spill scratch per problem, [warp slot][row][lane] (ys_rows rows per
     // slot); null: spill through the output column instead
     float4 *ys[2];
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
             const int m = b.work[item];
             const BatchInst in = b.inst[b.mode_inst[m]];
             const BatchCls cl = b.cls[b.mode_cls[m]];
-            const long off = 2 * (in.col0 + (long)(m - in.mode0) * in.N);
+            const long off = 2 * (in.col0 - b.col_shift + (long)(m - in.mode0) * in.N);
             if (PROBLEM == SHEN_HELMHOLTZ) {
                 if (PREC == 0) {
                     chains::solve_helm_fp64_chain(in.N, par, f + off, u + off,
@@ -178,9 +181,17 @@ void build_row_tables(int N, std::vector<double> &h, std::vector<float> &h32, in
 
 using namespace shen;
 
+namespace shen {
+struct BatchHostPipe;
+void batch_host_free(BatchHostPipe *h);
+long long batch_host_bytes(const BatchHostPipe *h);
+}  // namespace shen
+
 struct shen_batch_s {
     BatchDev d{};
     std::vector<BatchInst> inst;
+    std::vector<int> work;                       // the work order (host copy), for the host pipeline
+    BatchHostPipe *host = nullptr;               // shen_batch_solve_host's staging, built at its first call
     std::vector<int> tab_N;
     // owned device allocations
     std::vector<void *> allocs;
@@ -190,6 +201,7 @@ struct shen_batch_s {
     int auto_prec[2] = {SHEN_DF, SHEN_DF};       // SHEN_AUTO per problem (autotuned)
     int df_variant[2] = {0, 0};                  // float-float shape per problem (autotuned)
     ~shen_batch_s() {
+        batch_host_free(host);
         for (void *p : allocs) cudaFree(p);
     }
 };
@@ -311,6 +323,7 @@ shen_status shen_batch_plan_create(shen_batch_t *out, int n_inst, const shen_ins
         if (e_ != cudaSuccess) return fail(cuda_status(e_)); \
     } while (0)
     b->inst = inst;
+    b->work = work;
     const int n_tabs = (int)tab_of_N.size();
     b->tab_N.assign((size_t)n_tabs, 0);
     int N_max = 0;
@@ -426,7 +439,7 @@ shen_status shen_batch_info(shen_batch_t batch, long *n_modes, long *field_elems
         *field_elems = l.col0 + l.n_modes * l.N;
     }
     if (n_classes) *n_classes = batch->d.n_cls;
-    if (device_bytes) *device_bytes = batch->device_bytes;
+    if (device_bytes) *device_bytes = batch->device_bytes + batch_host_bytes(batch->host);
     return SHEN_OK;
 }
 
@@ -543,6 +556,165 @@ shen_status shen_batch_autotune(shen_batch_t batch, int problem, const double *f
 void shen_batch_destroy(shen_batch_t batch) { delete batch; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Batched solves on HOST fields.  The batched field is cut into chunks of whole modes
+// (contiguous in the field, at most kBatchChunkBytes each); chunk c goes through staging
+// slot c mod 3: copy in, one persistent launch over the chunk's modes (its own work list,
+// in the batch's decreasing-N order, and its own queue counter), copy out, on three
+// internal streams ordered by events, so that copies in both directions overlap the
+// solves of the neighbouring chunks.  Like shen_solve_host for single plans.
+// ---------------------------------------------------------------------------------
+
+namespace shen {
+
+struct BatchHostPipe {
+    static constexpr int kSlots = 3;
+    double *slot[kSlots] = {};
+    int *d_work = nullptr;                 // the chunks' work lists, one after the other
+    int *d_queue = nullptr;                // queue counter of the pipeline's launches
+    std::vector<long> m0, c0;              // chunk c: modes [m0[c], m0[c+1]), complex elements from c0[c]
+    cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+    cudaEvent_t loaded[kSlots] = {}, solved[kSlots] = {}, freed[kSlots] = {};
+    cudaEvent_t start = nullptr, done_out = nullptr;
+    long chunk = 0;                        // chunks issued so far (slot = chunk % kSlots)
+    long long bytes = 0;
+};
+
+void batch_host_free(BatchHostPipe *h) {
+    if (!h) return;
+    for (cudaStream_t s : {h->in, h->comp, h->out})
+        if (s) cudaStreamSynchronize(s);
+    for (int i = 0; i < BatchHostPipe::kSlots; i++) {
+        cudaFree(h->slot[i]);
+        for (cudaEvent_t e : {h->loaded[i], h->solved[i], h->freed[i]})
+            if (e) cudaEventDestroy(e);
+    }
+    cudaFree(h->d_work);
+    cudaFree(h->d_queue);
+    for (cudaEvent_t e : {h->start, h->done_out})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : {h->in, h->comp, h->out})
+        if (s) cudaStreamDestroy(s);
+    delete h;
+}
+
+long long batch_host_bytes(const BatchHostPipe *h) { return h ? h->bytes : 0; }
+
+namespace {
+
+constexpr long kBatchChunkBytes = 256L << 20;   // target size of one staging slot
+
+// Chunks, work lists and staging of a batched plan (blocking: the work lists are copied
+// to the device synchronously).
+cudaError_t batch_host_init(const shen_batch_s &b, BatchHostPipe &h) {
+    const long cap = kBatchChunkBytes / 16;       // complex elements per slot (> 8192, the largest N)
+    h.m0.assign(1, 0);
+    h.c0.assign(1, 0);
+    long used = 0, m = 0;
+    for (const BatchInst &in : b.inst)
+        for (long r = in.n_modes; r > 0;) {
+            long fit = (cap - used) / in.N;
+            if (fit == 0) {                       // close the chunk at mode m
+                h.m0.push_back(m);
+                h.c0.push_back(in.col0 + (m - in.mode0) * in.N);
+                used = 0;
+                fit = cap / in.N;
+            }
+            const long take = std::min(fit, r);
+            used += take * in.N;
+            m += take;
+            r -= take;
+        }
+    const BatchInst &last = b.inst.back();
+    h.m0.push_back(m);
+    h.c0.push_back(last.col0 + last.n_modes * last.N);
+    const long n_chunks = (long)h.m0.size() - 1;
+    long span = 0;
+    for (long c = 0; c < n_chunks; c++) span = std::max(span, h.c0[c + 1] - h.c0[c]);
+    // each chunk's modes in the batch's work order (decreasing N, instance, class)
+    std::vector<long> fill(h.m0.begin(), h.m0.end() - 1);
+    std::vector<int> work((size_t)b.d.n_modes);
+    for (int md : b.work) {
+        const long c = (long)(std::upper_bound(h.m0.begin(), h.m0.end(), (long)md) - h.m0.begin()) - 1;
+        work[(size_t)fill[c]++] = md;
+    }
+    cudaError_t e = cudaMalloc((void **)&h.d_work, work.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h.d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(h.d_work, work.data(), work.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    h.bytes = (long long)(work.size() * sizeof(int) + sizeof(int));
+    for (int i = 0; i < BatchHostPipe::kSlots; i++) {
+        if ((e = cudaMalloc((void **)&h.slot[i], (size_t)span * 16)) != cudaSuccess) return e;
+        h.bytes += (long long)span * 16;
+        if ((e = cudaEventCreateWithFlags(&h.loaded[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&h.solved[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&h.freed[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    for (cudaStream_t *s : {&h.in, &h.comp, &h.out})
+        if ((e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming)) != cudaSuccess) return e;
+    return cudaEventCreateWithFlags(&h.done_out, cudaEventDisableTiming);
+}
+
+}  // namespace
+}  // namespace shen
+
+extern "C" shen_status shen_batch_solve_host(shen_batch_t batch, int problem, const double *f_host, double *u_host,
+                                             int precision, void *stream) {
+    if (!batch || !f_host || !u_host) return SHEN_ERR_ARG;
+    if (problem != SHEN_HELMHOLTZ && problem != SHEN_BIHARMONIC) return SHEN_ERR_ARG;
+    if (precision == SHEN_AUTO) precision = batch->auto_prec[problem];
+    if (precision != SHEN_FP64 && precision != SHEN_DF) {
+        if ((precision >= SHEN_FP32_R1 && precision <= SHEN_DF_R2) || precision == SHEN_FP64_R1)
+            return SHEN_ERR_UNSUPPORTED;
+        return SHEN_ERR_ARG;
+    }
+    long elems = 0;
+    shen_batch_info(batch, nullptr, &elems, nullptr, nullptr);
+    if (f_host != u_host && !(f_host + 2 * elems <= u_host || u_host + 2 * elems <= f_host)) return SHEN_ERR_ARG;
+    if (!batch->host) {
+        batch->host = new (std::nothrow) BatchHostPipe;
+        if (!batch->host) return SHEN_ERR_ALLOC;
+        const cudaError_t e = batch_host_init(*batch, *batch->host);
+        if (e != cudaSuccess) {                   // release what was made; the next call starts over
+            batch_host_free(batch->host);
+            batch->host = nullptr;
+            return cuda_status(e);
+        }
+    }
+    BatchHostPipe &h = *batch->host;
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    // the pipeline starts after the work already on the caller's stream
+    cudaError_t e = cudaEventRecord(h.start, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h.in, h.start, 0);
+    const long n_chunks = (long)h.m0.size() - 1;
+    for (long c = 0; c < n_chunks && e == cudaSuccess; c++) {
+        const int s = (int)(h.chunk % BatchHostPipe::kSlots);
+        const size_t bytes = (size_t)(h.c0[c + 1] - h.c0[c]) * 16;
+        const size_t off = (size_t)h.c0[c] * 2;  // doubles
+        BatchDev D = batch->d;
+        D.work = h.d_work + h.m0[c];
+        D.n_modes = h.m0[c + 1] - h.m0[c];
+        D.col_shift = h.c0[c];
+        D.queue = h.d_queue;
+        if (h.chunk >= BatchHostPipe::kSlots) e = cudaStreamWaitEvent(h.in, h.freed[s], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.slot[s], f_host + off, bytes, cudaMemcpyHostToDevice, h.in);
+        if (e == cudaSuccess) e = cudaEventRecord(h.loaded[s], h.in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h.comp, h.loaded[s], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h.d_queue, 0, sizeof(int), h.comp);
+        if (e == cudaSuccess) e = launch_batch(batch, D, problem, precision, h.slot[s], h.slot[s], h.comp);
+        if (e == cudaSuccess) e = cudaEventRecord(h.solved[s], h.comp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h.out, h.solved[s], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u_host + off, h.slot[s], bytes, cudaMemcpyDeviceToHost, h.out);
+        if (e == cudaSuccess) e = cudaEventRecord(h.freed[s], h.out);
+        h.chunk++;
+    }
+    // the caller's stream continues once every copy out has landed
+    if (e == cudaSuccess) e = cudaEventRecord(h.done_out, h.out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h.done_out, 0);
+    return e == cudaSuccess ? SHEN_OK : cuda_status(e);
+}
 
 // ---------------------------------------------------------------------------------
 // No-allocation variant of the batched solve.
