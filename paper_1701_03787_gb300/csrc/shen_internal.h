@@ -78,7 +78,8 @@ struct Plan {
     int vel_grid = 0;                     // its fixed grid of resident blocks
     // wall-normal transforms (power-of-two N, Gauss points): per-N tables, launch shape
     float4 *d_tr = nullptr;
-    int tr_stride = 0, tr_ntw = 0, tr_off_mass = 0, tr_G = 1;
+    int tr_stride = 0, tr_ntw = 0, tr_G = 1;
+    float tr_ls[2][3][2] = {};   // forward phi / psi: (rho, kappa, tau) per parity, float-float pairs
     int tr_groups[3][3] = {}, tr_smem[3][3] = {}, tr_grid[3][3] = {};   // per (kind, space)
     // grid of the modes (plans from shen_plan_create; zero for explicit z2 lists)
     int grid_Nx = 0, grid_Nz = 0;

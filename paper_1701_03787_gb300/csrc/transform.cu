@@ -23,14 +23,14 @@
 // FFT of length 2M of the even extension (x_0 .. x_M, x_{M-1} .. x_1).
 // The FFT is an in-place decimation-in-frequency radix-4 (and one radix-2) pass sequence
 // in shared memory; its output sits in digit-reversed positions, which the post-processing
-// reads through dpos().  The forward transforms in phi and psi add the mass solve
-// B uhat = S (tridiagonal per parity for phi, pentadiagonal for psi, the same for every
-// mode) as a second kernel, one thread per parity chain in place on the output column, with
-// the LU rows of B as per-N tables.
+// reads through dpos().  The forward transforms in phi and psi solve B uhat = S in the same
+// kernel, from the column's Chebyshev coefficients in shared memory: B = P W P^T makes
+// uhat a weighted least-squares fit whose triangular part inverts as prefix sums
+// (forward_ls), so no banded sweep runs.
 //
 // One group of warps per mode column, persistent blocks; float-float arithmetic (pairs of
-// float32, df.cuh), float64 (complex128) in and out.  N a power of two (Gauss) or one more
-// than a power of two (Gauss-Lobatto).
+// float32, df.cuh), float64 (complex128) in and out.  FFT length N (Gauss) or 2 (N - 1)
+// (Gauss-Lobatto), a power of two or three times one.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -126,11 +126,11 @@ __device__ __forceinline__ F2 ratio(float n, float d) {
     return F2{hi, __fmaf_rn(__fmaf_rn(-lo, d, rem), r, lo)};
 }
 
-// Raw (unrenormalised) sums in the FFT passes of the scalar products too.  The inverse
-// transform always uses them.  The scalar products feed the forward transform's mass solve,
-// which amplifies their error by the conditioning of B: their Makhoul pair step and basis
-// combination stay renormalised (raw sums there raised the forward transform's error on
-// smooth spectra 15- to 300-fold, to the bound of its tests).
+// Raw (unrenormalised) sums in the FFT passes of the scalar products and forward transforms
+// too.  The inverse transform always uses them.  The Makhoul pair step and the basis
+// combination stay renormalised: with the earlier banded mass solve, which amplified the
+// scalar products' error by the conditioning of B, raw sums there raised the forward
+// transform's error on smooth spectra 15- to 300-fold.
 constexpr bool kRawForward = true;
 
 // Position of frequency k after the in-place DIF passes (radix 4 first, then one radix 2
@@ -181,6 +181,19 @@ struct Group {
     }
 };
 
+// Physical slot of FFT position p in a group's column buffer A.  After the DIF passes
+// frequency k sits at dpos(k), whose top bits come from k's low bits, so eight consecutive
+// frequencies read by the eight lanes of a 16-byte access phase would share one bank group
+// (8-way conflicts).  XORing position bits lg-1, lg-2 and lg-4 (filled from k's bits 0, 1,
+// 2; lg the power-of-two part of the FFT length) into the low three bits spreads them over
+// all eight (the XOR only permutes inside aligned blocks of eight).  The layout changes at
+// the FFT's last pass: the pre-processing and the FFT passes use natural slots, the last
+// pass stores position p at slot swz(p), and every access after the FFT goes through swz.
+// s = lg - 4 >= 3, or 0: no swizzle (short columns).
+__device__ __forceinline__ int swz(int p, int s) {
+    return s ? p ^ (((p >> (s + 2)) & 3) | (((p >> s) & 1) << 2)) : p;
+}
+
 // In-place FFT of the group's column A[0 .. NF), NF = f3 2^lg (f3 = 1 or 3): forward
 // e^{-2 pi i jk/NF}, or (INV) e^{+...}, unnormalised, output in dpos() order.
 // f3 = 3: a radix-3 decimation-in-frequency pass first (tw[0] = e^{-2 pi i/3}; tw[1 + 2 n],
@@ -190,7 +203,7 @@ struct Group {
 // [3 j + m - 1] = e^{-2 pi i m j 4^p / 2^lg}, j < Q, m = 1, 2, 3, passes stored one after the
 // other, so a pass reads its twiddles contiguously.
 template <bool INV, bool RAW>
-__device__ void fft_dif(float4 *A, int lg, int f3, const float4 *tw, const Group &g) {
+__device__ void fft_dif(float4 *A, int lg, int f3, const float4 *tw, const Group &g, int sw) {
     const int N = f3 << lg, half = N >> 1;
     int lgL = lg;
     const float4 *twp = tw;
@@ -219,18 +232,44 @@ __device__ void fft_dif(float4 *A, int lg, int f3, const float4 *tw, const Group
         twp += 1 + 2 * Q;
         g.sync();
     }
+    auto bfly4 = [&](Z a, Z bb, Z c, Z d, Z &y0, Z &y1, Z &y2, Z &y3) {   // untwiddled outputs
+        const Z s0 = zadd_raw(a, c), s1 = zsub_raw(a, c), s2 = zadd_raw(bb, d), s3 = zsub_raw(bb, d);
+        auto sum = [](Z u, Z v) { return RAW ? zadd_raw(u, v) : zadd(u, v); };
+        y0 = sum(s0, s2);
+        y2 = sum(s0, zneg(s2));
+        y1 = sum(s1, INV ? zi(s3) : zmi(s3));
+        y3 = sum(s1, INV ? zmi(s3) : zi(s3));
+    };
     for (; lgL >= 2; lgL -= 2) {
         const int lgQ = lgL - 2, Q = 1 << lgQ;
+        if (lgL == 2 && sw) {
+            // last pass (no radix-2 follows), stores to the swizzled slots: the slots of
+            // butterflies b and b ^ 1 (one aligned block of eight, two lanes of one warp) mix,
+            // so every lane of the warp loads before any stores (uniform trip count)
+            const int nb = N >> 2;
+            for (int b0 = 0; b0 < nb; b0 += g.nt) {
+                const int b = b0 + g.t, base = b << 2;
+                Z y0 = kZero, y1 = kZero, y2 = kZero, y3 = kZero;
+                if (b < nb)
+                    bfly4(ldz(A, base), ldz(A, base + 1), ldz(A, base + 2), ldz(A, base + 3), y0, y1, y2, y3);
+                __syncwarp();
+                if (b < nb) {
+                    stz(A, swz(base, sw), y0);
+                    stz(A, swz(base + 1, sw), y1);
+                    stz(A, swz(base + 2, sw), y2);
+                    stz(A, swz(base + 3, sw), y3);
+                }
+                __syncwarp();
+            }
+            g.sync();
+            continue;
+        }
 #pragma unroll 2
         for (int b = g.t; b < (N >> 2); b += g.nt) {
             const int j = b & (Q - 1);
             const int base = ((b >> lgQ) << lgL) + j;
-            const Z a = ldz(A, base), bb = ldz(A, base + Q), c = ldz(A, base + 2 * Q), d = ldz(A, base + 3 * Q);
-            const Z s0 = zadd_raw(a, c), s1 = zsub_raw(a, c), s2 = zadd_raw(bb, d), s3 = zsub_raw(bb, d);
-            auto sum = [](Z u, Z v) { return RAW ? zadd_raw(u, v) : zadd(u, v); };
-            Z y0 = sum(s0, s2), y2 = sum(s0, zneg(s2));
-            Z y1 = sum(s1, INV ? zi(s3) : zmi(s3));
-            Z y3 = sum(s1, INV ? zmi(s3) : zi(s3));
+            Z y0, y1, y2, y3;
+            bfly4(ldz(A, base), ldz(A, base + Q), ldz(A, base + 2 * Q), ldz(A, base + 3 * Q), y0, y1, y2, y3);
             if (j != 0) {
                 Z w1 = ldz(twp, 3 * j), w2 = ldz(twp, 3 * j + 1), w3 = ldz(twp, 3 * j + 2);
                 if (INV) {
@@ -252,10 +291,22 @@ __device__ void fft_dif(float4 *A, int lg, int f3, const float4 *tw, const Group
         g.sync();
     }
     if (lgL == 1) {
-        for (int b = g.t; b < half; b += g.nt) {
-            const Z a = ldz(A, 2 * b), c = ldz(A, 2 * b + 1);
-            stz(A, 2 * b, zadd(a, c));
-            stz(A, 2 * b + 1, zsub(a, c));
+        // last pass: as above, the four lanes of an aligned block of eight load before any
+        // of them stores to the swizzled slots
+        for (int b0 = 0; b0 < half; b0 += g.nt) {
+            const int b = b0 + g.t;
+            Z y0 = kZero, y1 = kZero;
+            if (b < half) {
+                const Z a = ldz(A, 2 * b), c = ldz(A, 2 * b + 1);
+                y0 = zadd(a, c);
+                y1 = zsub(a, c);
+            }
+            __syncwarp();
+            if (b < half) {
+                stz(A, swz(2 * b, sw), y0);
+                stz(A, swz(2 * b + 1, sw), y1);
+            }
+            __syncwarp();
         }
         g.sync();
     }
@@ -307,6 +358,9 @@ struct TrArgs {
     const float4 *mk;        // e^{-i pi k/(2N)}, k = 0 .. N/2
     int *err;                // set to 1 if a column copy did not complete
     F2 pi_over_N;
+    // forward transforms in phi / psi, per parity h: ls[h] = (rho_h, kappa_h, tau_h) of the
+    // least-squares correction (forward_ls)
+    F2 ls[2][3];
 };
 
 // Two buffers of `stride` float4 per mode group, A and R (= B).  The column copy lands in
@@ -314,14 +368,183 @@ struct TrArgs {
 // mode's FFT.
 constexpr int kBuffers = 2;
 
-// KIND: 0 inverse, 1 scalar products, 2 forward (the T_k space only: the forward transforms
-// in phi, psi are the scalar products followed by mass_sweep_kernel).  SPACE: 0 T_k, 1 phi_k,
-// 2 psi_k.  GL: Gauss-Lobatto points (a compile-time choice, so the Gauss kernels carry none
+// float4 of per-group shared scratch of the forward transforms in phi / psi (warp totals
+// of their sums, up to 4 warps): [0, 8) and [16, 24) scans, [8, 16) sums.
+constexpr int kScratch = 24;
+
+__device__ __forceinline__ Z zshfl_xor(Z v, int o) {
+    return Z{F2{__shfl_xor_sync(0xffffffffu, v.re.hi, o), __shfl_xor_sync(0xffffffffu, v.re.lo, o)},
+             F2{__shfl_xor_sync(0xffffffffu, v.im.hi, o), __shfl_xor_sync(0xffffffffu, v.im.lo, o)}};
+}
+__device__ __forceinline__ Z zshfl_up(Z v, int o) {
+    return Z{F2{__shfl_up_sync(0xffffffffu, v.re.hi, o), __shfl_up_sync(0xffffffffu, v.re.lo, o)},
+             F2{__shfl_up_sync(0xffffffffu, v.im.hi, o), __shfl_up_sync(0xffffffffu, v.im.lo, o)}};
+}
+__device__ __forceinline__ Z zmulf(Z v, float b) { return Z{nrm(df::mul(v.re, b)), nrm(df::mul(v.im, b))}; }
+// v - c f (c complex, f real float-float)
+__device__ __forceinline__ Z zsubmul(Z v, Z c, F2 f) {
+    return Z{df::add(v.re, dneg(df::mul(c.re, f))), df::add(v.im, dneg(df::mul(c.im, f)))};
+}
+
+// Inclusive prefix sums over the warp's lanes of two values (one per parity), in lane order.
+__device__ __forceinline__ void warp_inclusive_scan(int lane, Z &i0, Z &i1) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Z u0 = zshfl_up(i0, o), u1 = zshfl_up(i1, o);
+        if (lane >= o) {
+            i0 = zadd(u0, i0);
+            i1 = zadd(u1, i1);
+        }
+    }
+}
+
+// Forward transform in phi (SPACE 1) or psi (SPACE 2), uhat = B^{-1} S (Eqs. sst2, fstB),
+// from the column's Chebyshev coefficients chat (chat_K = (u, T_K)_sigma / w_K, w_K =
+// pi c_K / 2) without a banded solve.  The discrete norms make B = P^T W P, with W =
+// diag(w_K) and P the basis combination (phi_l = sum_K P_Kl T_K, Eqs. phiD, phiN), and
+// S = P^T W chat, so uhat is the W-weighted least-squares solution of P uhat = chat.  Per
+// parity (K = 2 i + h over the Chebyshev indices K < N of that parity):
+//   phi: (P uhat)_K = uhat_i - uhat_{i-1};
+//   psi: P = (I - Shift)(I - b Shift), b_i = (K - 1) / (K + 1), since 1 + b_i = 2K / (K + 1)
+//        and b_{i-1} = (K - 3) / (K - 1) are the combination's coefficients of Eq. phiN at
+//        row K.
+// The residual chat - P uhat of the least-squares solution is W^{-1} times a vector of the
+// null space of P^T (phi: constants; psi: constants and K^2, orthogonalised in the weight
+// omega_K = 1 / c_K as q_K = K^2 - kappa), fixed by asking chat - r to lie in the range of P:
+//   r_K = omega_K (cr + cq q_K),  cr = rho sum_K chat_K,  cq = tau sum_K q_K chat_K,
+//   rho = 1 / sum omega, kappa = sum omega K^2 / sum omega, tau = 1 / sum omega q^2
+// (cq for psi only; rho, kappa, tau per parity from the plan).  The triangular part of P
+// then inverts as prefix sums over the parity, and the prefix sums of r have closed forms
+// (Omega_K = sum_{m <= K} omega_m = (K + 1) / 2, sum_{m <= K} omega_m m^2 = K (K+1) (K+2) / 6
+// for either parity), so with P_K = sum_{m <= K} chat_m:
+//   phi: uhat_K = P_K - cr Omega_K;
+//   psi: v_K = P_K - cr Omega_K - cq Q_K,  Q_K = K (K+1) (K+2) / 6 - kappa Omega_K,
+//        uhat_K = (K + 1)^-1 sum_{m <= K} (m + 1) v_m
+// (the last from uhat_i = v_i + b_i uhat_{i-1}: the products of b telescope).
+// Every thread of the group owns a run of cpt = 2^lc >= 8 natural indices (from t cpt) and
+// keeps its running sums there; the sums across runs go through warp shuffles and the
+// group's scratch `scr` (2 float4 per warp and quantity).  The first pass reads the
+// Chebyshev coefficients from the FFT's digit-reversed positions in A; the later ones work
+// in W (the group's free staging buffer) at k ^ (t & 7): the eight lanes of a 16-byte access
+// phase then fall on distinct bank groups (W is not swizzled by swz).
+template <int SPACE, bool GL, class ChatFn>
+__device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *scr, const Group &g, ChatFn chat,
+                                           int n, double2 *y) {
+    const int N = a.N;
+    const int lane = g.t & 31, warp = g.t >> 5, nw = g.nt >> 5;
+    int lc = 3;
+    while ((g.nt << lc) < N) lc++;
+    const int k0 = min(N, g.t << lc), k1 = min(N, k0 + (1 << lc)), kn = min(k1, n), rx = g.t & 7;
+    // Sums over the group: each thread's run totals t0, t1 become the exclusive prefixes (in
+    // run order) and s0, s1 the totals over the column; area: 2 float4 per warp.
+    auto group_scan = [&](Z &t0, Z &t1, Z &s0, Z &s1, float4 *area, Z *red, float4 *red_area) {
+        Z i0 = t0, i1 = t1;
+        warp_inclusive_scan(lane, i0, i1);
+        Z e0 = zshfl_up(i0, 1), e1 = zshfl_up(i1, 1);
+        if (lane == 0) e0 = e1 = kZero;
+        if (lane == 31) {
+            stz(area, 2 * warp, i0);
+            stz(area, 2 * warp + 1, i1);
+        }
+        if (red) {                                   // warp sums of red[0..1] beside the scan
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                red[0] = zadd(red[0], zshfl_xor(red[0], o));
+                red[1] = zadd(red[1], zshfl_xor(red[1], o));
+            }
+            if (lane == 0) {
+                stz(red_area, 2 * warp, red[0]);
+                stz(red_area, 2 * warp + 1, red[1]);
+            }
+        }
+        g.sync();
+        Z w0 = kZero, w1 = kZero;
+        s0 = s1 = kZero;
+        for (int w = 0; w < nw; w++) {
+            if (w == warp) {
+                w0 = s0;
+                w1 = s1;
+            }
+            s0 = zadd(s0, ldz(area, 2 * w));
+            s1 = zadd(s1, ldz(area, 2 * w + 1));
+        }
+        t0 = zadd(w0, e0);
+        t1 = zadd(w1, e1);
+        if (red) {
+            red[0] = ldz(red_area, 0);
+            red[1] = ldz(red_area, 1);
+            for (int w = 1; w < nw; w++) {
+                red[0] = zadd(red[0], ldz(red_area, 2 * w));
+                red[1] = zadd(red[1], ldz(red_area, 2 * w + 1));
+            }
+        }
+    };
+    // pass 1: prefix sums of chat within the run (per parity); psi: sums of q chat
+    Z t0 = kZero, t1 = kZero, q[2] = {kZero, kZero};
+    for (int k = k0; k < k1; k++) {
+        const Z c = chat(k);
+        F2 qk{0.f, 0.f};
+        if (SPACE == 2) qk = df::add(F2{(float)k * (float)k, 0.f}, dneg(a.ls[k & 1][1]));   // k^2 exact
+        if (k & 1) {
+            t1 = zadd(t1, c);
+            stz(W, k ^ rx, t1);
+            if (SPACE == 2) q[1] = zfma(qk, c, q[1]);
+        } else {
+            t0 = zadd(t0, c);
+            stz(W, k ^ rx, t0);
+            if (SPACE == 2) q[0] = zfma(qk, c, q[0]);
+        }
+    }
+    Z s0, s1;
+    group_scan(t0, t1, s0, s1, scr, SPACE == 2 ? q : nullptr, scr + 8);
+    const Z cr0 = zscale(s0, a.ls[0][0]), cr1 = zscale(s1, a.ls[1][0]);
+    if (SPACE == 1) {
+        for (int k = k0; k < kn; k++) {
+            const bool odd = k & 1;
+            const F2 om{0.5f * (float)(k + 1), 0.f};
+            stz(W, k ^ rx, zsubmul(zadd(ldz(W, k ^ rx), odd ? t1 : t0), odd ? cr1 : cr0, om));
+        }
+    } else {
+        const Z cq0 = zscale(q[0], a.ls[0][2]), cq1 = zscale(q[1], a.ls[1][2]);
+        const F2 sixth = ratio(1.0f, 6.0f);
+        // pass 2: v, then the prefix sums of (K + 1) v within the run
+        Z z0 = kZero, z1 = kZero;
+        for (int k = k0; k < kn; k++) {
+            const bool odd = k & 1;
+            const float kf = (float)k, om = 0.5f * (kf + 1.0f);
+            const F2 s2 = nrm(df::mul(nrm(df::mul(df::two_prod(kf, kf + 1.0f), kf + 2.0f)), sixth));
+            const F2 Q = df::add(s2, dneg(df::mul(a.ls[k & 1][1], om)));
+            Z v = zsubmul(zadd(ldz(W, k ^ rx), odd ? t1 : t0), odd ? cr1 : cr0, F2{om, 0.f});
+            v = zsubmul(v, odd ? cq1 : cq0, Q);
+            const Z w = zmulf(v, kf + 1.0f);
+            if (odd) {
+                z1 = zadd(z1, w);
+                stz(W, k ^ rx, z1);
+            } else {
+                z0 = zadd(z0, w);
+                stz(W, k ^ rx, z0);
+            }
+        }
+        Z u0, u1;
+        group_scan(z0, z1, u0, u1, scr + 16, nullptr, nullptr);
+        for (int k = k0; k < kn; k++)
+            stz(W, k ^ rx, zscale(zadd(ldz(W, k ^ rx), (k & 1) ? z1 : z0), ratio(1.0f, (float)(k + 1))));
+    }
+    g.sync();
+    for (int k = g.t; k < N; k += g.nt) y[k] = k < n ? ztof64(ldz(W, k ^ ((k >> lc) & 7))) : make_double2(0.0, 0.0);
+}
+
+// KIND: 0 inverse, 1 scalar products, 2 forward (phi, psi: forward_ls on the Chebyshev
+// coefficients).  SPACE: 0 T_k, 1 phi_k, 2 psi_k.  GL: Gauss-Lobatto points (a compile-time choice, so the Gauss kernels carry none
 // of its code).
 template <int KIND, int SPACE, bool GL>
 __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *in, double *out) {
     extern __shared__ float4 sm[];
     const int N = a.N, lg = a.lg, f3 = a.f3, half = N >> 1, M = N - 1;
+    // slot swizzle of A (swz) for the scalar products and forward transforms, whose
+    // post-processing reads the digit-reversed positions two to four times per point; the
+    // inverse reads them once, where the swizzle's own instructions cost more than it saves
+    const int sw = (KIND != 0 && lg >= 7) ? lg - 4 : 0;
     const float4 *tw = sm;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + a.n_tw);
     for (int t = threadIdx.x; t < a.n_tw; t += blockDim.x) sm[t] = __ldg(a.tw + t);
@@ -349,6 +572,7 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
         if (g.t == 0 && next < a.n_modes) bulk_load(R, in + 2 * next * (long)N, col_bytes, bar);
     };
     auto mkz = [&](int k) { return zld(a.mk + k); };
+    constexpr bool kLs = KIND == 2 && SPACE != 0;   // forward phi / psi (forward_ls)
     for (; mode < a.n_modes; mode += groups_total) {
         const long next = mode + groups_total;
         if (!g.all(mbar_wait(bar, parity))) {
@@ -391,10 +615,10 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     if (k >= 1 && k < M) stz(A, 2 * M - k, t);
                 }
                 prefetch_next(next);
-                fft_dif<false, kRawForward>(A, lg, f3, tw, g);
+                fft_dif<false, kRawForward>(A, lg, f3, tw, g, sw);
                 for (int i = g.t; i < N; i += g.nt) {
                     const Z e = zadd(t0, (i & 1) ? Z{dneg(tM.re), dneg(tM.im)} : tM);
-                    y[i] = ztof64(zhalf(zadd(ldz(A, dpos(i, lg, f3)), e)));
+                    y[i] = ztof64(zhalf(zadd(ldz(A, swz(dpos(i, lg, f3), sw)), e)));
                 }
                 g.sync();
                 continue;
@@ -412,10 +636,10 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                 if (k != half) stz(A, N - k, zhalf(zi(zmul_raw(zadd_raw(t2, zmi(t1)), w))));
             }
             prefetch_next(next);
-            fft_dif<true, true>(A, lg, f3, tw, g);
+            fft_dif<true, true>(A, lg, f3, tw, g, sw);
             for (int m = g.t; m < N; m += g.nt) {
                 const int src = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
-                y[m] = ztof64(ldz(A, dpos(src, lg, f3)));
+                y[m] = ztof64(ldz(A, swz(dpos(src, lg, f3), sw)));
             }
         } else {
             if (GL) {
@@ -427,49 +651,55 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
                     stz(A, m, v);
                     if (m >= 1 && m < M) stz(A, 2 * M - m, v);
                 }
-                prefetch_next(next);
-                fft_dif<false, kRawForward>(A, lg, f3, tw, g);
+                if (kLs)
+                    g.sync();                  // A written by every thread before the FFT reads it
+                else
+                    prefetch_next(next);       // (its barrier orders A's writes the same way)
+                fft_dif<false, kRawForward>(A, lg, f3, tw, g, sw);
             } else {
-            // values -> Makhoul order in A; R free for the next column
+            // values -> Makhoul order in A; R free for the next column (the forward phi / psi
+            // kernels use R as forward_ls's work buffer and load the next column after it)
             for (int m = g.t; m < N; m += g.nt) {
                 const int dst = (m & 1) ? N - 1 - (m >> 1) : (m >> 1);
                 stz(A, dst, zfromf64(xs[m]));
             }
-            prefetch_next(next);
-            fft_dif<false, kRawForward>(A, lg, f3, tw, g);
+            if (kLs)
+                g.sync();
+            else
+                prefetch_next(next);
+            fft_dif<false, kRawForward>(A, lg, f3, tw, g, sw);
             // C_k (DCT-II) in place: the pair (k, N-k) is read and written by one thread at
             // positions dpos(k), dpos(N-k)
             for (int k = g.t; k <= half; k += g.nt) {
                 if (k == 0) continue;                                  // C_0 = V_0
                 const int pk = dpos(k, lg, f3), pn = dpos(N - k, lg, f3);
                 const Z w = mkz(k);
-                const Z P = zmul(ldz(A, pk), w);
-                const Z Q = zmulc(ldz(A, pn), w);
-                stz(A, pk, zhalf(zadd(P, Q)));
-                if (k != half) stz(A, pn, zhalf(zi(zsub(P, Q))));
+                const Z P = zmul(ldz(A, swz(pk, sw)), w);
+                const Z Q = zmulc(ldz(A, swz(pn, sw)), w);
+                stz(A, swz(pk, sw), zhalf(zadd(P, Q)));
+                if (k != half) stz(A, swz(pn, sw), zhalf(zi(zsub(P, Q))));
             }
             }
             g.sync();
-            auto C = [&](int k) { return ldz(A, dpos(k, lg, f3)); };
-            if (KIND == 2 && SPACE == 0) {
-                // uhat_k = S_k / (pi c_k / 2): Gauss: C_k 2 / (N c_k) (c_0 = 2);
-                // Gauss-Lobatto: Y_k / (M c_k) (c_0 = c_M = 2); N, M powers of two
-                // (1 / M or 2 / N is a power of two for power-of-two lengths; with a factor 3
-                // it is applied as a float-float quotient)
-                if (GL) {
-                    const float sc = 1.0f / (float)M;
-                    const F2 scd = ratio(1.0f, (float)M);
-                    for (int k = g.t; k < N; k += g.nt) {
-                        const float h = (k == 0 || k == M) ? 0.5f : 1.0f;
-                        y[k] = ztof64(f3 == 1 ? zpow2(C(k), h * sc) : zpow2(zscale(C(k), scd), h));
-                    }
+            auto C = [&](int k) { return ldz(A, swz(dpos(k, lg, f3), sw)); };
+            if (KIND == 2) {
+                // Chebyshev coefficients chat_k = S_k / (pi c_k / 2): Gauss: C_k 2 / (N c_k)
+                // (c_0 = 2); Gauss-Lobatto: Y_k / (M c_k) (c_0 = c_M = 2).  2 / N or 1 / M is a
+                // power of two for power-of-two lengths; with a factor 3 it is applied as a
+                // float-float quotient.
+                const float sc = GL ? 1.0f / (float)M : 2.0f / (float)N;
+                const F2 scd = GL ? ratio(1.0f, (float)M) : ratio(2.0f, (float)N);
+                auto chat = [&](int k) -> Z {
+                    const float h = (k == 0 || (GL && k == M)) ? 0.5f : 1.0f;
+                    return f3 == 1 ? zpow2(C(k), h * sc) : zpow2(zscale(C(k), scd), h);
+                };
+                if (SPACE == 0) {
+                    for (int k = g.t; k < N; k += g.nt) y[k] = ztof64(chat(k));
                 } else {
-                    const float sc = 2.0f / (float)N;
-                    const F2 scd = ratio(2.0f, (float)N);
-                    for (int k = g.t; k < N; k += g.nt) {
-                        const float h = k == 0 ? 0.5f : 1.0f;
-                        y[k] = ztof64(f3 == 1 ? zpow2(C(k), h * sc) : zpow2(zscale(C(k), scd), h));
-                    }
+                    forward_ls<SPACE, GL>(a, R, sm + a.n_tw + 8 + (long)a.n_groups * kBuffers * a.stride +
+                                                     (long)gi * kScratch,
+                                          g, chat, n, y);
+                    prefetch_next(next);
                 }
             } else {
                 // scalar products S_l (Algorithm fst, forwardScalar)
@@ -492,85 +722,6 @@ __global__ void __launch_bounds__(768) transform_kernel(TrArgs a, const double *
     }
 }
 
-// Forward transform in phi / psi, second pass: B uhat = S in place on every column (S from
-// the scalar-product pass).  B is the same for every mode, so its LU rows (mass_rows: planes
-// (l1, l2), (1/d, U_{i,i+1}/d), (U_{i,i+2}/d, 0)) serve all chains from L1 / L2.
-// One thread per (mode, parity) chain, as in the solves: the forward sweep overwrites each
-// row with y (float-float, 16 bytes, in the row's own slot), the back substitution
-// overwrites it with uhat (float64); rows are fetched PB at a time ahead of their stores.
-template <int BW, int PB>
-__global__ void __launch_bounds__(128) mass_sweep_kernel(const float4 *T, int RM, int N, int n, long count,
-                                                         double *col0) {
-    using chains::CF2;
-    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (tid >= 2 * count) return;
-    const long mode = tid >> 1;
-    const int h = (int)(tid & 1);
-    double2 *col = reinterpret_cast<double2 *>(col0) + mode * N;
-    float4 *ys = reinterpret_cast<float4 *>(col);
-    const int R = (n - h + 1) / 2;
-    const float4 *TL = T + (long)(0 + h) * RM, *TB = T + (long)(2 + h) * RM, *TF = T + (long)(4 + h) * RM;
-    const F2 zero{0.f, 0.f};
-    CF2 y1{zero, zero}, y2 = y1;
-    for (int i0 = 0; i0 < R; i0 += PB) {
-        double2 sb[PB];
-        float4 lb[PB];
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = min(i0 + q, R - 1);
-            sb[q] = col[2 * i + h];
-            lb[q] = __ldg(TL + i);
-        }
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            if (i0 + q < R) {
-                CF2 y;
-                y.re = df::from_f64(sb[q].x);
-                y.im = df::from_f64(sb[q].y);
-                if (BW == 2) {
-                    y.re = chains::fnma(hi2(lb[q]), y2.re, y.re);
-                    y.im = chains::fnma(hi2(lb[q]), y2.im, y.im);
-                }
-                y.re = chains::fnma(lo2(lb[q]), y1.re, y.re);
-                y.im = chains::fnma(lo2(lb[q]), y1.im, y.im);
-                ys[2 * (i0 + q) + h] = make_float4(y.re.hi, y.re.lo, y.im.hi, y.im.lo);
-                y2 = y1;
-                y1 = y;
-            }
-        }
-    }
-    CF2 x1{zero, zero}, x2 = x1;
-    for (int i0 = R - 1; i0 >= 0; i0 -= PB) {
-        float4 yb[PB], bb[PB], fb[PB];
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = max(i0 - q, 0);
-            yb[q] = ys[2 * i + h];
-            bb[q] = __ldg(TB + i);
-            if (BW == 2) fb[q] = __ldg(TF + i);
-        }
-#pragma unroll
-        for (int q = 0; q < PB; q++) {
-            const int i = i0 - q;
-            if (i >= 0) {
-                const CF2 yi{F2{yb[q].x, yb[q].y}, F2{yb[q].z, yb[q].w}};
-                CF2 x;
-                x.re = nrm(df::mul(lo2(bb[q]), yi.re));
-                x.im = nrm(df::mul(lo2(bb[q]), yi.im));
-                if (BW == 2) {
-                    x.re = chains::fnma(lo2(fb[q]), x2.re, x.re);
-                    x.im = chains::fnma(lo2(fb[q]), x2.im, x.im);
-                }
-                x.re = chains::fnma(hi2(bb[q]), x1.re, x.re);
-                x.im = chains::fnma(hi2(bb[q]), x1.im, x.im);
-                col[2 * i + h] = make_double2(df::to_f64(x.re), df::to_f64(x.im));
-                x2 = x1;
-                x1 = x;
-            }
-        }
-    }
-}
-
 template <int KIND, int SPACE, bool GL>
 const void *kernel_ptr() {
     return reinterpret_cast<const void *>(&transform_kernel<KIND, SPACE, GL>);
@@ -580,12 +731,12 @@ const void *kernel_of(int kind, int space, bool gl) {
     static const void *const k[2][3][3] = {
         {{kernel_ptr<0, 0, false>(), kernel_ptr<0, 1, false>(), kernel_ptr<0, 2, false>()},
          {kernel_ptr<1, 0, false>(), kernel_ptr<1, 1, false>(), kernel_ptr<1, 2, false>()},
-         {kernel_ptr<2, 0, false>(), kernel_ptr<1, 1, false>(), kernel_ptr<1, 2, false>()}},
+         {kernel_ptr<2, 0, false>(), kernel_ptr<2, 1, false>(), kernel_ptr<2, 2, false>()}},
         {{kernel_ptr<0, 0, true>(), kernel_ptr<0, 1, true>(), kernel_ptr<0, 2, true>()},
          {kernel_ptr<1, 0, true>(), kernel_ptr<1, 1, true>(), kernel_ptr<1, 2, true>()},
-         {kernel_ptr<2, 0, true>(), kernel_ptr<1, 1, true>(), kernel_ptr<1, 2, true>()}},
+         {kernel_ptr<2, 0, true>(), kernel_ptr<2, 1, true>(), kernel_ptr<2, 2, true>()}},
     };
-    return k[gl ? 1 : 0][kind][space];   // forward phi / psi: their scalar-product kernels
+    return k[gl ? 1 : 0][kind][space];
 }
 
 inline float4 pair4(long double a, long double b) {
@@ -601,51 +752,6 @@ int ilog2(int v) {
 
 // Warps per mode group of an N-mode plan (more threads per column for larger N).
 int group_warps(int N) { return std::max(1, std::min(4, N / 256)); }
-
-// Mass-solve tables of one space in the three planes mass_sweep_kernel reads (B rows:
-// diagonal, +1, +2 per parity chain), from the unpivoted LU of each parity chain of B in
-// long double arithmetic, rounded to float-float pairs: plane f, parity h, row i at
-// [(2 f + h) RM + i]:  f = 0 (l1, l2) = (L_{i,i-1}, L_{i,i-2});  f = 1 (1/d, U_{i,i+1}/d);
-// f = 2 (U_{i,i+2}/d, 0).
-void mass_rows(int N, int space, int RM, std::vector<float4> &T, bool gl) {
-    const long double pi = 3.141592653589793238462643383279502884L;
-    const int n = space == 1 ? N - 2 : N - 4;
-    T.assign((size_t)2 * RM * 3, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int h = 0; h < 2; h++) {
-        const int R = (n - h + 1) / 2;
-        std::vector<long double> dg(R), s1(R, 0.0L), s2(R, 0.0L);
-        for (int i = 0; i < R; i++) {
-            const long double k = 2 * i + h, ck = (2 * i + h == 0) ? 2.0L : 1.0L;
-            // Gauss-Lobatto: c_{N-1} = 2 in the highest row (Table tab:matrices)
-            const long double ck2 = (gl && 2 * i + h + 2 == N - 1) ? 2.0L : 1.0L;
-            const long double ck4 = (gl && 2 * i + h + 4 == N - 1) ? 2.0L : 1.0L;
-            if (space == 1) {
-                dg[i] = pi / 2 * (ck + ck2);
-                if (i + 1 < R) s1[i] = -pi / 2;
-            } else {
-                const long double r2 = (k + 2) / (k + 3), r1 = (k + 1) / (k + 3);
-                dg[i] = pi / 2 * (ck + 4 * r2 * r2 + ck4 * r1 * r1);
-                if (i + 1 < R) s1[i] = -pi * (r2 + (k + 4) * (k + 1) / ((k + 5) * (k + 3)));
-                if (i + 2 < R) s2[i] = pi / 2 * r1;
-            }
-        }
-        // unpivoted banded LU: B = L U, L unit lower (l1, l2), U (d, e1, e2); B symmetric
-        std::vector<long double> l1(R, 0.0L), l2(R, 0.0L), d(R), e1(R), e2(R);
-        for (int i = 0; i < R; i++) {
-            if (i >= 2) l2[i] = s2[i - 2] / d[i - 2];
-            if (i >= 1) l1[i] = (s1[i - 1] - (i >= 2 ? l2[i] * e1[i - 2] : 0.0L)) / d[i - 1];
-            d[i] = dg[i] - (i >= 1 ? l1[i] * e1[i - 1] : 0.0L) - (i >= 2 ? l2[i] * e2[i - 2] : 0.0L);
-            e1[i] = s1[i] - (i >= 1 ? l1[i] * e2[i - 1] : 0.0L);
-            e2[i] = s2[i];
-        }
-        auto at = [&](int f, int i) -> float4 & { return T[(size_t)(2 * f + h) * RM + i]; };
-        for (int i = 0; i < R; i++) {
-            at(0, i) = pair4(l1[i], l2[i]);
-            at(1, i) = pair4(1.0L / d[i], e1[i] / d[i]);
-            at(2, i) = pair4(e2[i] / d[i], 0.0L);
-        }
-    }
-}
 
 }  // namespace
 
@@ -677,12 +783,34 @@ int twiddle_count(int NF) {
 // Tables of the transforms of an N-mode plan (float4 units, float-float pairs):
 //   [0, ntw)                per-pass twiddles of fft_dif
 //   [ntw, ntw + N/2 + 1)    mk[k] = e^{-i pi k/(2N)}, k = 0 .. N/2
-//   then the mass-solve rows of phi (2 RMd 3) and of psi (2 RMb 3).
+// and the constants of the forward transforms' least-squares correction (forward_ls).
 cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (!transform_supported(p)) return cudaSuccess;
     const int N = p.N, NF = fft_length(p), f3 = fft_f3(NF), L2 = NF / f3, lg = ilog2(L2);
     const long double pi = 3.141592653589793238462643383279502884L;
-    const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
+    // per parity h over the Chebyshev indices K = h, h + 2, .. < N with omega_K = 1 / c_K
+    // (1/2 at K = 0, and at K = N - 1 on Gauss-Lobatto points):
+    // rho = 1 / sum omega, kappa = sum omega K^2 / sum omega, tau = 1 / sum omega (K^2 - kappa)^2
+    for (int h = 0; h < 2; h++) {
+        long double so = 0.0L, sk = 0.0L;
+        for (int K = h; K < N; K += 2) {
+            const long double om = (K == 0 || (p.gl && K == N - 1)) ? 0.5L : 1.0L;
+            so += om;
+            sk += om * (long double)K * K;
+        }
+        const long double kap = sk / so;
+        long double sq = 0.0L;
+        for (int K = h; K < N; K += 2) {
+            const long double om = (K == 0 || (p.gl && K == N - 1)) ? 0.5L : 1.0L, q = (long double)K * K - kap;
+            sq += om * q * q;
+        }
+        const long double c[3] = {1.0L / so, kap, 1.0L / sq};
+        for (int j = 0; j < 3; j++) {
+            const float hi = (float)c[j];
+            p.tr_ls[h][j][0] = hi;
+            p.tr_ls[h][j][1] = (float)(c[j] - (long double)hi);
+        }
+    }
     const int ntw = twiddle_count(NF), nmk = N / 2 + 1;
     std::vector<float4> tab;
     tab.reserve((size_t)ntw + nmk);
@@ -707,12 +835,6 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
         const long double ang = -pi * k / (2 * (long double)N);
         tab.push_back(pair4(cosl(ang), sinl(ang)));
     }
-    std::vector<float4> md, mb;
-    mass_rows(N, 1, RMd, md, p.gl);
-    mass_rows(N, 2, RMb, mb, p.gl);
-    p.tr_off_mass = (int)tab.size();
-    tab.insert(tab.end(), md.begin(), md.end());
-    tab.insert(tab.end(), mb.begin(), mb.end());
     p.tr_ntw = ntw;
     bytes += (long long)(tab.size() * sizeof(float4));
     cudaError_t e = cudaMalloc((void **)&p.d_tr, tab.size() * sizeof(float4));
@@ -721,8 +843,9 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     // launch shape per (kind, space): G warps per mode group (more threads per column for
     // larger N), groups per block from the shared memory budget (twiddles, barriers,
-    // nbuf buffers per group) and the kernel's 768-thread bound; persistent grid from the
-    // occupancy.  A (kind, space) whose buffers do not fit gets no shape (unsupported).
+    // nbuf buffers per group, and the forward phi / psi kernels' scratch) and the kernel's
+    // 768-thread bound; persistent grid from the occupancy.  A (kind, space) whose buffers
+    // do not fit gets no shape (unsupported).
     int dev = 0, smem_max = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
@@ -734,8 +857,8 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     const long fixed = (long)(ntw + 8) * sizeof(float4);
     for (int kind = 0; kind < 3; kind++)
         for (int space = 0; space < 3; space++) {
-            if (kind == 2 && space != 0) continue;     // forward phi / psi: the scalar-product kernels
-            const long per_group = (long)kBuffers * stride * sizeof(float4);
+            const long per_group = ((long)kBuffers * stride + (kind == 2 && space != 0 ? kScratch : 0)) *
+                                   (long)sizeof(float4);
             const int max_threads = 768;                 // the kernel's bound
             const int groups = (int)std::min<long>(std::min(8, max_threads / (32 * G)), (smem_max - fixed) / per_group);
             p.tr_groups[kind][space] = 0;
@@ -760,18 +883,12 @@ cudaError_t transform_setup(Plan &p, long long &bytes, cudaStream_t s) {
     return cudaSuccess;
 }
 
-bool transform_shape_ok(const Plan &p, int kind, int space) {
-    const int k = (kind == SHEN_TRANSFORM_FORWARD && space != SHEN_SPACE_CHEBYSHEV) ? SHEN_TRANSFORM_SCALAR : kind;
-    return p.d_tr && p.tr_groups[k][space] > 0;
-}
+bool transform_shape_ok(const Plan &p, int kind, int space) { return p.d_tr && p.tr_groups[kind][space] > 0; }
 
 cudaError_t launch_transform(const Plan &p, int kind, int space, long count, const double *in, double *out,
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    const int N = p.N;
-    // the forward transforms in phi, psi: the scalar products, then the mass solve in place
-    const bool mass = kind == SHEN_TRANSFORM_FORWARD && space != SHEN_SPACE_CHEBYSHEV;
-    const int k = mass ? SHEN_TRANSFORM_SCALAR : kind;
+    const int N = p.N, k = kind;
     TrArgs a;
     a.N = N;
     a.f3 = fft_f3(fft_length(p));
@@ -787,20 +904,14 @@ cudaError_t launch_transform(const Plan &p, int kind, int space, long count, con
     const float ph = (float)pn;
     a.pi_over_N = F2{ph, (float)(pn - (double)ph)};
     a.err = p.d_err + 3;
+    for (int h = 0; h < 2; h++)
+        for (int j = 0; j < 3; j++) a.ls[h][j] = F2{p.tr_ls[h][j][0], p.tr_ls[h][j][1]};
     const long need = (count + a.n_groups - 1) / a.n_groups;
     const dim3 grid((unsigned)std::max<long>(1, std::min<long>(p.tr_grid[k][space], need))),
         block((unsigned)(32 * a.G * a.n_groups));
     void *args[] = {&a, &in, &out};
-    cudaError_t e = cudaLaunchKernel(kernel_of(k, space, p.gl), grid, block, args, (size_t)p.tr_smem[k][space], s);
-    if (e != cudaSuccess || !mass) return e;
-    const int RMd = (N - 2 + 1) / 2, RMb = (N - 4 + 1) / 2;
-    const float4 *T = p.d_tr + p.tr_off_mass;
-    const unsigned blocks = (unsigned)((2 * count + 127) / 128);
-    if (space == SHEN_SPACE_DIRICHLET)
-        mass_sweep_kernel<1, 8><<<blocks, 128, 0, s>>>(T, RMd, N, N - 2, count, out);
-    else
-        mass_sweep_kernel<2, 4><<<blocks, 128, 0, s>>>(T + (size_t)2 * RMd * 3, RMb, N, N - 4, count, out);
-    return cudaGetLastError();
+    const cudaError_t e = cudaLaunchKernel(kernel_of(k, space, p.gl), grid, block, args, (size_t)p.tr_smem[k][space], s);
+    return e;
 }
 
 }  // namespace shen
