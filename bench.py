@@ -110,8 +110,7 @@ def measured_traffic(kind, rows):
     return entry * rows
 
 
-# kernel name (as ncu prints it) -> traffic kinds its per-launch bytes stand for; the
-# forward transform in phi / psi is the scalar-product kernel plus one mass sweep
+# kernel name (as ncu prints it) -> traffic kinds its per-launch bytes stand for
 TRAFFIC_KERNELS = (
     (r"bih_df_kernel<0>", ("biharmonic:df",)),
     (r"helm_df_kernel<0>", ("helmholtz:df",)),
@@ -122,11 +121,11 @@ TRAFFIC_KERNELS = (
     (r"transform_kernel<0, 1, (0|false)>", ("transform:inverse_dirichlet",)),
     (r"transform_kernel<0, 2, (0|false)>", ("transform:inverse_biharmonic",)),
     (r"transform_kernel<1, 0, (0|false)>", ("transform:scalar_chebyshev",)),
-    (r"transform_kernel<1, 1, (0|false)>", ("transform:scalar_dirichlet", "transform:forward_dirichlet")),
-    (r"transform_kernel<1, 2, (0|false)>", ("transform:scalar_biharmonic", "transform:forward_biharmonic")),
+    (r"transform_kernel<1, 1, (0|false)>", ("transform:scalar_dirichlet",)),
+    (r"transform_kernel<1, 2, (0|false)>", ("transform:scalar_biharmonic",)),
     (r"transform_kernel<2, 0, (0|false)>", ("transform:forward_chebyshev",)),
-    (r"mass_sweep_kernel<1, 8>", ("transform:forward_dirichlet",)),
-    (r"mass_sweep_kernel<2, 4>", ("transform:forward_biharmonic",)),
+    (r"transform_kernel<2, 1, (0|false)>", ("transform:forward_dirichlet",)),
+    (r"transform_kernel<2, 2, (0|false)>", ("transform:forward_biharmonic",)),
 )
 
 
@@ -164,7 +163,7 @@ def write_traffic(csv_paths, w):
                 per_kind[k] = per_kind.get(k, 0.0) + sum(launches) / len(launches)
     bpr = {k: round(v / n_rows, 2) for k, v in sorted(per_kind.items())}
     out = {"note": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per complex row (n_modes * N rows) "
-                   "for one launch (the forward transform in phi / psi: its two kernels), from an ncu capture "
+                   "for one launch, from an ncu capture "
                    f"on the N={w['N']}, {w['Nx']}x{w['Nz']} workload, written by bench.py --write-traffic; each "
                    "figure is valid while its kernels' CUDA sources hash to sources_sha1[group] "
                    "(groups and files: bench.py TRAFFIC_SOURCES)",

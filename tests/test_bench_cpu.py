@@ -42,21 +42,21 @@ def test_write_and_read_back(tmp_path, monkeypatch):
          1, 1),                                                          # other shape: not the table's
         ("void shen::<unnamed>::transform_kernel<1, 1, 0>(shen::<unnamed>::TrArgs, const double *, double *)",
          768 * 16, 768 * 16),
-        ("void unnamed>::mass_sweep_kernel<1, 8>(const float4 *, int, int, int, long, double *)",
-         768 * 30, 768 * 29),
+        ("void shen::<unnamed>::transform_kernel<2, 1, 0>(shen::<unnamed>::TrArgs, const double *, double *)",
+         768 * 16, 768 * 15),
     ])
     out = bench.write_traffic(path, W)
     bpr = out["bytes_per_row"]
     assert bpr["biharmonic:df"] == pytest.approx(81.0)                   # mean of 80 and 82
     assert bpr["transform:scalar_dirichlet"] == pytest.approx(32.0)
-    assert bpr["transform:forward_dirichlet"] == pytest.approx(32.0 + 59.0)
+    assert bpr["transform:forward_dirichlet"] == pytest.approx(31.0)
     assert "helmholtz:df" not in bpr
     assert out["launches"]["bih_df_kernel<0>"] == 2
     saved = json.loads((tmp_path / "traffic.json").read_text())
     assert saved["sources_sha1"] == {g: bench.sources_sha1(n) for g, n in bench.TRAFFIC_SOURCES.items()}
     # read back, scaled to another workload's rows
     assert bench.measured_traffic("biharmonic:df", 1000) == pytest.approx(81000.0)
-    assert bench.measured_traffic("transform:forward_dirichlet", 10) == pytest.approx(910.0)
+    assert bench.measured_traffic("transform:forward_dirichlet", 10) == pytest.approx(310.0)
     assert bench.measured_traffic("helmholtz:df", 10) is None
 
 
