@@ -78,10 +78,7 @@ def test_scalar_matches_oracle(N, space):
 
 
 def _forward_cases():
-    # (biharmonic, 1024) is left to the error test below: its L^-1 has a double
-    # characteristic root at 1, so the chunk-local homogeneous solutions grow like the
-    # chunk length and the residual is no longer bounded by u |B| |uhat|
-    return [(N, s) for N in (8, 16, 24, 64, 96, 128, 1024) for s in tr.SPACES if not (s == "biharmonic" and N > 128)]
+    return [(N, s) for N in (8, 16, 24, 64, 96, 128, 1024) for s in tr.SPACES]
 
 
 @pytest.mark.parametrize("N,space", _forward_cases())
