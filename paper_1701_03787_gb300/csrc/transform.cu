@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "chains.cuh"
+#include "colgroup.cuh"
 #include "df.cuh"
 #include "shen_internal.h"
 
@@ -43,19 +44,8 @@ namespace shen {
 namespace {
 
 using df::F2;
+using namespace colg;
 
-struct Z {   // complex float-float
-    F2 re, im;
-};
-
-__device__ __forceinline__ Z ldz(const float4 *A, int i) {
-    const float4 v = A[i];
-    return Z{F2{v.x, v.y}, F2{v.z, v.w}};
-}
-__device__ __forceinline__ void stz(float4 *A, int i, Z v) { A[i] = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
-__device__ __forceinline__ F2 dneg(F2 a) { return F2{-a.hi, -a.lo}; }
-__device__ __forceinline__ F2 nrm(F2 a) { return df::fast_two_sum(a.hi, a.lo); }
-__device__ __forceinline__ Z zadd(Z a, Z b) { return Z{df::add(a.re, b.re), df::add(a.im, b.im)}; }
 // Sum without the final renormalisation: hi carries the float32 sum, lo the exact error of
 // it plus the low parts, so hi + lo is the float-float sum.  lo may exceed half an ulp of
 // hi (after cancellation), but the absolute error stays that of float32 arithmetic on lo,
@@ -71,7 +61,6 @@ __device__ __forceinline__ Z zadd_raw(Z a, Z b) { return Z{add_raw(a.re, b.re), 
 __device__ __forceinline__ Z zsub_raw(Z a, Z b) {
     return Z{add_raw(a.re, F2{-b.re.hi, -b.re.lo}), add_raw(a.im, F2{-b.im.hi, -b.im.lo})};
 }
-__device__ __forceinline__ Z zsub(Z a, Z b) { return Z{df::add(a.re, dneg(b.re)), df::add(a.im, dneg(b.im))}; }
 __device__ __forceinline__ Z zmul_raw(Z a, Z w) {    // a w, raw sums
     return Z{add_raw(df::mul(a.re, w.re), dneg(df::mul(a.im, w.im))), add_raw(df::mul(a.re, w.im), df::mul(a.im, w.re))};
 }
@@ -86,18 +75,10 @@ __device__ __forceinline__ Z zmulc(Z a, Z w) {       // a conj(w)
     return Z{df::add(df::mul(a.re, w.re), df::mul(a.im, w.im)),
              df::add(df::mul(a.im, w.re), dneg(df::mul(a.re, w.im)))};
 }
-__device__ __forceinline__ Z zneg(Z a) { return Z{dneg(a.re), dneg(a.im)}; }
 __device__ __forceinline__ Z zi(Z a) { return Z{dneg(a.im), a.re}; }      // i a
 __device__ __forceinline__ Z zmi(Z a) { return Z{a.im, dneg(a.re)}; }     // -i a
-__device__ __forceinline__ Z zhalf(Z a) {
-    return Z{F2{0.5f * a.re.hi, 0.5f * a.re.lo}, F2{0.5f * a.im.hi, 0.5f * a.im.lo}};
-}
 __device__ __forceinline__ Z zpow2(Z a, float s) {   // a s, s a power of two (exact)
     return Z{F2{s * a.re.hi, s * a.re.lo}, F2{s * a.im.hi, s * a.im.lo}};
-}
-__device__ __forceinline__ Z zscale(Z a, F2 s) { return Z{nrm(df::mul(a.re, s)), nrm(df::mul(a.im, s))}; }
-__device__ __forceinline__ Z zfma(F2 s, Z a, Z b) {  // b + s a
-    return Z{df::add(b.re, df::mul(a.re, s)), df::add(b.im, df::mul(a.im, s))};
 }
 __device__ __forceinline__ Z zfma_raw(F2 s, Z a, Z b) {  // b + s a, raw sum
     return Z{add_raw(b.re, df::mul(a.re, s)), add_raw(b.im, df::mul(a.im, s))};
@@ -106,10 +87,7 @@ __device__ __forceinline__ Z zld(const float4 *p) {
     const float4 v = __ldg(p);
     return Z{F2{v.x, v.y}, F2{v.z, v.w}};
 }
-__device__ __forceinline__ Z zfromf64(double2 v) { return Z{df::from_f64(v.x), df::from_f64(v.y)}; }
-__device__ __forceinline__ double2 ztof64(Z v) { return make_double2(df::to_f64(v.re), df::to_f64(v.im)); }
 
-constexpr Z kZero{F2{0.f, 0.f}, F2{0.f, 0.f}};
 
 // n / d as a float-float, for integers 0 < n, d < 2^13 held exactly in float32: hi from an
 // approximate quotient, the remainder n - hi d exactly by one FMA (a multiple of hi's ulp,
@@ -158,28 +136,6 @@ __device__ __forceinline__ int dpos(int k, int lg, int f3) {
 __device__ __forceinline__ F2 lo2(float4 v) { return F2{v.x, v.y}; }
 __device__ __forceinline__ F2 hi2(float4 v) { return F2{v.z, v.w}; }
 
-// Thread group of one mode column: G warps (32 G threads) synchronised by the named
-// barrier `id` (ids 1 .. 15; 0 is __syncthreads).
-struct Group {
-    int t, nt, id;   // thread index in the group, group size, barrier id
-    __device__ __forceinline__ void sync() const {
-        if (nt == 32)
-            __syncwarp();
-        else
-            asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nt) : "memory");
-    }
-    // AND of v over the group (also a barrier)
-    __device__ __forceinline__ bool all(bool v) const {
-        uint32_t r;
-        asm volatile(
-            "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, %2, %3, pi;\n"
-            " selp.u32 %0, 1, 0, po;\n}\n"
-            : "=r"(r)
-            : "r"((uint32_t)v), "r"(id), "r"(nt)
-            : "memory");
-        return r != 0;
-    }
-};
 
 // Physical slot of FFT position p in a group's column buffer A.  After the DIF passes
 // frequency k sits at dpos(k), whose top bits come from k's low bits, so eight consecutive
@@ -372,31 +328,7 @@ constexpr int kBuffers = 2;
 // of their sums, up to 4 warps): [0, 8) and [16, 24) scans, [8, 16) sums.
 constexpr int kScratch = 24;
 
-__device__ __forceinline__ Z zshfl_xor(Z v, int o) {
-    return Z{F2{__shfl_xor_sync(0xffffffffu, v.re.hi, o), __shfl_xor_sync(0xffffffffu, v.re.lo, o)},
-             F2{__shfl_xor_sync(0xffffffffu, v.im.hi, o), __shfl_xor_sync(0xffffffffu, v.im.lo, o)}};
-}
-__device__ __forceinline__ Z zshfl_up(Z v, int o) {
-    return Z{F2{__shfl_up_sync(0xffffffffu, v.re.hi, o), __shfl_up_sync(0xffffffffu, v.re.lo, o)},
-             F2{__shfl_up_sync(0xffffffffu, v.im.hi, o), __shfl_up_sync(0xffffffffu, v.im.lo, o)}};
-}
-__device__ __forceinline__ Z zmulf(Z v, float b) { return Z{nrm(df::mul(v.re, b)), nrm(df::mul(v.im, b))}; }
-// v - c f (c complex, f real float-float)
-__device__ __forceinline__ Z zsubmul(Z v, Z c, F2 f) {
-    return Z{df::add(v.re, dneg(df::mul(c.re, f))), df::add(v.im, dneg(df::mul(c.im, f)))};
-}
 
-// Inclusive prefix sums over the warp's lanes of two values (one per parity), in lane order.
-__device__ __forceinline__ void warp_inclusive_scan(int lane, Z &i0, Z &i1) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Z u0 = zshfl_up(i0, o), u1 = zshfl_up(i1, o);
-        if (lane >= o) {
-            i0 = zadd(u0, i0);
-            i1 = zadd(u1, i1);
-        }
-    }
-}
 
 // Forward transform in phi (SPACE 1) or psi (SPACE 2), uhat = B^{-1} S (Eqs. sst2, fstB),
 // from the column's Chebyshev coefficients chat (chat_K = (u, T_K)_sigma / w_K, w_K =
@@ -435,50 +367,6 @@ __device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *s
     int lc = 3;
     while ((g.nt << lc) < N) lc++;
     const int k0 = min(N, g.t << lc), k1 = min(N, k0 + (1 << lc)), kn = min(k1, n), rx = g.t & 7;
-    // Sums over the group: each thread's run totals t0, t1 become the exclusive prefixes (in
-    // run order) and s0, s1 the totals over the column; area: 2 float4 per warp.
-    auto group_scan = [&](Z &t0, Z &t1, Z &s0, Z &s1, float4 *area, Z *red, float4 *red_area) {
-        Z i0 = t0, i1 = t1;
-        warp_inclusive_scan(lane, i0, i1);
-        Z e0 = zshfl_up(i0, 1), e1 = zshfl_up(i1, 1);
-        if (lane == 0) e0 = e1 = kZero;
-        if (lane == 31) {
-            stz(area, 2 * warp, i0);
-            stz(area, 2 * warp + 1, i1);
-        }
-        if (red) {                                   // warp sums of red[0..1] beside the scan
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                red[0] = zadd(red[0], zshfl_xor(red[0], o));
-                red[1] = zadd(red[1], zshfl_xor(red[1], o));
-            }
-            if (lane == 0) {
-                stz(red_area, 2 * warp, red[0]);
-                stz(red_area, 2 * warp + 1, red[1]);
-            }
-        }
-        g.sync();
-        Z w0 = kZero, w1 = kZero;
-        s0 = s1 = kZero;
-        for (int w = 0; w < nw; w++) {
-            if (w == warp) {
-                w0 = s0;
-                w1 = s1;
-            }
-            s0 = zadd(s0, ldz(area, 2 * w));
-            s1 = zadd(s1, ldz(area, 2 * w + 1));
-        }
-        t0 = zadd(w0, e0);
-        t1 = zadd(w1, e1);
-        if (red) {
-            red[0] = ldz(red_area, 0);
-            red[1] = ldz(red_area, 1);
-            for (int w = 1; w < nw; w++) {
-                red[0] = zadd(red[0], ldz(red_area, 2 * w));
-                red[1] = zadd(red[1], ldz(red_area, 2 * w + 1));
-            }
-        }
-    };
     // pass 1: prefix sums of chat within the run (per parity); psi: sums of q chat
     Z t0 = kZero, t1 = kZero, q[2] = {kZero, kZero};
     for (int k = k0; k < k1; k++) {
@@ -495,8 +383,27 @@ __device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *s
             if (SPACE == 2) q[0] = zfma(qk, c, q[0]);
         }
     }
+    if (SPACE == 2) {                                // warp sums of q chat, beside the scan's
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            q[0] = zadd(q[0], zshfl_xor(q[0], o));
+            q[1] = zadd(q[1], zshfl_xor(q[1], o));
+        }
+        if (lane == 0) {
+            stz(scr + 8, 2 * warp, q[0]);
+            stz(scr + 8, 2 * warp + 1, q[1]);
+        }
+    }
     Z s0, s1;
-    group_scan(t0, t1, s0, s1, scr, SPACE == 2 ? q : nullptr, scr + 8);
+    group_prefix(g, scr, t0, t1, s0, s1);               // its barrier also covers the sums above
+    if (SPACE == 2) {
+        q[0] = ldz(scr + 8, 0);
+        q[1] = ldz(scr + 8, 1);
+        for (int w = 1; w < nw; w++) {
+            q[0] = zadd(q[0], ldz(scr + 8, 2 * w));
+            q[1] = zadd(q[1], ldz(scr + 8, 2 * w + 1));
+        }
+    }
     const Z cr0 = zscale(s0, a.ls[0][0]), cr1 = zscale(s1, a.ls[1][0]);
     if (SPACE == 1) {
         for (int k = k0; k < kn; k++) {
@@ -526,7 +433,7 @@ __device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *s
             }
         }
         Z u0, u1;
-        group_scan(z0, z1, u0, u1, scr + 16, nullptr, nullptr);
+        group_prefix(g, scr + 16, z0, z1, u0, u1);
         for (int k = k0; k < kn; k++)
             stz(W, k ^ rx, zscale(zadd(ldz(W, k ^ rx), (k & 1) ? z1 : z0), ratio(1.0f, (float)(k + 1))));
     }
