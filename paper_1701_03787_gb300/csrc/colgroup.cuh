@@ -1,7 +1,7 @@
 // Column groups: a few warps working together on one mode column held in shared memory
-// (the wall-normal transforms, the velocity recovery).  The group's barrier, complex
-// float-float values and their shared-memory slots, warp shuffles, and the prefix and
-// suffix sums over the group's threads that the column algorithms build on.
+// (the wall-normal transforms).  The group's barrier, complex
+// float-float values and their shared-memory slots, warp shuffles, and the prefix sums
+// over the group's threads that the column algorithms build on.
 #pragma once
 
 #include <cstdint>
@@ -52,10 +52,6 @@ __device__ __forceinline__ Z zshfl_up(Z v, int o) {
     return Z{F2{__shfl_up_sync(0xffffffffu, v.re.hi, o), __shfl_up_sync(0xffffffffu, v.re.lo, o)},
              F2{__shfl_up_sync(0xffffffffu, v.im.hi, o), __shfl_up_sync(0xffffffffu, v.im.lo, o)}};
 }
-__device__ __forceinline__ Z zshfl_down(Z v, int o) {
-    return Z{F2{__shfl_down_sync(0xffffffffu, v.re.hi, o), __shfl_down_sync(0xffffffffu, v.re.lo, o)},
-             F2{__shfl_down_sync(0xffffffffu, v.im.hi, o), __shfl_down_sync(0xffffffffu, v.im.lo, o)}};
-}
 
 // Thread group of one mode column: G warps (32 G threads) synchronised by the named
 // barrier `id` (ids 1 .. 15; 0 is __syncthreads).
@@ -91,17 +87,6 @@ __device__ __forceinline__ void warp_inclusive_scan(int lane, Z &i0, Z &i1) {
         }
     }
 }
-// Inclusive suffix sums (from the last lane down).
-__device__ __forceinline__ void warp_inclusive_suffix_scan(int lane, Z &i0, Z &i1) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Z u0 = zshfl_down(i0, o), u1 = zshfl_down(i1, o);
-        if (lane + o < 32) {
-            i0 = zadd(i0, u0);
-            i1 = zadd(i1, u1);
-        }
-    }
-}
 
 // Over the group's threads, of two per-thread values t0, t1: the exclusive prefix sums in
 // thread order replace them, and s0, s1 receive the totals.  `area` holds 2 float4 per
@@ -132,26 +117,6 @@ __device__ __forceinline__ void group_prefix(const Group &g, float4 *area, Z &t0
     t1 = zadd(w1, e1);
 }
 
-// As group_prefix, in reverse thread order: t0, t1 become the sums over the later threads.
-__device__ __forceinline__ void group_suffix(const Group &g, float4 *area, Z &t0, Z &t1) {
-    const int lane = g.t & 31, warp = g.t >> 5, nw = g.nt >> 5;
-    Z i0 = t0, i1 = t1;
-    warp_inclusive_suffix_scan(lane, i0, i1);
-    Z e0 = zshfl_down(i0, 1), e1 = zshfl_down(i1, 1);
-    if (lane == 31) e0 = e1 = kZero;
-    if (lane == 0) {
-        stz(area, 2 * warp, i0);
-        stz(area, 2 * warp + 1, i1);
-    }
-    g.sync();
-    Z w0 = kZero, w1 = kZero;
-    for (int w = nw - 1; w > warp; w--) {
-        w0 = zadd(w0, ldz(area, 2 * w));
-        w1 = zadd(w1, ldz(area, 2 * w + 1));
-    }
-    t0 = zadd(w0, e0);
-    t1 = zadd(w1, e1);
-}
 
 }  // namespace colg
 }  // namespace shen
