@@ -1,7 +1,7 @@
 // Column groups: a few warps working together on one mode column held in shared memory
-// (the wall-normal transforms).  The group's barrier, complex
-// float-float values and their shared-memory slots, warp shuffles, and the prefix sums
-// over the group's threads that the column algorithms build on.
+// (the wall-normal transforms).  The group's barrier, complex float-float values and their
+// shared-memory slots, warp shuffles, and the prefix sums over the group's threads that
+// the column algorithms build on.
 #pragma once
 
 #include <cstdint>
@@ -116,7 +116,6 @@ __device__ __forceinline__ void group_prefix(const Group &g, float4 *area, Z &t0
     t0 = zadd(w0, e0);
     t1 = zadd(w1, e1);
 }
-
 
 }  // namespace colg
 }  // namespace shen
