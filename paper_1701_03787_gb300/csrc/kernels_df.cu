@@ -38,10 +38,11 @@ __device__ __forceinline__ bool work_item(const Plan &p, const int *order, long 
 // Both kernels run a fixed grid of resident blocks.  Warp slot w (one per resident warp)
 // takes the warp-sized groups of chains w, w + W, w + 2 W, ... (W slots) and spills its
 // forward results to its own [row][lane] slice of the plan's scratch.
-// Shape 1 is held to 128 registers so that four blocks (16 warps) fit on an SM: measured
-// 6.68 against 6.91 ms at N = 1024, 1024 x 1024 (shape 0 spills under that bound).
+// Shape 1 is compiled for four blocks (16 warps) per SM, which lets it use 128 registers;
+// left to itself the compiler picks 96 (five blocks).  Measured 6.67 against 6.91 ms at
+// N = 1024, 1024 x 1024; shape 0 would spill under that bound and keeps none.
 template <int V>
-__global__ void __launch_bounds__(128, V == 1 ? 4 : 1) helm_df_kernel(Plan p, const int *order, long m0, long count,
+__global__ void __launch_bounds__(128, V == 1 ? 4 : 0) helm_df_kernel(Plan p, const int *order, long m0, long count,
                                                       const double *f, double *u, float4 *scr) {
     const int lane = threadIdx.x & 31;
     const long slot = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
