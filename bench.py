@@ -65,7 +65,7 @@ TRAFFIC_SOURCES = {
     "df": ("kernels_df.cu", "chains.cuh", "df.cuh"),
     "velocity": ("velocity.cu", "chains.cuh", "df.cuh"),
     "matvec": ("matvec_df.cu", "df.cuh"),
-    "transform": ("transform.cu", "df.cuh"),
+    "transform": ("transform.cu", "colgroup.cuh", "df.cuh"),
 }
 
 
