@@ -164,6 +164,24 @@ def test_largest_N():
     assert np.abs(S[0] - sref).max() <= _bound(N, U[0], scale=np.pi / N, weight=2.0)
 
 
+@pytest.mark.parametrize("space", tr.SPACES)
+def test_largest_N_forward(space):
+    """N = 4096, where each thread of the least-squares mass solve owns a run of 32
+    frequencies: coefficients of the workload's spectrum -> values (longdouble oracle,
+    rounded to float64) -> GPU forward, back to the coefficients."""
+    N = 4096
+    with Plan(N, 2, 2, 1 / 180, 1e-3) as plan:
+        C = inputs.rhs_numpy(plan.n_modes, N, seed=43)
+        C[:, tr.dim(space, N):] = 0
+        U = np.repeat(tr.inverse_ref(space, C[:1]), plan.n_modes, axis=0)
+        Ch = _run(plan, "forward", space, U)
+    assert np.all(Ch[1:] == Ch[0])                      # identical columns, identical results
+    e, tol = _f64_factor_bound(N, Ch[:1], C[:1], tr.forward(space, U[:1]))
+    assert np.all(e <= tol), (e.max(), tol.min())
+    if space != "biharmonic":
+        assert np.all(e <= 1e-12 * np.abs(C[:1]).max(axis=1))
+
+
 def test_full_size_sampled():
     """The benchmark's workload (N = 1024, 1024 x 1024 grid, one launch per transform),
     checked on sampled modes."""
