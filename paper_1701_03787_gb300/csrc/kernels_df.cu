@@ -7,9 +7,10 @@
 // significant bits on the float32 pipes.  The sweeps need no refinement step.
 //
 // Work decomposition: one thread per (mode, parity) chain, real and imaginary parts
-// side by side.  The forward sweep writes y (float-float, 16 bytes per complex row)
-// into the output column and the back substitution reads it back in reverse and
-// overwrites it with u (float64), so the kernels use no scratch memory and u == f works.
+// side by side.  The forward sweep writes y (float-float, 16 bytes per complex row) to
+// the plan's spill scratch, [warp slot][row][lane], so a warp's 32 rows are one
+// 512-byte line; the back substitution reads it back in reverse and writes u (float64),
+// so u == f works.
 #include <algorithm>
 
 #include "chains.cuh"
