@@ -84,12 +84,18 @@ def traffic_group(kind):
 
 
 def sources_sha1(names):
+    """Hash of the kernels' code: the named CUDA sources with their comments removed (so
+    that a change of wording does not retire a capture of unchanged code)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for name in sorted(names):
         h.update(name.encode())
-        with open(os.path.join(ROOT, "paper_1701_03787_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1701_03787_gb300", "csrc", name)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(text.encode())
     return h.hexdigest()
 
 
@@ -165,7 +171,7 @@ def write_traffic(csv_paths, w):
     out = {"note": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per complex row (n_modes * N rows) "
                    "for one launch, from an ncu capture "
                    f"on the N={w['N']}, {w['Nx']}x{w['Nz']} workload, written by bench.py --write-traffic; each "
-                   "figure is valid while its kernels' CUDA sources hash to sources_sha1[group] "
+                   "figure is valid while its kernels' CUDA sources (comments removed) hash to sources_sha1[group] "
                    "(groups and files: bench.py TRAFFIC_SOURCES)",
            "workload": {k: w[k] for k in ("N", "Nx", "Nz")},
            "launches": {pat: counts[pat] for pat, _ in TRAFFIC_KERNELS if counts.get(pat)},

@@ -109,3 +109,17 @@ def test_traffic_from_one_capture_per_kernel(tmp_path, monkeypatch):
     bpr = bench.write_traffic([pa, pb], W)["bytes_per_row"]
     assert bpr["biharmonic:df"] == pytest.approx(80.0)
     assert bpr["helmholtz:df"] == pytest.approx(60.0)
+
+
+def test_source_hash_ignores_comments(tmp_path, monkeypatch):
+    """The traffic table stays valid across comment edits of unchanged kernel code, and
+    turns stale when the code changes."""
+    csrc = tmp_path / "paper_1701_03787_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "k.cu").write_text("// one\nint a = 1; /* two\nlines */ int b = 2;\n")
+    h0 = bench.sources_sha1(("k.cu",))
+    (csrc / "k.cu").write_text("// reworded\nint a = 1; /* other */ int b = 2;\n")
+    assert bench.sources_sha1(("k.cu",)) == h0
+    (csrc / "k.cu").write_text("// reworded\nint a = 3; /* other */ int b = 2;\n")
+    assert bench.sources_sha1(("k.cu",)) != h0
