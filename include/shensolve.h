@@ -257,20 +257,24 @@ shen_status shen_velocity(shen_plan_t plan, const double *u, const double *g, do
  *                           projection of u on the space (entries beyond written 0)
  * Each cosine sum is one complex FFT per column, of length N on Gauss points (Makhoul's
  * reordering, DCT-II / DCT-III) or 2 (N-1) on Gauss-Lobatto points (the even extension,
- * DCT-I), run in float-float arithmetic (about 48 significant bits) in shared memory; the mass
- * solves use the float64 LU of B (the same for every mode) as per-N tables.  Relative
- * errors are of order 1e-14 for the inverse and scalar transforms; the forward transform
- * adds the conditioning of B (about 1e9 for the biharmonic B at N = 1024, so inputs far
- * from the space lose digits there, as a float64 solve of the same system does).
+ * DCT-I), run in float-float arithmetic (about 48 significant bits) in shared memory.  The
+ * forward transforms in phi and psi solve with B in the same kernel: since B = P^T W P (P
+ * the basis combination, W the discrete norms of the T_k), out is the W-weighted
+ * least-squares fit of the Chebyshev coefficients, computed as prefix sums with a rank-1
+ * (phi) or rank-2 (psi) correction, without forming B.  Relative errors are of order
+ * 1e-14 for the inverse and scalar transforms and for the forward transform in T_k; the
+ * forward transforms in phi and psi add the norm of the prefix sums (growing like N for
+ * phi, N^2 for psi), well inside the float64 solve of B's own error (whose conditioning
+ * is about 1e9 for the biharmonic B at N = 1024).
  *
- * in, out: DEVICE fields of n_modes * N complex values, mode-major like the solves'
- * (in == out allowed; other overlap SHEN_ERR_ARG).  N must be a power of two on Gauss
- * points and one more than a power of two on Gauss-Lobatto points (N - 1 intervals); other
- * plans, and wall-index-first plans, return SHEN_ERR_UNSUPPORTED, as do FFT lengths whose
- * two shared-memory buffers do not fit one block (on GB300: N = 8192, and N = 4097 on
- * Gauss-Lobatto points).  The forward transforms in phi and psi run the scalar products and
- * then the mass solve in place on `out` (a second kernel).  Asynchronous
- * on `stream`; no scratch memory: calls on one plan may overlap.  Each column is staged
+ * in, out: DEVICE fields of n_modes * N complex values in the plan's layout (in == out
+ * allowed; other overlap SHEN_ERR_ARG).  The FFT length must be 2^p or 3 2^p (N on Gauss
+ * points, 2 (N - 1) on Gauss-Lobatto points), at least 8; other plans return
+ * SHEN_ERR_UNSUPPORTED, as do lengths whose two shared-memory buffers do not fit one block
+ * (on GB300: N = 8192 on Gauss points, N = 4097 on Gauss-Lobatto points).  Asynchronous on
+ * `stream`.  Mode-major plans use no scratch memory, so calls on one plan may overlap;
+ * wall-index-first plans gather each chunk of columns into plan-owned staging, transform it
+ * and scatter it back, so their calls on one plan must not overlap.  Each column is staged
  * in shared memory by a bulk asynchronous copy; a copy that does not complete within a
  * bounded wait stops the kernel and is reported by shen_plan_check as SHEN_ERR_CUDA. */
 typedef enum {
