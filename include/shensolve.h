@@ -365,7 +365,7 @@ shen_status shen_solve_refine(shen_plan_t plan, int problem, const double *f, do
  *      as 0);
  *   2  one lane per real chain (the real or imaginary part of one parity chain), one
  *      CTA of 4 warps per SM, the forward result of each chain kept in Tensor Memory
- *      (its last 256 rows) and shared memory (the 224 rows before them), only the rest
+ *      (its last 256 rows) and shared memory (the 96 rows before them), only the rest
  *      spilled to global memory; each row's float-float sum renormalised once;
  *   3  as 2 without the Tensor Memory part.
  * Shapes 2 and 3 round differently from 0 and 1 (same terms, same order, one

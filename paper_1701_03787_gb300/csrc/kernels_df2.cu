@@ -11,12 +11,13 @@
 //     one mode: lane = 4 j + 2 parity + part, 8 modes per warp), which halves the y each
 //     lane holds while the four lanes of a mode still read and write whole 32-byte sectors;
 //   - one CTA of 4 warps per SM (one warp per scheduler) keeps 128 chains in flight, and
-//     their y lives in Tensor Memory (256 rows per lane) and shared memory (224 rows per
-//     lane) before any of it goes to a global spill: at N = 1024 (510 rows per chain) 94 %
-//     of y stays on chip;
+//     their y lives in Tensor Memory (256 rows per lane) and shared memory (96 rows per
+//     lane, beside the copy rings below) before any of it goes to a global spill: at
+//     N = 1024 (510 rows per chain) 69 % of y stays on chip;
 //   - each row's float-float sum is accumulated with one renormalisation (sweep2.cuh),
-//     and the column, factor and spill streams are prefetched into L2 ahead of the
-//     register double-buffering, since 4 warps cannot hide DRAM latency by occupancy.
+//     and f and the factor rows stream through per-lane cp.async rings in shared memory
+//     (32 rows ahead in the forward sweep, 16 in the backward one), since 4 warps cannot
+//     hide DRAM latency by occupancy.
 // Same arithmetic as the other float-float shapes, same ordering of the terms within a
 // row up to the accumulation (so results agree to rounding, not bit for bit).
 #include <algorithm>
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 constexpr int kSmemLimit = 232448;                                  // 227 KB per block
-constexpr int kSmemBlocks = (kSmemLimit - 16 - (kThreads / 32) * kRingBytes) / (kRB * kThreads * 8);   // 26
+constexpr int kSmemBlocks = (kSmemLimit - 16 - (kThreads / 32) * kRingBytes) / (kRB * kThreads * 8);   // 24
 constexpr int kTmemCols = 512;
 
 inline size_t smem_bytes(int blocks) {
