@@ -41,6 +41,13 @@ __device__ __forceinline__ Z zfma(F2 s, Z a, Z b) {  // b + s a
 __device__ __forceinline__ Z zsubmul(Z v, Z c, F2 f) {
     return Z{df::add(v.re, dneg(df::mul(c.re, f))), df::add(v.im, dneg(df::mul(c.im, f)))};
 }
+// v - c f and v + c f for a float32 f (one product term fewer than with a pair)
+__device__ __forceinline__ Z zsubmulf(Z v, Z c, float f) {
+    return Z{df::add(v.re, dneg(df::mul(c.re, f))), df::add(v.im, dneg(df::mul(c.im, f)))};
+}
+__device__ __forceinline__ Z zaddmulf(Z v, Z c, float f) {
+    return Z{df::add(v.re, df::mul(c.re, f)), df::add(v.im, df::mul(c.im, f))};
+}
 __device__ __forceinline__ Z zfromf64(double2 v) { return Z{df::from_f64(v.x), df::from_f64(v.y)}; }
 __device__ __forceinline__ double2 ztof64(Z v) { return make_double2(df::to_f64(v.re), df::to_f64(v.im)); }
 

@@ -367,23 +367,23 @@ __device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *s
     int lc = 3;
     while ((g.nt << lc) < N) lc++;
     const int k0 = min(N, g.t << lc), k1 = min(N, k0 + (1 << lc)), kn = min(k1, n), rx = g.t & 7;
-    // pass 1: prefix sums of chat within the run (per parity); psi: sums of q chat
+    // pass 1: prefix sums of chat within the run (per parity); psi: sums of K^2 chat (the
+    // sums of q chat = K^2 chat - kappa chat follow from them and the totals of chat)
     Z t0 = kZero, t1 = kZero, q[2] = {kZero, kZero};
     for (int k = k0; k < k1; k++) {
         const Z c = chat(k);
-        F2 qk{0.f, 0.f};
-        if (SPACE == 2) qk = df::add(F2{(float)k * (float)k, 0.f}, dneg(a.ls[k & 1][1]));   // k^2 exact
+        const float kk = (float)k * (float)k;          // exact: k < 4096
         if (k & 1) {
             t1 = zadd(t1, c);
             stz(W, k ^ rx, t1);
-            if (SPACE == 2) q[1] = zfma(qk, c, q[1]);
+            if (SPACE == 2) q[1] = zaddmulf(q[1], c, kk);
         } else {
             t0 = zadd(t0, c);
             stz(W, k ^ rx, t0);
-            if (SPACE == 2) q[0] = zfma(qk, c, q[0]);
+            if (SPACE == 2) q[0] = zaddmulf(q[0], c, kk);
         }
     }
-    if (SPACE == 2) {                                // warp sums of q chat, beside the scan's
+    if (SPACE == 2) {                                // warp sums of K^2 chat, beside the scan's
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             q[0] = zadd(q[0], zshfl_xor(q[0], o));
@@ -408,11 +408,11 @@ __device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *s
     if (SPACE == 1) {
         for (int k = k0; k < kn; k++) {
             const bool odd = k & 1;
-            const F2 om{0.5f * (float)(k + 1), 0.f};
-            stz(W, k ^ rx, zsubmul(zadd(ldz(W, k ^ rx), odd ? t1 : t0), odd ? cr1 : cr0, om));
+            stz(W, k ^ rx, zsubmulf(zadd(ldz(W, k ^ rx), odd ? t1 : t0), odd ? cr1 : cr0, 0.5f * (float)(k + 1)));
         }
     } else {
-        const Z cq0 = zscale(q[0], a.ls[0][2]), cq1 = zscale(q[1], a.ls[1][2]);
+        const Z cq0 = zscale(zsubmul(q[0], s0, a.ls[0][1]), a.ls[0][2]);      // tau (sum K^2 chat - kappa sum chat)
+        const Z cq1 = zscale(zsubmul(q[1], s1, a.ls[1][1]), a.ls[1][2]);
         const F2 sixth = ratio(1.0f, 6.0f);
         // pass 2: v, then the prefix sums of (K + 1) v within the run
         Z z0 = kZero, z1 = kZero;
@@ -421,14 +421,13 @@ __device__ __forceinline__ void forward_ls(const TrArgs &a, float4 *W, float4 *s
             const float kf = (float)k, om = 0.5f * (kf + 1.0f);
             const F2 s2 = nrm(df::mul(nrm(df::mul(df::two_prod(kf, kf + 1.0f), kf + 2.0f)), sixth));
             const F2 Q = df::add(s2, dneg(df::mul(a.ls[k & 1][1], om)));
-            Z v = zsubmul(zadd(ldz(W, k ^ rx), odd ? t1 : t0), odd ? cr1 : cr0, F2{om, 0.f});
+            Z v = zsubmulf(zadd(ldz(W, k ^ rx), odd ? t1 : t0), odd ? cr1 : cr0, om);
             v = zsubmul(v, odd ? cq1 : cq0, Q);
-            const Z w = zmulf(v, kf + 1.0f);
             if (odd) {
-                z1 = zadd(z1, w);
+                z1 = zaddmulf(z1, v, kf + 1.0f);
                 stz(W, k ^ rx, z1);
             } else {
-                z0 = zadd(z0, w);
+                z0 = zaddmulf(z0, v, kf + 1.0f);
                 stz(W, k ^ rx, z0);
             }
         }
