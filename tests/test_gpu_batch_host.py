@@ -76,6 +76,20 @@ def test_batch_host_equals_device_small(problem, precision):
         _oracle_sample(bp, insts, hf, hu, problem, 1e-12 if precision == "fp64" else 1e-10, seed=3)
 
 
+def test_batch_host_gauss_lobatto():
+    """A Gauss-Lobatto batch (SHEN_PLAN_GL): host solve equals the device solve bit for bit."""
+    import torch
+    insts = _instances_small()
+    with BatchPlan(insts, gl=True) as bp:
+        f = inputs.batch_rhs_torch(bp.offsets, insts, seed=13)
+        for problem in ("helmholtz", "biharmonic"):
+            ref = bp.solve(problem, f, precision="df")
+            torch.cuda.synchronize()
+            hu = bp.solve_host(problem, _pinned(f.cpu()), precision="df")
+            torch.cuda.synchronize()
+            assert torch.equal(hu, ref.cpu()), problem
+
+
 def test_batch_host_several_chunks_two_problems_on_two_streams():
     """Both problems through the shared pipeline, issued on two caller streams: each
     result equals its device solve bit for bit; the staging is counted by the plan."""

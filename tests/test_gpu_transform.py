@@ -244,7 +244,7 @@ def test_gl_inverse_and_scalar_match_oracle(N, space):
         assert np.all(S[m, tr.dim(space, N):] == 0)
 
 
-@pytest.mark.parametrize("N", [9, 65, 257, 1025])
+@pytest.mark.parametrize("N", [9, 25, 65, 97, 257, 1025])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_gl_forward_matches_refined_projection(N, space):
     with Plan(N, 4, 4, 1 / 180, 1e-3, gl=True) as plan:
