@@ -109,7 +109,7 @@ def _f64_factor_bound(N, got, ref, f64):
     return e_got, 64 * e_64.max() + floor
 
 
-@pytest.mark.parametrize("N", [8, 64, 96, 192, 256, 1024])
+@pytest.mark.parametrize("N", [8, 64, 96, 192, 256, 512, 768, 1024])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_forward_matches_refined_projection(N, space):
     """Random values (not in the space) against the refined projection: the conditioning
@@ -244,7 +244,7 @@ def test_gl_inverse_and_scalar_match_oracle(N, space):
         assert np.all(S[m, tr.dim(space, N):] == 0)
 
 
-@pytest.mark.parametrize("N", [9, 25, 65, 97, 257, 1025])
+@pytest.mark.parametrize("N", [9, 25, 65, 97, 257, 513, 769, 1025])
 @pytest.mark.parametrize("space", tr.SPACES)
 def test_gl_forward_matches_refined_projection(N, space):
     with Plan(N, 4, 4, 1 / 180, 1e-3, gl=True) as plan:
