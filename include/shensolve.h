@@ -361,7 +361,7 @@ shen_status shen_solve_refine(shen_plan_t plan, int problem, const double *f, do
  *   0  one thread per (mode, parity) chain, real and imaginary parts together, rows
  *      prefetched in registers, 4 (biharmonic) / 8 (Helmholtz) per block, two blocks in
  *      flight; the forward result spilled to a plan scratch in global memory;
- *   1  the same with 4 + 4 rows (biharmonic) / 4 rows (Helmholtz) per block (same bits
+ *   1  the same with 4 + 4 rows (biharmonic) / 5 rows (Helmholtz) per block (same bits
  *      as 0);
  *   2  one lane per real chain (the real or imaginary part of one parity chain), one
  *      CTA of 4 warps per SM, the forward result of each chain kept in Tensor Memory

@@ -655,7 +655,7 @@ __device__ inline void solve_bih_f32_chain(int N, int par, const double *fcol, d
 template <int V>
 __device__ inline void solve_helm_df_chain(int N, int par, const double *fcol, double *ucol, HelmDF F, F2 h,
                                            float4 *ys, int ystride, long rs = 1) {
-    solve_helm_df_chain_t<V == 0 ? 8 : 4>(N, par, fcol, ucol, F, h, ys, ystride, rs);
+    solve_helm_df_chain_t<V == 0 ? 8 : 5>(N, par, fcol, ucol, F, h, ys, ystride, rs);
 }
 
 template <int V>

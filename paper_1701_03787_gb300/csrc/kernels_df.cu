@@ -41,7 +41,8 @@ __device__ __forceinline__ bool work_item(const Plan &p, const int *order, long 
 // forward results to its own [row][lane] slice of the plan's scratch.
 // Shape 1 is compiled for four blocks (16 warps) per SM, which lets it use 128 registers;
 // left to itself the compiler picks 96 (five blocks).  Measured 6.67 against 6.91 ms at
-// N = 1024, 1024 x 1024; shape 0 would spill under that bound and keeps none.
+// N = 1024, 1024 x 1024 (6.56 ms with its 5-row blocks); shape 0 would spill under that
+// bound and keeps none.
 template <int V>
 __global__ void __launch_bounds__(128, V == 1 ? 4 : 0) helm_df_kernel(Plan p, const int *order, long m0, long count,
                                                       const double *f, double *u, float4 *scr) {
