@@ -196,7 +196,8 @@ cudaError_t launch_solve_df(const Plan &p, int problem, long m0, long count, con
                             cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     // wall-index-first fields: modes in their own order, so that a warp's rows are contiguous
-    // (measured 14.3 / 10.0 ms at N = 1024, 1024 x 1024, against 22.7 / 21.5 ms in the class order)
+    // (measured 14.3 / 10.0 ms at N = 1024, 1024 x 1024,
+    // against 22.7 / 21.5 ms in the class order)
     const int *order = (m0 == 0 && count == p.n_modes && !p.wall_first) ? p.d_order : nullptr;
     const int pb = problem == SHEN_HELMHOLTZ ? 0 : 1;
     const int v = p.df_variant[pb];
