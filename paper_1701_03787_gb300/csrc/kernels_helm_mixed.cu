@@ -8,11 +8,12 @@
 //   d  = H^-1 r     float32 sweeps again
 //   u  = u0 + d     float-float / float64, written as float64
 //
-// Work decomposition: one warp per mode.  Lanes 0-15 take the even chain, lanes
-// 16-31 the odd chain (k = 2 i + parity); lane s of a half owns rows s R .. s R + R - 1
-// of its chain, held in registers.  The sweeps are linear recurrences along each
-// chain: every lane runs its R rows with a zero carry, the 16 lanes of a chain combine
-// their maps with a shuffle scan (scalar affine maps for the forward sweep, 2x2 maps
+// Work decomposition: L lanes per parity chain (k = 2 i + parity).  L = 16: one warp per
+// mode, lanes 0-15 on the even chain and 16-31 on the odd one; L = 32: one warp per
+// (mode, parity), the two warps of a block on the two parities of one mode.  Lane s of a
+// chain owns rows s R .. s R + R - 1 of it, held in registers.  The sweeps are linear
+// recurrences along each chain: every lane runs its R rows with a zero carry, the L
+// lanes of a chain combine their maps with a shuffle scan (scalar affine maps for the forward sweep, 2x2 maps
 // for the back substitution whose state is (u_i, sum_{j >= i} u_j)), and each lane
 // then adds the carried part.
 //
@@ -30,11 +31,16 @@ namespace {
 constexpr float kPiHi = 3.14159274101257324f;           // float(pi)
 constexpr float kPiLo = -8.74227765734758577e-08f;      // pi - float(pi)
 constexpr unsigned kFull = 0xffffffffu;
+// chains of at least this many rows per lane at 16 lanes run on 32 lanes
+#ifndef SHEN_MIXED_L32_MIN
+#define SHEN_MIXED_L32_MIN 16
+#endif
+constexpr int kMixedL32Min = SHEN_MIXED_L32_MIN;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Forward elimination y_i = f_i + g_i y_{i-1}, in place in w.  gs: [j][lane] shared.
-template <int R>
+template <int R, int L>
 __device__ __forceinline__ void forward_sweep(float2 (&w)[R], const float *gs, int lane, int s) {
     float2 y = f2(0.f, 0.f);
     float G = 1.f;
@@ -47,17 +53,17 @@ __device__ __forceinline__ void forward_sweep(float2 (&w)[R], const float *gs, i
         G *= g;
     }
 #pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const float Gu = __shfl_up_sync(kFull, G, d, 16);
-        const float Yx = __shfl_up_sync(kFull, y.x, d, 16);
-        const float Yy = __shfl_up_sync(kFull, y.y, d, 16);
+    for (int d = 1; d < L; d <<= 1) {
+        const float Gu = __shfl_up_sync(kFull, G, d, L);
+        const float Yx = __shfl_up_sync(kFull, y.x, d, L);
+        const float Yy = __shfl_up_sync(kFull, y.y, d, L);
         if (s >= d) {
             y.x = fmaf(G, Yx, y.x);
             y.y = fmaf(G, Yy, y.y);
             G *= Gu;
         }
     }
-    float cx = __shfl_up_sync(kFull, y.x, 1, 16), cy = __shfl_up_sync(kFull, y.y, 1, 16);
+    float cx = __shfl_up_sync(kFull, y.x, 1, L), cy = __shfl_up_sync(kFull, y.y, 1, L);
     if (s == 0) cx = cy = 0.f;
     float P = 1.f;
 #pragma unroll
@@ -72,14 +78,14 @@ __device__ __forceinline__ void forward_sweep(float2 (&w)[R], const float *gs, i
 //   u_i = a u_{i+1} - c S_{i+1} + inv0 y_i,  S_i = S_{i+1} + u_i.
 // With FIRST, m0 ([j][lane] shared) receives row 0 of the lane-local transfer matrices
 // (response of u_i to the carried state); otherwise the stored rows are reused.
-template <int R, bool FIRST>
+template <int R, int L, bool FIRST>
 __device__ __forceinline__ void backward_sweep(float2 (&w)[R], const float2 *fac, int lane, int s, float h,
                                                float2 *m0) {
     float2 u = f2(0.f, 0.f), S = f2(0.f, 0.f);
     float t00 = 1.f, t01 = 0.f, t10 = 0.f, t11 = 1.f;
 #pragma unroll
     for (int j = R - 1; j >= 0; j--) {
-        const float2 fu = fac[j * 16];                  // (inv0, U2) of row s R + j
+        const float2 fu = fac[j * L];                   // (inv0, U2) of row s R + j
         const float a = h * fu.x, c = fu.y * fu.x;
         float2 un;
         un.x = fmaf(a, u.x, fmaf(-c, S.x, fu.x * w[j].x));
@@ -95,14 +101,14 @@ __device__ __forceinline__ void backward_sweep(float2 (&w)[R], const float2 *fac
         t01 = n01;
         if (FIRST) m0[j * 32 + lane] = f2(n00, n01);
     }
-    // suffix scan over the 16 lanes of the chain of the maps x -> T x + v, v = (u, S)
+    // suffix scan over the L lanes of the chain of the maps x -> T x + v, v = (u, S)
 #pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const float b00 = __shfl_down_sync(kFull, t00, d, 16), b01 = __shfl_down_sync(kFull, t01, d, 16);
-        const float b10 = __shfl_down_sync(kFull, t10, d, 16), b11 = __shfl_down_sync(kFull, t11, d, 16);
-        const float wux = __shfl_down_sync(kFull, u.x, d, 16), wuy = __shfl_down_sync(kFull, u.y, d, 16);
-        const float wSx = __shfl_down_sync(kFull, S.x, d, 16), wSy = __shfl_down_sync(kFull, S.y, d, 16);
-        if (s + d < 16) {
+    for (int d = 1; d < L; d <<= 1) {
+        const float b00 = __shfl_down_sync(kFull, t00, d, L), b01 = __shfl_down_sync(kFull, t01, d, L);
+        const float b10 = __shfl_down_sync(kFull, t10, d, L), b11 = __shfl_down_sync(kFull, t11, d, L);
+        const float wux = __shfl_down_sync(kFull, u.x, d, L), wuy = __shfl_down_sync(kFull, u.y, d, L);
+        const float wSx = __shfl_down_sync(kFull, S.x, d, L), wSy = __shfl_down_sync(kFull, S.y, d, L);
+        if (s + d < L) {
             u.x = fmaf(t00, wux, fmaf(t01, wSx, u.x));
             u.y = fmaf(t00, wuy, fmaf(t01, wSy, u.y));
             S.x = fmaf(t10, wux, fmaf(t11, wSx, S.x));
@@ -112,9 +118,9 @@ __device__ __forceinline__ void backward_sweep(float2 (&w)[R], const float2 *fac
             t00 = n00; t01 = n01; t10 = n10; t11 = n11;
         }
     }
-    float cux = __shfl_down_sync(kFull, u.x, 1, 16), cuy = __shfl_down_sync(kFull, u.y, 1, 16);
-    float cSx = __shfl_down_sync(kFull, S.x, 1, 16), cSy = __shfl_down_sync(kFull, S.y, 1, 16);
-    if (s == 15) cux = cuy = cSx = cSy = 0.f;
+    float cux = __shfl_down_sync(kFull, u.x, 1, L), cuy = __shfl_down_sync(kFull, u.y, 1, L);
+    float cSx = __shfl_down_sync(kFull, S.x, 1, L), cSy = __shfl_down_sync(kFull, S.y, 1, L);
+    if (s == L - 1) cux = cuy = cSx = cSy = 0.f;
 #pragma unroll
     for (int j = 0; j < R; j++) {
         const float2 m = m0[j * 32 + lane];
@@ -128,7 +134,7 @@ __device__ __forceinline__ void backward_sweep(float2 (&w)[R], const float2 *fac
 //   E_i = alpha (delta_k u_i - (u_{i-1} + u_{i+1}) / 2) + 2(k+1)(k+2) u_i + 4(k+1) sum_{j>i} u_j
 //   r_i = f_i - pi E_i.
 // The row loop is kept rolled (its body is long) so the kernel stays small.
-template <int R, bool DF>
+template <int R, int L, bool DF>
 __device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const double *fcol, int lane, int s,
                                          int p, int n, double alpha, int k_gl) {
     const df::F2 a_df = df::from_f64(alpha);
@@ -148,35 +154,35 @@ __device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const do
         }
     }
 #pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
+    for (int d = 1; d < L; d <<= 1) {
         if (DF) {
-            const float a0 = __shfl_down_sync(kFull, tre, d, 16), a1 = __shfl_down_sync(kFull, ere, d, 16);
-            const float b0 = __shfl_down_sync(kFull, tim, d, 16), b1 = __shfl_down_sync(kFull, eim, d, 16);
-            if (s + d < 16) {
+            const float a0 = __shfl_down_sync(kFull, tre, d, L), a1 = __shfl_down_sync(kFull, ere, d, L);
+            const float b0 = __shfl_down_sync(kFull, tim, d, L), b1 = __shfl_down_sync(kFull, eim, d, L);
+            if (s + d < L) {
                 df::F2 q = df::add(df::F2{tre, ere}, df::F2{a0, a1}); tre = q.hi; ere = q.lo;
                 q = df::add(df::F2{tim, eim}, df::F2{b0, b1}); tim = q.hi; eim = q.lo;
             }
         } else {
-            const double a0 = __shfl_down_sync(kFull, dre, d, 16), b0 = __shfl_down_sync(kFull, dim, d, 16);
-            if (s + d < 16) { dre += a0; dim += b0; }
+            const double a0 = __shfl_down_sync(kFull, dre, d, L), b0 = __shfl_down_sync(kFull, dim, d, L);
+            if (s + d < L) { dre += a0; dim += b0; }
         }
     }
     // running sums over rows above the current row: (hi, unnormalised error)
     float Tre, Tim, Ere, Eim;
     double Dre, Dim;
     {
-        float a0 = __shfl_down_sync(kFull, tre, 1, 16), a1 = __shfl_down_sync(kFull, ere, 1, 16);
-        float b0 = __shfl_down_sync(kFull, tim, 1, 16), b1 = __shfl_down_sync(kFull, eim, 1, 16);
-        double da = __shfl_down_sync(kFull, dre, 1, 16), db = __shfl_down_sync(kFull, dim, 1, 16);
-        if (s == 15) { a0 = a1 = b0 = b1 = 0.f; da = db = 0.0; }
+        float a0 = __shfl_down_sync(kFull, tre, 1, L), a1 = __shfl_down_sync(kFull, ere, 1, L);
+        float b0 = __shfl_down_sync(kFull, tim, 1, L), b1 = __shfl_down_sync(kFull, eim, 1, L);
+        double da = __shfl_down_sync(kFull, dre, 1, L), db = __shfl_down_sync(kFull, dim, 1, L);
+        if (s == L - 1) { a0 = a1 = b0 = b1 = 0.f; da = db = 0.0; }
         Tre = a0; Ere = a1; Tim = b0; Eim = b1;
         Dre = da; Dim = db;
     }
     const float2 top = u0s[(R - 1) * 32 + lane], bot = u0s[lane];
-    float2 below = f2(__shfl_up_sync(kFull, top.x, 1, 16), __shfl_up_sync(kFull, top.y, 1, 16));
-    float2 above = f2(__shfl_down_sync(kFull, bot.x, 1, 16), __shfl_down_sync(kFull, bot.y, 1, 16));
+    float2 below = f2(__shfl_up_sync(kFull, top.x, 1, L), __shfl_up_sync(kFull, top.y, 1, L));
+    float2 above = f2(__shfl_down_sync(kFull, bot.x, 1, L), __shfl_down_sync(kFull, bot.y, 1, L));
     if (s == 0) below = f2(0.f, 0.f);
-    if (s == 15) above = f2(0.f, 0.f);
+    if (s == L - 1) above = f2(0.f, 0.f);
     float2 up = above;
     float2 uc = top;
     // per-class constants: pi alpha / 2 (float-float)
@@ -245,14 +251,19 @@ __device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const do
     }
 }
 
-// One warp per work item.  fac: float32 factors [class][parity][j][segment] = (inv0, U2).
-template <int R, bool DF>
+// Blocks of two warps.  L = 16: a warp per mode (work item); L = 32: a warp per parity
+// chain, the block's two warps on one mode.  fac: float32 factors [class][parity][j][s] =
+// (inv0, U2), s < L.
+template <int R, int L, bool DF>
 __global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order, long m0, long count,
                                                          const double *f, double *u, const float2 *fac) {
+    static_assert(L == 16 || L == 32, "16 or 32 lanes per chain");
     extern __shared__ float2 smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int par = lane >> 4, s = lane & 15;
-    const long item = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int s = lane & (L - 1);
+    const long wid = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const long item = L == 16 ? wid : wid >> 1;
+    const int par = L == 16 ? lane >> 4 : (int)(wid & 1);
     if (item >= count) return;                          // the whole warp leaves together
     const long mode = order ? (long)order[item] : m0 + item;
     const long col = mode - m0;
@@ -265,7 +276,7 @@ __global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order
     float *gbuf = reinterpret_cast<float *>(u0buf + R * 32);        // [R][32] g
     const double *fcol = f + 2 * col * N;
     double *ucol = u + 2 * col * N;
-    const float2 *F = fac + ((size_t)cls * 2 + par) * R * 16 + s;  // row s R + j at F[j * 16]
+    const float2 *F = fac + ((size_t)cls * 2 + par) * R * L + s;   // row s R + j at F[j * L]
 
     float2 w[R];
 #pragma unroll
@@ -279,22 +290,22 @@ __global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order
             w[j] = f2(0.f, 0.f);
         }
         float prev = 0.f;                               // 1/U of row i-1
-        if (i > 0) prev = j > 0 ? F[(j - 1) * 16].x : F[(R - 1) * 16 - 1].x;
+        if (i > 0) prev = j > 0 ? F[(j - 1) * L].x : F[(R - 1) * L - 1].x;
         gbuf[j * 32 + lane] = h * prev;
     }
     __syncwarp();
-    forward_sweep<R>(w, gbuf, lane, s);
-    backward_sweep<R, true>(w, F, lane, s, h, m0buf);
+    forward_sweep<R, L>(w, gbuf, lane, s);
+    backward_sweep<R, L, true>(w, F, lane, s, h, m0buf);
 #pragma unroll
     for (int j = 0; j < R; j++) u0buf[j * 32 + lane] = w[j];
     __syncwarp();
-    residual<R, DF>(m0buf, u0buf, fcol, lane, s, par, n, alpha, p.gl ? n - 1 : -1);
+    residual<R, L, DF>(m0buf, u0buf, fcol, lane, s, par, n, alpha, p.gl ? n - 1 : -1);
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < R; j++) w[j] = m0buf[j * 32 + lane];
     __syncwarp();
-    forward_sweep<R>(w, gbuf, lane, s);
-    backward_sweep<R, true>(w, F, lane, s, h, m0buf);
+    forward_sweep<R, L>(w, gbuf, lane, s);
+    backward_sweep<R, L, true>(w, F, lane, s, h, m0buf);
 #pragma unroll
     for (int j = 0; j < R; j++) {
         const int k = 2 * (s * R + j) + par;
@@ -313,20 +324,20 @@ __global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order
             reinterpret_cast<double2 *>(ucol)[k] = out;
         }
     }
-    // trailing entries beyond the lanes' reach (at most 2, since N - 2 <= 32 R)
-    if (lane == 0)
-        for (int k = max(n, 32 * R); k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
+    // trailing entries beyond the lanes' reach (at most 2, since N - 2 <= 2 L R)
+    if (s == 0 && par == 0)
+        for (int k = max(n, 2 * L * R); k < N; k++) reinterpret_cast<double2 *>(ucol)[k] = make_double2(0.0, 0.0);
 }
 
 // float64 factors -> float32 table in the lane layout: row i = s R + j of chain
-// (class, parity) goes to [class][parity][j][s].
-__global__ void pack_helm_f32_kernel(Plan p, int R, float2 *out) {
+// (class, parity) goes to [class][parity][j][s], s < L.
+__global__ void pack_helm_f32_kernel(Plan p, int R, int L, float2 *out) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const long total = p.n_classes * 2 * (long)R * 16;
+    const long total = p.n_classes * 2 * (long)R * L;
     if (t >= total) return;
-    const int s = (int)(t % 16);
-    const int j = (int)((t / 16) % R);
-    const long chain = t / (16L * R);                  // class * 2 + parity
+    const int s = (int)(t % L);
+    const int j = (int)((t / L) % R);
+    const long chain = t / ((long)L * R);              // class * 2 + parity
     const int i = s * R + j;
     float2 v = make_float2(0.f, 0.f);
     if (i < p.rows_h) {
@@ -336,16 +347,17 @@ __global__ void pack_helm_f32_kernel(Plan p, int R, float2 *out) {
     out[t] = v;
 }
 
-template <int R, bool DF>
+template <int R, int L, bool DF>
 cudaError_t launch_helm_mixed_R(const Plan &p, const int *order, long m0, long count, const double *f, double *u,
                                 const float2 *fac, cudaStream_t st) {
     const int warps = 2;
     // per warp: transfer rows and u0 ([R][32] float2 each) and g ([R][32] float)
     const size_t smem = (size_t)warps * 5 * R * 16 * sizeof(float2);
-    auto kern = helm_mixed_kernel<R, DF>;
+    auto kern = helm_mixed_kernel<R, L, DF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((count + warps - 1) / warps);
+    const long per_block = L == 16 ? warps : 1;          // modes per block
+    const unsigned blocks = (unsigned)((count + per_block - 1) / per_block);
     kern<<<blocks, warps * 32, smem, st>>>(p, order, m0, count, f, u, fac);
     return cudaGetLastError();
 }
@@ -368,9 +380,15 @@ int helm_mixed_R(int N) {
     return 0;
 }
 
-cudaError_t pack_helm_f32(const Plan &p, int R, float2 *out, cudaStream_t s) {
-    const long total = p.n_classes * 2 * (long)R * 16;
-    pack_helm_f32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, R, out);
+// Lanes per chain for R16 rows per lane at 16 lanes: chains of more than 128 rows take a
+// whole warp each (R16 / 2 rows per lane), which halves the registers and shared memory a
+// warp holds (N = 1024: 168 -> 118 registers, 11.85 -> 9.39 ms for the 1024 x 1024 grid).
+static int mixed_lanes(int R16) { return R16 >= kMixedL32Min ? 32 : 16; }
+
+cudaError_t pack_helm_f32(const Plan &p, int R16, float2 *out, cudaStream_t s) {
+    const int L = mixed_lanes(R16), R = R16 * 16 / L;
+    const long total = p.n_classes * 2 * (long)R * L;
+    pack_helm_f32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p, R, L, out);
     return cudaGetLastError();
 }
 
@@ -379,13 +397,19 @@ cudaError_t launch_helm_mixed(const Plan &p, bool dfres, long m0, long count, co
     if (count <= 0) return cudaSuccess;
     const int *order = (m0 == 0 && count == p.n_modes) ? p.d_order : nullptr;
     const float2 *fac = reinterpret_cast<const float2 *>(p.d_fac_h32);
-#define SHEN_CASE(RR)                                                                         \
-    case RR:                                                                                  \
-        return dfres ? launch_helm_mixed_R<RR, true>(p, order, m0, count, f, u, fac, s)       \
-                     : launch_helm_mixed_R<RR, false>(p, order, m0, count, f, u, fac, s);
+#define SHEN_CASE(RR, LL)                                                                              \
+    case RR:                                                                                           \
+        return dfres ? launch_helm_mixed_R<RR * 16 / LL, LL, true>(p, order, m0, count, f, u, fac, s)  \
+                     : launch_helm_mixed_R<RR * 16 / LL, LL, false>(p, order, m0, count, f, u, fac, s);
+    if (mixed_lanes(p.R_h) == 16) {
+        switch (p.R_h) {
+            SHEN_CASE(2, 16) SHEN_CASE(4, 16) SHEN_CASE(8, 16) SHEN_CASE(16, 16) SHEN_CASE(24, 16)
+            SHEN_CASE(32, 16) SHEN_CASE(48, 16) SHEN_CASE(64, 16)
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (p.R_h) {
-        SHEN_CASE(2) SHEN_CASE(4) SHEN_CASE(8) SHEN_CASE(16) SHEN_CASE(24) SHEN_CASE(32) SHEN_CASE(48)
-        SHEN_CASE(64)
+        SHEN_CASE(16, 32) SHEN_CASE(24, 32) SHEN_CASE(32, 32) SHEN_CASE(48, 32) SHEN_CASE(64, 32)
     default: return cudaErrorInvalidValue;
     }
 #undef SHEN_CASE

@@ -42,7 +42,7 @@ def test_mixed_all_modes(problem, precision, wl):
 
 
 @pytest.mark.parametrize("problem,precision", CASES)
-@pytest.mark.parametrize("N", [8, 9, 12, 63, 65, 66, 130, 257, 1000, 1537, 2048])
+@pytest.mark.parametrize("N", [8, 9, 12, 63, 65, 66, 130, 257, 300, 513, 1000, 1537, 2048])
 def test_mixed_ragged_N(problem, precision, N):
     """Chains that do not fill the lanes evenly; N up to the largest supported size."""
     nu, dt = 1 / 2000, 5e-5
