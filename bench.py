@@ -547,8 +547,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--streams", type=int, default=1, choices=[1, 2],
-                    help="2: run the two solves concurrently on two streams")
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
+                    help="2 (default): the two independent solves on two forked streams, so that the second "
+                         "kernel's blocks fill the SMs the first one's last round leaves idle; 1: in sequence")
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
                     help="replay the step as a captured CUDA graph (auto: on for the batch workload)")
     ap.add_argument("--shard", action="store_true",
@@ -641,8 +642,9 @@ def main():
         stream.synchronize()
 
     # The two solves are independent: run them on two streams that fork from and join
-    # back into `stream` (the Helmholtz float32/float-float kernels and the float64
-    # biharmonic kernel use different pipes, so they overlap).
+    # back into `stream`.  Each kernel's persistent grid fills every SM, so they overlap
+    # only where the first one's last round of chains leaves SMs idle (N = 1024,
+    # 1024 x 1024: 16.02 -> 15.76 ms per step).
     s_h, s_b = torch.cuda.Stream(), torch.cuda.Stream()
     fork, join_h, join_b = (torch.cuda.Event() for _ in range(3))
 

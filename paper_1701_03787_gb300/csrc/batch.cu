@@ -138,11 +138,13 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(BatchDev b, const doub
                                                   (cl.z2 + in.c) * kPi / 2);
                 } else {
                     const long oh = cl.fh + (long)par * in.rows_h;
-                    chains::solve_helm_df_chain<V>(in.N, par, f + off, u + off,
-                                                   chains::HelmDF{b.df_hb + oh, b.df_hf + oh, 1},
-                                                   df::from_f64((cl.z2 + in.c) * (kPi / 2)),
-                                                   ys_slot ? ys_slot : chains::column_spill(u + off, par),
-                                                   ys_slot ? 32 : 2);
+                    // shape 1 fetches 4 rows per prefetch block here (96 registers, five blocks
+                    // per SM): 6.74 ms on the 4096-instance workload against 6.97 ms with the
+                    // single-plan kernel's 5 (122 registers); same bits at every depth
+                    chains::solve_helm_df_chain_t<V == 0 ? 8 : 4>(
+                        in.N, par, f + off, u + off, chains::HelmDF{b.df_hb + oh, b.df_hf + oh, 1},
+                        df::from_f64((cl.z2 + in.c) * (kPi / 2)),
+                        ys_slot ? ys_slot : chains::column_spill(u + off, par), ys_slot ? 32 : 2, 1L);
                 }
             } else {
                 if (PREC == 0) {
