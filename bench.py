@@ -972,11 +972,11 @@ def main():
                     stream.synchronize()
                     fp64_ms[f"{problem}_f32_r{steps}_{resid}"] = a.elapsed_time(b)
             del work
-            # the warp-per-mode float32-sweep + one-refinement-step kernels of the Helmholtz problem
+            # the fused float32-sweep + one-refinement-step kernels of the Helmholtz problem
             for name in ("df_r1", "fp32_r1"):
                 try:
                     plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)
-                except Exception:                    # not built for this N (warp-per-mode limit)
+                except Exception:                    # not built for this N (limit of the fused kernels)
                     continue
                 a.record(stream)
                 plan.helmholtz_solve(f_h, u_h, precision=name, stream=stream)

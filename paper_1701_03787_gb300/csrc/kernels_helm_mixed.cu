@@ -364,7 +364,8 @@ cudaError_t launch_helm_mixed_R(const Plan &p, const int *order, long m0, long c
 
 }  // namespace
 
-// Rows per lane of the warp-per-mode Helmholtz kernels (16 lanes per parity chain).
+// Rows per lane of the fused Helmholtz refinement kernels, counted at 16 lanes per parity
+// chain (R16; chains of more than 128 rows then run on 32 lanes with R16 / 2 rows each).
 int helm_mixed_R(int N) {
     const int rows = (N - 2 + 1) / 2;
     const int R = (rows + 15) / 16;

@@ -242,7 +242,7 @@ shen_status create_from_z2(shen_plan_t *out, int N, long n_modes, const double *
         p.d_dd = d;
         PLAN_TRY(cudaMemcpyAsync(d, dd.data(), dd.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
     }
-    // float32 factors in the lane layout of the warp-per-mode kernels
+    // float32 factors in the lane layout of the fused Helmholtz refinement kernels
     p.df_only = (flags & SHEN_PLAN_DF_ONLY) != 0;
     p.R_h = p.df_only ? 0 : helm_mixed_R(N);
     if (p.R_h > 0) {

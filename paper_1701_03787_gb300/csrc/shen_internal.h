@@ -66,7 +66,7 @@ struct Plan {
     int *d_err = nullptr;                 // [4]: flag, first bad class, chains with a bad pivot,
                                           //      a transform column copy that did not complete
     unsigned long long *d_resmax = nullptr;   // largest relative residual of the last shen_residual (bits)
-    int R_h = 0;                          // rows per lane of the warp-per-mode Helmholtz kernels
+    int R_h = 0;                          // rows per lane (at 16 lanes) of the fused Helmholtz kernels
     float *d_fac_df = nullptr;            // backing store of the float-float factor streams below
     // float-float factor streams, row i of chain ch = 2 class + parity at [i * 2 n_classes + ch]
     const float4 *df_hb = nullptr, *df_bf = nullptr, *df_bb0 = nullptr, *df_bb1 = nullptr;
