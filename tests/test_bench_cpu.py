@@ -123,3 +123,13 @@ def test_source_hash_ignores_comments(tmp_path, monkeypatch):
     assert bench.sources_sha1(("k.cu",)) == h0
     (csrc / "k.cu").write_text("// reworded\nint a = 3; /* other */ int b = 2;\n")
     assert bench.sources_sha1(("k.cu",)) != h0
+
+
+def test_precision_per_problem():
+    """A refinement precision names the fused Helmholtz kernels; the biharmonic solve of the
+    step then runs in float-float (its plain solve has no fused refinement)."""
+    assert bench.resolve_precision("df_r1") == {"helmholtz": "df_r1", "biharmonic": "df"}
+    assert bench.resolve_precision("fp32_r1") == {"helmholtz": "fp32_r1", "biharmonic": "df"}
+    for p in ("fp64", "df"):
+        assert bench.resolve_precision(p) == {"helmholtz": p, "biharmonic": p}
+    assert set(bench.resolve_precision("auto")) == {"helmholtz", "biharmonic"}
