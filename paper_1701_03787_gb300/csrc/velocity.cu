@@ -28,8 +28,10 @@ namespace {
 using chains::CF2;
 using df::F2;
 
+// Element k of a u or g column, with the sweeps' 256-byte L2 fetch size (chains::ld_col:
+// 10.72 -> 10.58 ms at N = 1024, 1024 x 1024).  The outputs never overlap u or g.
 __device__ __forceinline__ CF2 ld_cf2(const double *col, long k) {
-    const double2 v = reinterpret_cast<const double2 *>(col)[k];
+    const double2 v = chains::ld_col(reinterpret_cast<const double2 *>(col) + k);
     return CF2{df::from_f64(v.x), df::from_f64(v.y)};
 }
 
