@@ -31,6 +31,17 @@ namespace {
 constexpr float kPiHi = 3.14159274101257324f;           // float(pi)
 constexpr float kPiLo = -8.74227765734758577e-08f;      // pi - float(pi)
 constexpr unsigned kFull = 0xffffffffu;
+
+// One complex row of f with a 256-byte L2 fetch size: a lane reads its segment of the
+// column row by row, so one miss brings its next rows into L2 (9.39 -> 9.25 ms for the
+// float-float-residual kernel at N = 1024, 1024 x 1024).  u is written only after the
+// warp's last read of f; with 32 lanes per chain the two warps of a mode (one per parity)
+// touch disjoint rows.
+__device__ __forceinline__ double2 ld_f(const double2 *p) {
+    double2 v;
+    asm volatile("ld.global.L2::256B.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
 // chains of at least this many rows per lane at 16 lanes run on 32 lanes
 #ifndef SHEN_MIXED_L32_MIN
 #define SHEN_MIXED_L32_MIN 16
@@ -188,12 +199,12 @@ __device__ __forceinline__ void residual(float2 *rs, const float2 *u0s, const do
     // per-class constants: pi alpha / 2 (float-float)
     const df::F2 pih = df::mul(pi_df, df::F2{0.5f * a_df.hi, 0.5f * a_df.lo});
     const int k_top = 2 * (s * R + R - 1) + p;
-    double2 fnext = k_top < n ? reinterpret_cast<const double2 *>(fcol)[k_top] : make_double2(0.0, 0.0);
+    double2 fnext = k_top < n ? ld_f(reinterpret_cast<const double2 *>(fcol) + k_top) : make_double2(0.0, 0.0);
 #pragma unroll 1
     for (int j = R - 1; j >= 0; j--) {
         const int k = 2 * (s * R + j) + p;
         const double2 fk = fnext;
-        if (j > 0 && k - 2 < n) fnext = reinterpret_cast<const double2 *>(fcol)[k - 2];   // prefetch
+        if (j > 0 && k - 2 < n) fnext = ld_f(reinterpret_cast<const double2 *>(fcol) + k - 2);   // prefetch
         const float2 um = j > 0 ? u0s[(j - 1) * 32 + lane] : below;
         float2 r = f2(0.f, 0.f);
         if (k < n) {
@@ -283,7 +294,7 @@ __global__ void __launch_bounds__(64) helm_mixed_kernel(Plan p, const int *order
     for (int j = 0; j < R; j++) {
         const int i = s * R + j, k = 2 * i + par;
         if (k < n) {
-            const double2 fk = reinterpret_cast<const double2 *>(fcol)[k];
+            const double2 fk = ld_f(reinterpret_cast<const double2 *>(fcol) + k);
             if (DF) w[j] = f2(df::hi_f64(fk.x), df::hi_f64(fk.y));
             else w[j] = f2((float)fk.x, (float)fk.y);
         } else {
